@@ -1,0 +1,301 @@
+/*
+ * edpc.h - C ABI of the GB300-native EDPC compressor.
+ *
+ * EDPC ("Accelerating Lossless Compression via Lightweight Probability
+ * Models and Decoupled Parallel Dataflow", ACM MM 2025) is an autoregressive
+ * lossless byte compressor. Algorithm 1 codes each byte x_i with arithmetic
+ * coding under Pr(i) = Model(x_{i-t..i-1}) and then takes one Adam step on
+ * the cross-entropy (Sec. 2.1, Eqs. 1-2). The decoder replays the same
+ * loop on the decoded bytes. The model (Sec. 3) is a byte embedding,
+ * Multi-path Byte Refinement Blocks (MBRB, Sec. 3.1.2, Eqs. 9-13), and a
+ * Latent Transformation Engine (LTE, Sec. 3.2, Eqs. 14-16) whose Feature
+ * Distribution Matrix U is learned per stream. The input is split into b
+ * streams that advance one byte per step together (Sec. 3.3). The model
+ * stage and the coder stage run as a decoupled pipeline (DPCA, Sec. 3.3).
+ *
+ * Conventions for every entry point:
+ *   - Return 0 (EDPC_OK) on success, else one of the EDPC_E* codes.
+ *     edpc_strerror() names each code, and edpc_last_error() gives the
+ *     detail of the last failure on the calling thread.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory on the current device. Input buffers are borrowed and
+ *     never written. Buffers the library allocates for the caller are
+ *     released with edpc_free().
+ *   - All floating-point tensors are FP32, row-major, densely packed.
+ *   - A NULL cuda_stream means the library's own stream. Calls return after
+ *     their GPU work has completed unless stated otherwise.
+ *   - Failures never leave a GPU wait spinning: every device-side wait is
+ *     bounded and reports EDPC_ETIMEOUT.
+ */
+#ifndef EDPC_H
+#define EDPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EDPC_ABI_VERSION 1u
+#define EDPC_FORMAT_VERSION 1u
+
+/* Status codes. */
+#define EDPC_OK 0
+#define EDPC_EINVAL 1    /* bad argument or configuration */
+#define EDPC_ENOMEM 2    /* host or device allocation failed */
+#define EDPC_ECORRUPT 3  /* bad magic, CRC, length or coder state in a bitstream */
+#define EDPC_EVERSION 4  /* bitstream format version not supported */
+#define EDPC_ECUDA 5     /* a CUDA runtime or driver call failed */
+#define EDPC_ETIMEOUT 6  /* a bounded device-side wait expired */
+#define EDPC_EARCH 7     /* bitstream was made by a GEMM/precision variant this build lacks */
+
+/* Arithmetic of the model's GEMMs. Softmax, CDF quantization, optimizer
+ * state and the FDM stay FP32 in every mode. */
+#define EDPC_FP32 0u     /* plain FP32 (SIMT) GEMMs */
+#define EDPC_BF16 1u     /* BF16 operands, FP32 accumulation (tcgen05) */
+
+/* cfg.flags */
+#define EDPC_FLAG_NO_PIPELINE 1u  /* run the coder stage inline (DPCA off) */
+#define EDPC_FLAG_NO_GRAPH 2u     /* launch every kernel eagerly (no CUDA graph) */
+
+/*
+ * Model and coder configuration. Everything here that changes the bitstream
+ * is stored in the header, so edpc_decompress needs no cfg.
+ *
+ *   streams    b, the number of parallel streams (the paper's batch size,
+ *              Sec. 4.4). The input is split into b_eff = min(b, max(1, n/K))
+ *              contiguous streams of q or q+1 bytes (q = n / b_eff).
+ *   context    K, history bytes per prediction (t in Algorithm 1; 16 in
+ *              Sec. 4.1). The first K bytes of each stream are coded with
+ *              equal probability (Algorithm 1, first line).
+ *   embed_dim  D, the byte embedding width; F = K * D is the model width.
+ *   latent     F' = F / r, the LTE latent width (Eq. 14); the FDM of each
+ *              stream is F' x F' (Eq. 15).
+ *   hidden     H, the width of each MBRB branch (Eq. 10).
+ *   blocks     n MBRBs: n/2 "Local" before the LTE and n - n/2 "Global"
+ *              after it (Fig. 3 caption).
+ *   branches   k, the MBRB paths multiplied together (Eq. 11); 2 by default
+ *              (Sec. 3.1.2), 1..3 accepted.
+ *   lr         Adam learning rate (Sec. 4.1: 1e-3).
+ *   precision  EDPC_FP32 or EDPC_BF16.
+ *   seed       seed of the initial parameters (SplitMix64 counter streams).
+ *
+ * Limits: 1 <= context <= 256; embed_dim a multiple of 8 in [8, 64];
+ * latent and hidden multiples of 8; F <= 2048, F' <= 1024, H <= 2048;
+ * streams <= 65536; blocks <= 16.
+ */
+typedef struct {
+  uint32_t version;     /* must be EDPC_ABI_VERSION */
+  uint32_t streams;
+  uint32_t context;
+  uint32_t embed_dim;
+  uint32_t latent;
+  uint32_t hidden;
+  uint32_t blocks;
+  uint32_t branches;
+  float lr;
+  uint32_t precision;
+  uint64_t seed;
+  uint32_t flags;
+  uint32_t reserved;
+} edpc_cfg;
+
+/* Fills *cfg with the small FP32 configuration: b = 4, K = 16, D = 16,
+ * F' = 128, H = 128, n = 2, k = 2, lr = 1e-3, seed = 1. */
+void edpc_default_cfg(edpc_cfg* cfg);
+
+/* Human-readable name of a status code (static storage). */
+const char* edpc_strerror(int status);
+
+/* Detail of the last failure on the calling thread (static thread-local
+ * storage, overwritten by the next failure). */
+const char* edpc_last_error(void);
+
+/* Number of shared FP32 parameters (embedding, MBRBs, LTE projections,
+ * head) in the canonical flat order documented at edpc_model_get_state. */
+uint64_t edpc_param_count(const edpc_cfg* cfg);
+
+/* Releases a buffer returned by the library. NULL is ignored. */
+void edpc_free(void* p);
+
+/*
+ * One-shot compression of host bytes (Algorithm 1, encoding side).
+ *   buf, len   input (host). len may be 0.
+ *   cfg        configuration (host, borrowed).
+ *   out        receives a library-allocated host buffer holding the
+ *              container: header, per-stream lengths, CRCs, substreams.
+ *   out_len    receives its size in bytes.
+ * Errors: EINVAL (NULL pointers, bad cfg), ENOMEM, ECUDA, ETIMEOUT.
+ */
+int edpc_compress(const uint8_t* buf, size_t len, const edpc_cfg* cfg,
+                  uint8_t** out, size_t* out_len);
+
+/*
+ * One-shot decompression (Algorithm 1, decoding side). The configuration is
+ * read from the header.
+ *   bits, bits_len  container from edpc_compress (host).
+ *   out, out_len    receive a library-allocated host buffer with the bytes.
+ * Errors: ECORRUPT (bad magic, header CRC, lengths, or the CRC32 of the
+ * decoded data does not match), EVERSION, EARCH, ENOMEM, ECUDA, ETIMEOUT.
+ */
+int edpc_decompress(const uint8_t* bits, size_t bits_len, uint8_t** out, size_t* out_len);
+
+/* Reads the configuration and original length stored in a container
+ * header without decoding. Errors: ECORRUPT, EVERSION. */
+int edpc_peek(const uint8_t* bits, size_t bits_len, edpc_cfg* cfg, uint64_t* orig_len,
+              uint32_t* streams_eff);
+
+/* ------------------------------------------------------------------------ */
+/* Sessions: the same loop, advanced a bounded number of steps per call.    */
+/* ------------------------------------------------------------------------ */
+typedef struct edpc_session edpc_session;
+
+/*
+ * Opens an encoder over `len` input bytes.
+ *   data            input bytes. If data_on_device is 0 they are host bytes
+ *                   and each run() copies the bytes its steps need to the
+ *                   device; otherwise `data` is a device pointer that must
+ *                   stay valid until the session is closed.
+ *   cuda_stream     cudaStream_t on which the model stage runs (NULL: the
+ *                   library's own). The coder stage runs on a second stream
+ *                   of the library's and joins back before run() returns.
+ * The uniform prefix (the first K bytes of each stream) is coded at open.
+ */
+int edpc_encoder_open(const edpc_cfg* cfg, const uint8_t* data, size_t len, int data_on_device,
+                      void* cuda_stream, edpc_session** out);
+
+/*
+ * Advances the session by up to `max_steps` model steps. A model step codes
+ * one byte of every active stream (one iteration of Algorithm 1's loop for
+ * the whole batch). *steps_done receives the number run (0 when finished).
+ * If `sync` is 0 the call may return before the GPU work finishes; the
+ * work is ordered on cuda_stream.
+ */
+int edpc_session_run(edpc_session* s, uint64_t max_steps, int sync, uint64_t* steps_done);
+
+/* Model steps left (total = max stream length - K, or 0). */
+int edpc_session_remaining(const edpc_session* s, uint64_t* steps_left);
+
+/* Encoder: runs any remaining steps, flushes the coders and returns the
+ * container (library-allocated host buffer). */
+int edpc_encoder_finish(edpc_session* s, uint8_t** out, size_t* out_len);
+
+/*
+ * Opens a decoder over a container. If out_device is non-NULL the decoded
+ * bytes are written there (device, orig_len bytes, caller-owned);
+ * otherwise the library allocates the device buffer.
+ */
+int edpc_decoder_open(const uint8_t* bits, size_t bits_len, void* out_device, void* cuda_stream,
+                      edpc_session** out);
+
+/* Decoder: runs remaining steps, checks the CRC32 of the decoded bytes and
+ * copies them to `out_host` (orig_len bytes, caller-owned) if non-NULL. */
+int edpc_decoder_finish(edpc_session* s, uint8_t* out_host);
+
+/* Per-session counters. kernel_ms_* are CUDA-event times of the FDM
+ * kernels, averaged over the launches recorded since profiling was
+ * enabled (see edpc_session_profile). */
+typedef struct {
+  uint64_t steps_run;
+  uint64_t steps_total;
+  uint32_t streams;
+  uint32_t launches_per_step;    /* kernels this library launches per model step */
+  double fdm_fwd_ms;             /* mean duration of one FDM forward launch */
+  double fdm_bwd_ms;             /* mean duration of one FDM backward+Adam launch */
+  uint64_t fdm_samples;
+  uint64_t coded_bytes;          /* substream bytes so far (after finish: final) */
+} edpc_stats;
+
+int edpc_session_stats(const edpc_session* s, edpc_stats* st);
+
+/* Turns on CUDA-event timing of the FDM kernels for subsequent run()
+ * calls. It records events around those two launches in every step. */
+int edpc_session_profile(edpc_session* s, int on);
+
+void edpc_session_close(edpc_session* s);
+
+/* ------------------------------------------------------------------------ */
+/* Single kernels on device buffers, for tests and benchmarks.              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * CDF quantization of `rows` FP32 probability vectors, the coder's input
+ * (Sec. 2.1 "Data Encoding"; the paper leaves the rule open, this is the
+ * library's rule).
+ *   p     device, rows x 256 FP32.
+ *   freq  device, rows x 256 uint32 out: f_j = 1 + floor(fl32(p_j * 65280)),
+ *         remainder 65536 - sum(f) added to the first largest f.
+ *   cum   device, rows x 257 uint32 out: exclusive prefix sums, cum[256] = 65536.
+ */
+int edpc_cdf_quantize(const float* p, uint32_t rows, uint32_t* freq, uint32_t* cum,
+                      void* cuda_stream);
+
+/*
+ * Range-encodes `nsym` symbols for each of `streams` independent coders
+ * (one 32-bit range coder per stream, the arithmetic coding of Sec. 2.1).
+ *   sym   device, nsym x streams uint32, step-major: sym[t*streams + s] =
+ *         cum | (freq - 1) << 16 of stream s's t-th symbol, or 0xFFFFFFFF
+ *         to skip. cum + freq <= 65536.
+ *   out   device, streams x cap bytes: stream s writes at out + s*cap.
+ *   out_len device, streams uint32 out: bytes written per stream.
+ * Errors: EINVAL if some stream needs more than cap bytes (its output is
+ * then truncated and out_len holds cap).
+ */
+int edpc_range_encode(const uint32_t* sym, uint32_t nsym, uint32_t streams, uint8_t* out,
+                      uint32_t cap, uint32_t* out_len, void* cuda_stream);
+
+/* ------------------------------------------------------------------------ */
+/* Model: one training step at a given state (gradient and parity checks).  */
+/* ------------------------------------------------------------------------ */
+typedef struct edpc_model edpc_model;
+
+/* A model for `streams` rows with cfg's dims and precision, initialised
+ * from cfg.seed exactly as the encoder initialises it. */
+int edpc_model_create(const edpc_cfg* cfg, uint32_t streams, edpc_model** out);
+void edpc_model_destroy(edpc_model* m);
+
+/*
+ * State exchange (host buffers; NULL skips that part).
+ *   shared  edpc_param_count(cfg) floats in the canonical order:
+ *           E[256][D];
+ *           for each block j = 0..n-1: ln_g[F], ln_b[F], W[k*H][F] (branch i
+ *             in rows i*H..i*H+H-1), c[k*H], Wo[F][H], co[F];
+ *           LTE W1[F'][F], b1[F'], W2[F][F'], b2[F];
+ *           head Wh[256][F], bh[256].
+ *   fdm     streams x F' x F' floats, U_s[i][j] at (s*F' + i)*F' + j.
+ *   m_*, v_* Adam moments in the same layouts. t = Adam steps taken.
+ */
+int edpc_model_get_state(const edpc_model* m, float* shared, float* fdm, float* m_shared,
+                         float* v_shared, float* m_fdm, float* v_fdm, uint32_t* t);
+int edpc_model_set_state(edpc_model* m, const float* shared, const float* fdm, const float* m_shared,
+                         const float* v_shared, const float* m_fdm, const float* v_fdm, uint32_t t);
+
+/*
+ * Forward pass (Eqs. 9-16 and the head) on host inputs.
+ *   ctx     host, streams x K bytes, oldest first.
+ *   logits  host out, streams x 256 (may be NULL).
+ *   probs   host out, streams x 256 FP32 softmax (may be NULL).
+ */
+int edpc_model_forward(edpc_model* m, const uint8_t* ctx, float* logits, float* probs);
+
+/*
+ * Gradient of the mean cross-entropy over the active rows (Eq. 2) at the
+ * current state, without updating it.
+ *   targets  host, streams bytes.   active  host, streams bytes (0/1).
+ *   g_shared host out (param_count floats, canonical order) or NULL.
+ *   g_fdm    host out (streams x F' x F') or NULL.
+ */
+int edpc_model_backward(edpc_model* m, const uint8_t* ctx, const uint8_t* targets,
+                        const uint8_t* active, float* g_shared, float* g_fdm);
+
+/* Forward, backward and one Adam step (Sec. 4.1), exactly as one model step
+ * of the encoder: inactive rows leave their FDM and its moments unchanged. */
+int edpc_model_train_step(edpc_model* m, const uint8_t* ctx, const uint8_t* targets,
+                          const uint8_t* active);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EDPC_H */

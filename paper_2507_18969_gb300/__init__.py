@@ -1,0 +1,241 @@
+"""GB300-native EDPC: an online-learning lossless byte compressor.
+
+Python binding of the C ABI in include/edpc.h (libedpc.so, built in-tree by
+``_build.build()``). Every function here only marshals arguments; the
+method itself runs in the library's CUDA kernels. The library must be
+built: importing this package does not build it, and a missing library
+raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from ._lib import (EDPC_BF16, EDPC_FLAG_NO_GRAPH, EDPC_FLAG_NO_PIPELINE, EDPC_FP32, Cfg, EdpcError,
+                   Stats, check, load)
+
+__all__ = [
+    "Cfg", "EdpcError", "EDPC_FP32", "EDPC_BF16", "EDPC_FLAG_NO_PIPELINE", "EDPC_FLAG_NO_GRAPH",
+    "make_cfg", "compress", "decompress", "peek", "param_count", "Encoder", "Decoder", "Model",
+    "cdf_quantize", "range_encode", "load",
+]
+
+
+def make_cfg(streams=4, context=16, embed_dim=16, latent=128, hidden=128, blocks=2, branches=2,
+             lr=1e-3, precision=EDPC_FP32, seed=1, flags=0) -> Cfg:
+    c = Cfg()
+    load().edpc_default_cfg(C.byref(c))
+    c.streams, c.context, c.embed_dim = streams, context, embed_dim
+    c.latent, c.hidden, c.blocks, c.branches = latent, hidden, blocks, branches
+    c.lr, c.precision, c.seed, c.flags = lr, precision, seed, flags
+    return c
+
+
+def _buf(x) -> np.ndarray:
+    return np.ascontiguousarray(np.frombuffer(x, dtype=np.uint8) if isinstance(x, (bytes, bytearray)) else x,
+                                dtype=np.uint8)
+
+
+def _ptr(a: np.ndarray):
+    return C.c_void_p(a.ctypes.data) if a.size else C.c_void_p(0)
+
+
+def param_count(cfg: Cfg) -> int:
+    return int(load().edpc_param_count(C.byref(cfg)))
+
+
+def compress(data, cfg: Cfg) -> bytes:
+    lib = load()
+    a = _buf(data)
+    out = C.c_void_p()
+    n = C.c_size_t()
+    check(lib.edpc_compress(_ptr(a), a.size, C.byref(cfg), C.byref(out), C.byref(n)), "edpc_compress")
+    try:
+        return C.string_at(out, n.value)
+    finally:
+        lib.edpc_free(out)
+
+
+def decompress(bits) -> np.ndarray:
+    lib = load()
+    a = _buf(bits)
+    out = C.c_void_p()
+    n = C.c_size_t()
+    check(lib.edpc_decompress(_ptr(a), a.size, C.byref(out), C.byref(n)), "edpc_decompress")
+    try:
+        return np.frombuffer(C.string_at(out, n.value), dtype=np.uint8).copy()
+    finally:
+        lib.edpc_free(out)
+
+
+def peek(bits):
+    lib = load()
+    a = _buf(bits)
+    c = Cfg()
+    n = C.c_uint64()
+    b = C.c_uint32()
+    check(lib.edpc_peek(_ptr(a), a.size, C.byref(c), C.byref(n), C.byref(b)), "edpc_peek")
+    return c, n.value, b.value
+
+
+class _Session:
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    def run(self, max_steps: int, sync: bool = True) -> int:
+        done = C.c_uint64()
+        check(load().edpc_session_run(self._h, max_steps, int(sync), C.byref(done)), "edpc_session_run")
+        return done.value
+
+    def remaining(self) -> int:
+        n = C.c_uint64()
+        check(load().edpc_session_remaining(self._h, C.byref(n)), "edpc_session_remaining")
+        return n.value
+
+    def profile(self, on: bool = True) -> None:
+        check(load().edpc_session_profile(self._h, int(on)), "edpc_session_profile")
+
+    def stats(self) -> Stats:
+        s = Stats()
+        check(load().edpc_session_stats(self._h, C.byref(s)), "edpc_session_stats")
+        return s
+
+    def close(self) -> None:
+        if self._h:
+            load().edpc_session_close(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Encoder(_Session):
+    """Encoder session. ``data``: host bytes / uint8 array, or ``device_ptr`` + ``length``."""
+
+    def __init__(self, cfg: Cfg, data=None, device_ptr: int | None = None, length: int | None = None,
+                 stream: int | None = None):
+        lib = load()
+        h = C.c_void_p()
+        if device_ptr is not None:
+            keep = None
+            check(lib.edpc_encoder_open(C.byref(cfg), C.c_void_p(device_ptr), int(length), 1,
+                                        C.c_void_p(stream or 0), C.byref(h)), "edpc_encoder_open")
+        else:
+            keep = _buf(data)
+            check(lib.edpc_encoder_open(C.byref(cfg), _ptr(keep), keep.size, 0, C.c_void_p(stream or 0),
+                                        C.byref(h)), "edpc_encoder_open")
+        super().__init__(h, keep)
+
+    def finish(self) -> bytes:
+        lib = load()
+        out = C.c_void_p()
+        n = C.c_size_t()
+        check(lib.edpc_encoder_finish(self._h, C.byref(out), C.byref(n)), "edpc_encoder_finish")
+        try:
+            return C.string_at(out, n.value)
+        finally:
+            lib.edpc_free(out)
+
+
+class Decoder(_Session):
+    def __init__(self, bits, out_device_ptr: int | None = None, stream: int | None = None):
+        lib = load()
+        keep = _buf(bits)
+        h = C.c_void_p()
+        check(lib.edpc_decoder_open(_ptr(keep), keep.size, C.c_void_p(out_device_ptr or 0), C.c_void_p(stream or 0),
+                                    C.byref(h)), "edpc_decoder_open")
+        self.n = peek(keep)[1]
+        super().__init__(h, keep)
+
+    def finish(self, to_host: bool = True):
+        out = np.empty(self.n, dtype=np.uint8) if to_host else None
+        check(load().edpc_decoder_finish(self._h, _ptr(out) if to_host else C.c_void_p(0)), "edpc_decoder_finish")
+        return out
+
+
+class Model:
+    """One model step at a given state (gradient and parity checks)."""
+
+    def __init__(self, cfg: Cfg, streams: int):
+        self.cfg = cfg
+        self.b = streams
+        self.np = param_count(cfg)
+        self.fdm = streams * cfg.latent * cfg.latent
+        h = C.c_void_p()
+        check(load().edpc_model_create(C.byref(cfg), streams, C.byref(h)), "edpc_model_create")
+        self._h = h
+
+    def close(self):
+        if self._h:
+            load().edpc_model_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_state(self):
+        P = np.empty(self.np, np.float32)
+        U = np.empty(self.fdm, np.float32)
+        M = np.empty(self.np, np.float32)
+        V = np.empty(self.np, np.float32)
+        Um = np.empty(self.fdm, np.float32)
+        Uv = np.empty(self.fdm, np.float32)
+        t = C.c_uint32()
+        check(load().edpc_model_get_state(self._h, _ptr(P), _ptr(U), _ptr(M), _ptr(V), _ptr(Um), _ptr(Uv),
+                                          C.byref(t)), "edpc_model_get_state")
+        return dict(P=P, U=U, M=M, V=V, Um=Um, Uv=Uv, t=t.value)
+
+    def set_state(self, P=None, U=None, M=None, V=None, Um=None, Uv=None, t=0):
+        arrs = [None if x is None else np.ascontiguousarray(x, dtype=np.float32) for x in (P, U, M, V, Um, Uv)]
+        ptrs = [C.c_void_p(0) if a is None else _ptr(a) for a in arrs]
+        check(load().edpc_model_set_state(self._h, *ptrs, t), "edpc_model_set_state")
+
+    def forward(self, ctx):
+        ctx = np.ascontiguousarray(ctx, dtype=np.uint8)
+        z = np.empty((self.b, 256), np.float32)
+        p = np.empty((self.b, 256), np.float32)
+        check(load().edpc_model_forward(self._h, _ptr(ctx), _ptr(z), _ptr(p)), "edpc_model_forward")
+        return z, p
+
+    def backward(self, ctx, targets, active):
+        ctx = np.ascontiguousarray(ctx, dtype=np.uint8)
+        tg = np.ascontiguousarray(targets, dtype=np.uint8)
+        ac = np.ascontiguousarray(active, dtype=np.uint8)
+        g = np.empty(self.np, np.float32)
+        gu = np.empty(self.fdm, np.float32)
+        check(load().edpc_model_backward(self._h, _ptr(ctx), _ptr(tg), _ptr(ac), _ptr(g), _ptr(gu)),
+              "edpc_model_backward")
+        return g, gu
+
+    def train_step(self, ctx, targets, active):
+        ctx = np.ascontiguousarray(ctx, dtype=np.uint8)
+        tg = np.ascontiguousarray(targets, dtype=np.uint8)
+        ac = np.ascontiguousarray(active, dtype=np.uint8)
+        check(load().edpc_model_train_step(self._h, _ptr(ctx), _ptr(tg), _ptr(ac)), "edpc_model_train_step")
+
+
+def cdf_quantize(p_dev: int, rows: int, freq_dev: int, cum_dev: int, stream: int = 0) -> None:
+    """Device pointers: p (rows x 256 f32) -> freq (rows x 256 u32), cum (rows x 257 u32)."""
+    check(load().edpc_cdf_quantize(C.c_void_p(p_dev), rows, C.c_void_p(freq_dev), C.c_void_p(cum_dev),
+                                   C.c_void_p(stream)), "edpc_cdf_quantize")
+
+
+def range_encode(sym_dev: int, nsym: int, streams: int, out_dev: int, cap: int, out_len_dev: int,
+                 stream: int = 0) -> None:
+    """Device pointers: sym (nsym x streams u32) -> out (streams x cap bytes), out_len (streams u32)."""
+    check(load().edpc_range_encode(C.c_void_p(sym_dev), nsym, streams, C.c_void_p(out_dev), cap,
+                                   C.c_void_p(out_len_dev), C.c_void_p(stream)), "edpc_range_encode")

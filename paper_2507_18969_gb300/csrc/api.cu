@@ -1,0 +1,989 @@
+// C ABI of the library: configuration checks, the container format, encoder
+// and decoder sessions (Algorithm 1 over b streams with the decoupled coder
+// stage of Sec. 3.3), single-kernel entry points, and the model API.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "engine.cuh"
+
+using namespace edpc;
+
+// ==========================================================================================
+// errors
+// ==========================================================================================
+namespace edpc {
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+}  // namespace edpc
+
+extern "C" const char* edpc_strerror(int status) {
+  switch (status) {
+    case EDPC_OK: return "ok";
+    case EDPC_EINVAL: return "invalid argument";
+    case EDPC_ENOMEM: return "out of memory";
+    case EDPC_ECORRUPT: return "corrupt bitstream";
+    case EDPC_EVERSION: return "unsupported bitstream version";
+    case EDPC_ECUDA: return "CUDA error";
+    case EDPC_ETIMEOUT: return "device wait timed out";
+    case EDPC_EARCH: return "bitstream variant not supported by this build";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* edpc_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" void edpc_free(void* p) { free(p); }
+
+extern "C" void edpc_default_cfg(edpc_cfg* c) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->version = EDPC_ABI_VERSION;
+  c->streams = 4;
+  c->context = 16;
+  c->embed_dim = 16;
+  c->latent = 128;
+  c->hidden = 128;
+  c->blocks = 2;
+  c->branches = 2;
+  c->lr = 1e-3f;
+  c->precision = EDPC_FP32;
+  c->seed = 1;
+}
+
+static int check_cfg(const edpc_cfg* c) {
+  if (!c) return fail(EDPC_EINVAL, "cfg is NULL");
+  if (c->version != EDPC_ABI_VERSION) return fail(EDPC_EINVAL, "cfg.version != EDPC_ABI_VERSION");
+  if (c->streams < 1 || c->streams > 65536) return fail(EDPC_EINVAL, "streams must be in [1, 65536]");
+  if (c->context < 1 || c->context > 256) return fail(EDPC_EINVAL, "context must be in [1, 256]");
+  if (c->embed_dim < 8 || c->embed_dim > 64 || c->embed_dim % 8)
+    return fail(EDPC_EINVAL, "embed_dim must be a multiple of 8 in [8, 64]");
+  if ((uint64_t)c->context * c->embed_dim > 2048) return fail(EDPC_EINVAL, "context * embed_dim must be <= 2048");
+  if (c->latent < 8 || c->latent > 1024 || c->latent % 8)
+    return fail(EDPC_EINVAL, "latent must be a multiple of 8 in [8, 1024]");
+  if (c->hidden < 8 || c->hidden > 2048 || c->hidden % 8)
+    return fail(EDPC_EINVAL, "hidden must be a multiple of 8 in [8, 2048]");
+  if (c->blocks < 1 || c->blocks > (uint32_t)kMaxBlocks) return fail(EDPC_EINVAL, "blocks must be in [1, 16]");
+  if (c->branches < 1 || c->branches > 3) return fail(EDPC_EINVAL, "branches must be in [1, 3]");
+  if (!(c->lr > 0.f) || !std::isfinite(c->lr)) return fail(EDPC_EINVAL, "lr must be finite and > 0");
+  if (c->precision != EDPC_FP32 && c->precision != EDPC_BF16) return fail(EDPC_EINVAL, "unknown precision");
+  return EDPC_OK;
+}
+
+extern "C" uint64_t edpc_param_count(const edpc_cfg* c) {
+  if (check_cfg(c) != EDPC_OK) return 0;
+  return make_offsets(make_dims(*c, 1)).total;
+}
+
+static int current_device_ok() {
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || n == 0) return fail(EDPC_ECUDA, "no CUDA device available");
+  return EDPC_OK;
+}
+
+// ==========================================================================================
+// checksums
+// ==========================================================================================
+namespace {
+
+uint32_t crc32_ieee(const uint8_t* p, size_t n) {
+  static uint32_t table[256];
+  static bool init = false;
+  if (!init) {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t c = i;
+      for (int k = 0; k < 8; ++k) c = (c & 1) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+      table[i] = c;
+    }
+    init = true;
+  }
+  uint32_t c = 0xFFFFFFFFu;
+  for (size_t i = 0; i < n; ++i) c = table[(c ^ p[i]) & 0xFF] ^ (c >> 8);
+  return c ^ 0xFFFFFFFFu;
+}
+
+// Data checksum: XOR over positions i of SplitMix64's finalizer applied to
+// (i << 8) | x_i. Any single changed byte changes it.
+__global__ void checksum_kernel(const uint8_t* __restrict__ x, unsigned long long n, unsigned long long* out) {
+  unsigned long long h = 0;
+  for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned long long z = (i << 8) | x[i];
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    h ^= z ^ (z >> 31);
+  }
+  for (int o = 16; o > 0; o >>= 1) h ^= __shfl_xor_sync(0xffffffffu, h, o);
+  if ((threadIdx.x & 31) == 0 && h) atomicXor(out, h);
+}
+
+int device_checksum(const uint8_t* x, uint64_t n, unsigned long long* scratch, cudaStream_t st, uint64_t* out) {
+  EDPC_CUDA(cudaMemsetAsync(scratch, 0, sizeof(unsigned long long), st));
+  if (n) {
+    int grid = (int)std::min<uint64_t>((n + 255) / 256, 152 * 16);
+    checksum_kernel<<<grid, 256, 0, st>>>(x, n, scratch);
+    EDPC_CUDA(cudaGetLastError());
+  }
+  unsigned long long h = 0;
+  EDPC_CUDA(cudaMemcpyAsync(&h, scratch, sizeof(h), cudaMemcpyDeviceToHost, st));
+  EDPC_CUDA(cudaStreamSynchronize(st));
+  *out = h;
+  return EDPC_OK;
+}
+
+// Copies each stream's bytes into one contiguous buffer.
+__global__ void gather_streams_kernel(const uint8_t* __restrict__ src, const unsigned long long* __restrict__ src_off,
+                                      const uint32_t* __restrict__ len, const unsigned long long* __restrict__ dst_off,
+                                      uint8_t* __restrict__ dst) {
+  const int s = blockIdx.x;
+  const uint8_t* a = src + src_off[s];
+  uint8_t* b = dst + dst_off[s];
+  for (uint32_t i = threadIdx.x; i < len[s]; i += blockDim.x) b[i] = a[i];
+}
+
+// ------------------------------------------------------------------------------------------
+// container header
+// ------------------------------------------------------------------------------------------
+constexpr uint32_t kMagic = 0x43504445u;  // "EDPC" little-endian
+constexpr size_t kFixedHeader = 88;
+
+struct Header {
+  edpc_cfg cfg;
+  uint64_t n = 0;
+  uint32_t b = 0;
+  uint64_t checksum = 0;
+  uint32_t variant = 0;
+  std::vector<uint32_t> len;
+  size_t header_len = 0;
+};
+
+template <class T>
+void put(std::vector<uint8_t>& v, size_t off, T x) {
+  memcpy(v.data() + off, &x, sizeof(T));
+}
+template <class T>
+T get(const uint8_t* p, size_t off) {
+  T x;
+  memcpy(&x, p + off, sizeof(T));
+  return x;
+}
+
+std::vector<uint8_t> write_header(const Header& h) {
+  std::vector<uint8_t> v(kFixedHeader + 4 * (size_t)h.b + 4, 0);
+  put<uint32_t>(v, 0, kMagic);
+  put<uint32_t>(v, 4, EDPC_FORMAT_VERSION);
+  put<uint32_t>(v, 8, (uint32_t)v.size());
+  put<uint32_t>(v, 12, h.cfg.precision);
+  put<uint32_t>(v, 16, h.cfg.context);
+  put<uint32_t>(v, 20, h.cfg.embed_dim);
+  put<uint32_t>(v, 24, h.cfg.latent);
+  put<uint32_t>(v, 28, h.cfg.hidden);
+  put<uint32_t>(v, 32, h.cfg.blocks);
+  put<uint32_t>(v, 36, h.cfg.branches);
+  put<float>(v, 40, h.cfg.lr);
+  put<uint32_t>(v, 44, 0);
+  put<uint64_t>(v, 48, h.cfg.seed);
+  put<uint64_t>(v, 56, h.n);
+  put<uint32_t>(v, 64, h.cfg.streams);
+  put<uint32_t>(v, 68, h.b);
+  put<uint64_t>(v, 72, h.checksum);
+  put<uint32_t>(v, 80, h.variant);
+  put<uint32_t>(v, 84, 0);
+  for (uint32_t s = 0; s < h.b; ++s) put<uint32_t>(v, kFixedHeader + 4 * s, h.len[s]);
+  put<uint32_t>(v, v.size() - 4, crc32_ieee(v.data(), v.size() - 4));
+  return v;
+}
+
+int read_header(const uint8_t* p, size_t n, Header* h) {
+  if (!p) return fail(EDPC_EINVAL, "bitstream is NULL");
+  if (n < kFixedHeader + 4) return fail(EDPC_ECORRUPT, "bitstream shorter than the header");
+  if (get<uint32_t>(p, 0) != kMagic) return fail(EDPC_ECORRUPT, "bad magic");
+  if (get<uint32_t>(p, 4) != EDPC_FORMAT_VERSION) return fail(EDPC_EVERSION, "unsupported format version");
+  size_t hl = get<uint32_t>(p, 8);
+  uint32_t b = get<uint32_t>(p, 68);
+  if (b < 1 || b > 65536 || hl != kFixedHeader + 4 * (size_t)b + 4 || hl > n)
+    return fail(EDPC_ECORRUPT, "bad header length or stream count");
+  if (crc32_ieee(p, hl - 4) != get<uint32_t>(p, hl - 4)) return fail(EDPC_ECORRUPT, "header CRC mismatch");
+  edpc_default_cfg(&h->cfg);
+  h->cfg.precision = get<uint32_t>(p, 12);
+  h->cfg.context = get<uint32_t>(p, 16);
+  h->cfg.embed_dim = get<uint32_t>(p, 20);
+  h->cfg.latent = get<uint32_t>(p, 24);
+  h->cfg.hidden = get<uint32_t>(p, 28);
+  h->cfg.blocks = get<uint32_t>(p, 32);
+  h->cfg.branches = get<uint32_t>(p, 36);
+  h->cfg.lr = get<float>(p, 40);
+  h->cfg.seed = get<uint64_t>(p, 48);
+  h->n = get<uint64_t>(p, 56);
+  h->cfg.streams = get<uint32_t>(p, 64);
+  h->b = b;
+  h->checksum = get<uint64_t>(p, 72);
+  h->variant = get<uint32_t>(p, 80);
+  if (h->variant != 0) return fail(EDPC_EARCH, "unknown GEMM variant in header");
+  int r = check_cfg(&h->cfg);
+  if (r != EDPC_OK) return fail(EDPC_ECORRUPT, "header holds an invalid configuration: " + g_last_error);
+  h->len.resize(b);
+  uint64_t total = 0;
+  for (uint32_t s = 0; s < b; ++s) {
+    h->len[s] = get<uint32_t>(p, kFixedHeader + 4 * (size_t)s);
+    total += h->len[s];
+  }
+  h->header_len = hl;
+  if (hl + total != n) return fail(EDPC_ECORRUPT, "stream lengths do not match the bitstream size");
+  uint32_t be = (uint32_t)std::min<uint64_t>(h->cfg.streams, std::max<uint64_t>(1, h->n / h->cfg.context));
+  if (be != b) return fail(EDPC_ECORRUPT, "stream count does not match the split rule");
+  return EDPC_OK;
+}
+
+Split make_split(uint64_t n, int b) {
+  Split sp;
+  sp.n = (long long)n;
+  sp.q = (long long)(n / (uint64_t)b);
+  sp.rem = (int)(n % (uint64_t)b);
+  return sp;
+}
+
+int effective_streams(const edpc_cfg& c, uint64_t n) {
+  return (int)std::min<uint64_t>(c.streams, std::max<uint64_t>(1, n / c.context));
+}
+
+}  // namespace
+
+// ==========================================================================================
+// sessions
+// ==========================================================================================
+struct edpc_session {
+  bool encoder = true;
+  edpc_cfg cfg{};
+  Model model;
+  Split sp{};
+  int b = 0;
+  uint64_t n = 0;
+  cudaStream_t st = nullptr;
+  bool own_stream = false;
+  cudaStream_t st_coder = nullptr;
+  bool pipeline = true;
+  bool use_graph = true;
+  uint8_t* data = nullptr;
+  bool own_data = false;
+  unsigned long long* scratch = nullptr;
+
+  // encoder
+  uint8_t* out = nullptr;
+  unsigned long long* out_off = nullptr;
+  uint32_t* out_cap = nullptr;
+  uint32_t* out_len = nullptr;
+  EncState* es = nullptr;
+  uint32_t* ring = nullptr;
+  int chunk = 64;
+  int ring_slots = 128;
+  cudaEvent_t ev_model[2] = {}, ev_coder[2] = {}, ev_join = nullptr;
+  uint64_t coded = 0;
+  std::vector<unsigned long long> h_out_off;
+
+  // decoder
+  uint8_t* bits = nullptr;
+  unsigned long long* bits_off = nullptr;
+  uint32_t* bits_len = nullptr;
+  DecState* ds = nullptr;
+  uint64_t checksum_expected = 0;
+
+  uint64_t steps_total = 0, steps_run = 0;
+  bool finished = false;
+
+  // graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int graph_kernels = 0;
+  cudaGraphNode_t ev_nodes[4] = {};
+
+  // FDM kernel timing
+  bool profiling = false;
+  static constexpr int kEvSets = 64;
+  cudaEvent_t tev[kEvSets][4] = {};
+  uint64_t tev_step[kEvSets] = {};
+  bool tev_live[kEvSets] = {};
+  double fwd_ms = 0, bwd_ms = 0;
+  uint64_t samples = 0;
+
+  Model::StepIO io;
+
+  ~edpc_session();
+  int setup_common(const edpc_cfg& c, uint64_t n_, void* stream);
+  int capture_graph();
+  int launch_step();
+  int code_pending();
+  int join();
+  int harvest(int k);
+};
+
+edpc_session::~edpc_session() {
+  if (st) cudaStreamSynchronize(st);
+  if (st_coder) cudaStreamSynchronize(st_coder);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  for (auto& e : ev_model)
+    if (e) cudaEventDestroy(e);
+  for (auto& e : ev_coder)
+    if (e) cudaEventDestroy(e);
+  if (ev_join) cudaEventDestroy(ev_join);
+  for (auto& set : tev)
+    for (auto& e : set)
+      if (e) cudaEventDestroy(e);
+  for (auto& e : model.ev_fdm) e = nullptr;  // owned by the session's tev sets
+  if (own_data && data) cudaFree(data);
+  cudaFree(scratch);
+  cudaFree(out);
+  cudaFree(out_off);
+  cudaFree(out_cap);
+  cudaFree(out_len);
+  cudaFree(es);
+  cudaFree(ring);
+  cudaFree(bits);
+  cudaFree(bits_off);
+  cudaFree(bits_len);
+  cudaFree(ds);
+  if (st_coder) cudaStreamDestroy(st_coder);
+  if (own_stream && st) cudaStreamDestroy(st);
+}
+
+int edpc_session::setup_common(const edpc_cfg& c, uint64_t n_, void* stream) {
+  cfg = c;
+  n = n_;
+  b = effective_streams(c, n);
+  sp = make_split(n, b);
+  pipeline = !(c.flags & EDPC_FLAG_NO_PIPELINE);
+  use_graph = !(c.flags & EDPC_FLAG_NO_GRAPH);
+  if (stream) {
+    st = static_cast<cudaStream_t>(stream);
+  } else {
+    EDPC_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    own_stream = true;
+  }
+  EDPC_CUDA(cudaStreamCreateWithFlags(&st_coder, cudaStreamNonBlocking));
+  for (int k = 0; k < 2; ++k) {
+    EDPC_CUDA(cudaEventCreateWithFlags(&ev_model[k], cudaEventDisableTiming));
+    EDPC_CUDA(cudaEventCreateWithFlags(&ev_coder[k], cudaEventDisableTiming));
+  }
+  EDPC_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+  EDPC_CUDA(cudaMalloc(&scratch, 64));
+  EDPC_TRY(model.init(c, b));
+  long long L = sp.q + (sp.rem ? 1 : 0);
+  steps_total = L > (long long)c.context ? (uint64_t)(L - c.context) : 0;
+  chunk = 64;
+  ring_slots = 2 * chunk;
+  return EDPC_OK;
+}
+
+int edpc_session::capture_graph() {
+  if (!use_graph || steps_total == 0) return EDPC_OK;
+  // Four FDM timing events are recorded in the graph; their nodes are re-pointed
+  // at per-step event sets when profiling (cudaGraphExecEventRecordNodeSetEvent).
+  for (int k = 0; k < 4; ++k) model.ev_fdm[k] = tev[0][k];
+  model.timing = true;
+  EDPC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int r = model.step(io, st);
+  cudaGraph_t g = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(st, &g);
+  model.timing = false;
+  if (r != EDPC_OK) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (ce != cudaSuccess) return fail(EDPC_ECUDA, std::string("stream capture: ") + cudaGetErrorString(ce));
+  graph = g;
+  EDPC_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  size_t nn = 0;
+  EDPC_CUDA(cudaGraphGetNodes(graph, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  EDPC_CUDA(cudaGraphGetNodes(graph, nodes.data(), &nn));
+  graph_kernels = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    EDPC_CUDA(cudaGraphNodeGetType(nd, &t));
+    if (t == cudaGraphNodeTypeKernel) ++graph_kernels;
+    if (t == cudaGraphNodeTypeEventRecord) {
+      cudaEvent_t e;
+      EDPC_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &e));
+      for (int k = 0; k < 4; ++k)
+        if (e == tev[0][k]) ev_nodes[k] = nd;
+    }
+  }
+  return EDPC_OK;
+}
+
+int edpc_session::harvest(int k) {
+  if (!tev_live[k]) return EDPC_OK;
+  EDPC_CUDA(cudaEventSynchronize(tev[k][3]));
+  float a = 0, c = 0;
+  EDPC_CUDA(cudaEventElapsedTime(&a, tev[k][0], tev[k][1]));
+  EDPC_CUDA(cudaEventElapsedTime(&c, tev[k][2], tev[k][3]));
+  fwd_ms += a;
+  bwd_ms += c;
+  ++samples;
+  tev_live[k] = false;
+  return EDPC_OK;
+}
+
+int edpc_session::launch_step() {
+  const uint64_t j = steps_run;
+  if (encoder && pipeline && j % chunk == 0 && j >= (uint64_t)(2 * chunk))
+    EDPC_CUDA(cudaStreamWaitEvent(st, ev_coder[(j / chunk) % 2], 0));
+  int k = (int)(j % kEvSets);
+  if (profiling) {
+    EDPC_TRY(harvest(k));
+    if (exec) {
+      for (int q = 0; q < 4; ++q) EDPC_CUDA(cudaGraphExecEventRecordNodeSetEvent(exec, ev_nodes[q], tev[k][q]));
+    } else {
+      for (int q = 0; q < 4; ++q) model.ev_fdm[q] = tev[k][q];
+      model.timing = true;
+    }
+  }
+  if (exec) {
+    EDPC_CUDA(cudaGraphLaunch(exec, st));
+  } else {
+    int r = model.step(io, st);
+    model.timing = false;
+    if (r != EDPC_OK) return r;
+  }
+  if (profiling) {
+    tev_live[k] = true;
+    tev_step[k] = j;
+  }
+  ++steps_run;
+  if (encoder && steps_run % chunk == 0) EDPC_TRY(code_pending());
+  return EDPC_OK;
+}
+
+// Hands the steps [coded, steps_run) to the coder stage (DPCA): on the
+// coder stream after the model stream's event, or inline when pipelining is off.
+int edpc_session::code_pending() {
+  const uint64_t cnt = steps_run - coded;
+  if (cnt == 0) return EDPC_OK;
+  const int slot0 = (int)(coded % ring_slots);
+  const int par = (int)((coded / chunk) % 2);
+  if (pipeline) {
+    EDPC_CUDA(cudaEventRecord(ev_model[par], st));
+    EDPC_CUDA(cudaStreamWaitEvent(st_coder, ev_model[par], 0));
+    EDPC_CUDA(launch_range_encode(es, ring, ring_slots, slot0, (int)cnt, b, out, out_off, out_cap, st_coder));
+    EDPC_CUDA(cudaEventRecord(ev_coder[par], st_coder));
+  } else {
+    EDPC_CUDA(launch_range_encode(es, ring, ring_slots, slot0, (int)cnt, b, out, out_off, out_cap, st));
+  }
+  coded = steps_run;
+  return EDPC_OK;
+}
+
+int edpc_session::join() {
+  if (encoder && pipeline) {
+    EDPC_CUDA(cudaEventRecord(ev_join, st_coder));
+    EDPC_CUDA(cudaStreamWaitEvent(st, ev_join, 0));
+  }
+  return EDPC_OK;
+}
+
+static int session_prepare_events(edpc_session* s) {
+  for (int k = 0; k < edpc_session::kEvSets; ++k)
+    for (int q = 0; q < 4; ++q) EDPC_CUDA(cudaEventCreate(&s->tev[k][q]));
+  return EDPC_OK;
+}
+
+extern "C" int edpc_encoder_open(const edpc_cfg* cfg, const uint8_t* data, size_t len, int data_on_device,
+                                 void* cuda_stream, edpc_session** out) {
+  if (!out) return fail(EDPC_EINVAL, "out is NULL");
+  *out = nullptr;
+  EDPC_TRY(check_cfg(cfg));
+  if (!data && len) return fail(EDPC_EINVAL, "data is NULL");
+  EDPC_TRY(current_device_ok());
+  edpc_session* s = new (std::nothrow) edpc_session();
+  if (!s) return fail(EDPC_ENOMEM, "host allocation failed");
+  auto bail = [&](int r) {
+    delete s;
+    return r;
+  };
+  s->encoder = true;
+  int r = s->setup_common(*cfg, len, cuda_stream);
+  if (r != EDPC_OK) return bail(r);
+  if ((r = session_prepare_events(s)) != EDPC_OK) return bail(r);
+  cudaStream_t st = s->st;
+  // input bytes on the device
+  if (data_on_device) {
+    s->data = const_cast<uint8_t*>(data);
+  } else {
+    if (cudaMalloc(&s->data, std::max<size_t>(len, 1)) != cudaSuccess) return bail(fail(EDPC_ENOMEM, "input buffer"));
+    s->own_data = true;
+    if (len && cudaMemcpyAsync(s->data, data, len, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return bail(fail(EDPC_ECUDA, "input copy failed"));
+  }
+  // per-stream output buffers: a stream of L bytes codes to at most 2L + L/256 + 64 bytes
+  const int b = s->b;
+  s->h_out_off.resize(b + 1);
+  std::vector<uint32_t> cap(b);
+  unsigned long long tot = 0;
+  for (int i = 0; i < b; ++i) {
+    long long L = s->sp.len(i);
+    cap[i] = (uint32_t)(2 * L + (L >> 8) + 64);
+    s->h_out_off[i] = tot;
+    tot += (cap[i] + 15) & ~15u;
+  }
+  s->h_out_off[b] = tot;
+  if (cudaMalloc(&s->out, tot) != cudaSuccess || cudaMalloc(&s->out_off, 8 * (size_t)b) != cudaSuccess ||
+      cudaMalloc(&s->out_cap, 4 * (size_t)b) != cudaSuccess || cudaMalloc(&s->out_len, 4 * (size_t)b) != cudaSuccess ||
+      cudaMalloc(&s->es, sizeof(EncState) * b) != cudaSuccess ||
+      cudaMalloc(&s->ring, sizeof(uint32_t) * (size_t)b * s->ring_slots) != cudaSuccess)
+    return bail(fail(EDPC_ENOMEM, "encoder buffers"));
+  if (cudaMemcpyAsync(s->out_off, s->h_out_off.data(), 8 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(s->out_cap, cap.data(), 4 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return bail(fail(EDPC_ECUDA, "encoder setup copies"));
+  // Algorithm 1, first line: the first K bytes of each stream with equal probability
+  if (launch_prefix_encode(s->es, s->data, s->sp, (int)cfg->context, b, s->out, s->out_off, s->out_cap, st) !=
+      cudaSuccess)
+    return bail(fail(EDPC_ECUDA, "prefix encode launch"));
+  long long i0 = cfg->context;
+  int bact = (i0 < s->sp.q) ? b : (i0 == s->sp.q ? s->sp.rem : 0);
+  if ((r = s->model.set_ctl_for_step((int)i0, 1, bact, s->ring_slots, st)) != EDPC_OK) return bail(r);
+  s->io.mode = 0;
+  s->io.data = s->data;
+  s->io.sp = s->sp;
+  s->io.ring = s->ring;
+  s->io.ring_slots = s->ring_slots;
+  if ((r = s->capture_graph()) != EDPC_OK) return bail(r);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(EDPC_ECUDA, "encoder open sync"));
+  *out = s;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_session_run(edpc_session* s, uint64_t max_steps, int sync, uint64_t* steps_done) {
+  if (!s) return fail(EDPC_EINVAL, "session is NULL");
+  if (s->finished) return fail(EDPC_EINVAL, "session already finished");
+  uint64_t left = s->steps_total - s->steps_run;
+  uint64_t n = std::min(left, max_steps);
+  for (uint64_t k = 0; k < n; ++k) EDPC_TRY(s->launch_step());
+  EDPC_TRY(s->join());
+  if (sync) EDPC_CUDA(cudaStreamSynchronize(s->st));
+  if (steps_done) *steps_done = n;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_session_remaining(const edpc_session* s, uint64_t* left) {
+  if (!s || !left) return fail(EDPC_EINVAL, "NULL argument");
+  *left = s->steps_total - s->steps_run;
+  return EDPC_OK;
+}
+
+static int check_device_errors(edpc_session* s) {
+  StepCtl c;
+  EDPC_CUDA(cudaMemcpyAsync(&c, s->model.ctl, sizeof(c), cudaMemcpyDeviceToHost, s->st));
+  EDPC_CUDA(cudaStreamSynchronize(s->st));
+  if (c.err & kErrTcTimeout) return fail(EDPC_ETIMEOUT, "a tensor-core GEMM wait expired");
+  if (c.err) return fail(EDPC_ECUDA, "device error flags " + std::to_string(c.err));
+  return EDPC_OK;
+}
+
+extern "C" int edpc_encoder_finish(edpc_session* s, uint8_t** out, size_t* out_len) {
+  if (!s || !out || !out_len) return fail(EDPC_EINVAL, "NULL argument");
+  if (!s->encoder) return fail(EDPC_EINVAL, "not an encoder session");
+  *out = nullptr;
+  *out_len = 0;
+  uint64_t done = 0;
+  EDPC_TRY(edpc_session_run(s, UINT64_MAX, 0, &done));
+  EDPC_TRY(s->code_pending());
+  EDPC_TRY(s->join());
+  const int b = s->b;
+  cudaStream_t st = s->st;
+  EDPC_CUDA(launch_encode_flush(s->es, b, s->out, s->out_off, s->out_cap, s->out_len, st));
+  std::vector<uint32_t> len(b);
+  EDPC_CUDA(cudaMemcpyAsync(len.data(), s->out_len, 4 * (size_t)b, cudaMemcpyDeviceToHost, st));
+  EDPC_CUDA(cudaStreamSynchronize(st));
+  EDPC_TRY(check_device_errors(s));
+  uint64_t total = 0;
+  std::vector<unsigned long long> dst(b);
+  for (int i = 0; i < b; ++i) {
+    if (len[i] == 0xFFFFFFFFu) return fail(EDPC_ECUDA, "coder output buffer overflow");
+    dst[i] = total;
+    total += len[i];
+  }
+  Header h;
+  h.cfg = s->cfg;
+  h.n = s->n;
+  h.b = (uint32_t)b;
+  h.len = len;
+  EDPC_TRY(device_checksum(s->data, s->n, s->scratch, st, &h.checksum));
+  std::vector<uint8_t> hdr = write_header(h);
+  uint8_t* buf = static_cast<uint8_t*>(malloc(hdr.size() + total + 1));
+  if (!buf) return fail(EDPC_ENOMEM, "output buffer");
+  memcpy(buf, hdr.data(), hdr.size());
+  if (total) {
+    uint8_t* packed = nullptr;
+    unsigned long long* dst_dev = nullptr;
+    if (cudaMalloc(&packed, total) != cudaSuccess || cudaMalloc(&dst_dev, 8 * (size_t)b) != cudaSuccess) {
+      cudaFree(packed);
+      free(buf);
+      return fail(EDPC_ENOMEM, "packing buffer");
+    }
+    cudaMemcpyAsync(dst_dev, dst.data(), 8 * (size_t)b, cudaMemcpyHostToDevice, st);
+    gather_streams_kernel<<<b, 256, 0, st>>>(s->out, s->out_off, s->out_len, dst_dev, packed);
+    cudaError_t e = cudaMemcpyAsync(buf + hdr.size(), packed, total, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(packed);
+    cudaFree(dst_dev);
+    if (e != cudaSuccess) {
+      free(buf);
+      return fail(EDPC_ECUDA, std::string("stream gather: ") + cudaGetErrorString(e));
+    }
+  }
+  s->finished = true;
+  *out = buf;
+  *out_len = hdr.size() + total;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_peek(const uint8_t* bits, size_t bits_len, edpc_cfg* cfg, uint64_t* orig_len,
+                         uint32_t* streams_eff) {
+  Header h;
+  EDPC_TRY(read_header(bits, bits_len, &h));
+  if (cfg) *cfg = h.cfg;
+  if (orig_len) *orig_len = h.n;
+  if (streams_eff) *streams_eff = h.b;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_decoder_open(const uint8_t* bits, size_t bits_len, void* out_device, void* cuda_stream,
+                                 edpc_session** out) {
+  if (!out) return fail(EDPC_EINVAL, "out is NULL");
+  *out = nullptr;
+  Header h;
+  EDPC_TRY(read_header(bits, bits_len, &h));
+  EDPC_TRY(current_device_ok());
+  edpc_session* s = new (std::nothrow) edpc_session();
+  if (!s) return fail(EDPC_ENOMEM, "host allocation failed");
+  auto bail = [&](int r) {
+    delete s;
+    return r;
+  };
+  s->encoder = false;
+  int r = s->setup_common(h.cfg, h.n, cuda_stream);
+  if (r != EDPC_OK) return bail(r);
+  if ((r = session_prepare_events(s)) != EDPC_OK) return bail(r);
+  cudaStream_t st = s->st;
+  const int b = s->b;
+  s->checksum_expected = h.checksum;
+  if (out_device) {
+    s->data = static_cast<uint8_t*>(out_device);
+  } else {
+    if (cudaMalloc(&s->data, std::max<uint64_t>(h.n, 1)) != cudaSuccess) return bail(fail(EDPC_ENOMEM, "output"));
+    s->own_data = true;
+  }
+  const size_t payload = bits_len - h.header_len;
+  std::vector<unsigned long long> off(b);
+  unsigned long long o = 0;
+  for (int i = 0; i < b; ++i) {
+    off[i] = o;
+    o += h.len[i];
+  }
+  if (cudaMalloc(&s->bits, std::max<size_t>(payload, 1)) != cudaSuccess ||
+      cudaMalloc(&s->bits_off, 8 * (size_t)b) != cudaSuccess || cudaMalloc(&s->bits_len, 4 * (size_t)b) != cudaSuccess ||
+      cudaMalloc(&s->ds, sizeof(DecState) * b) != cudaSuccess)
+    return bail(fail(EDPC_ENOMEM, "decoder buffers"));
+  if ((payload && cudaMemcpyAsync(s->bits, bits + h.header_len, payload, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+      cudaMemcpyAsync(s->bits_off, off.data(), 8 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(s->bits_len, h.len.data(), 4 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return bail(fail(EDPC_ECUDA, "decoder input copies"));
+  if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(EDPC_ECUDA, "decoder input sync"));
+  if (launch_dec_init(s->ds, s->bits, s->bits_off, s->bits_len, b, st) != cudaSuccess ||
+      launch_prefix_decode(s->ds, s->bits, s->bits_off, s->bits_len, s->sp, (int)h.cfg.context, b, s->data, st) !=
+          cudaSuccess)
+    return bail(fail(EDPC_ECUDA, "decoder prefix launch"));
+  long long i0 = h.cfg.context;
+  int bact = (i0 < s->sp.q) ? b : (i0 == s->sp.q ? s->sp.rem : 0);
+  if ((r = s->model.set_ctl_for_step((int)i0, 1, bact, s->ring_slots, st)) != EDPC_OK) return bail(r);
+  s->io.mode = 1;
+  s->io.data = s->data;
+  s->io.sp = s->sp;
+  s->io.ring_slots = s->ring_slots;
+  s->io.dec = s->ds;
+  s->io.bits = s->bits;
+  s->io.bits_off = s->bits_off;
+  s->io.bits_len = s->bits_len;
+  if ((r = s->capture_graph()) != EDPC_OK) return bail(r);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(EDPC_ECUDA, "decoder open sync"));
+  *out = s;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_decoder_finish(edpc_session* s, uint8_t* out_host) {
+  if (!s) return fail(EDPC_EINVAL, "session is NULL");
+  if (s->encoder) return fail(EDPC_EINVAL, "not a decoder session");
+  uint64_t done = 0;
+  EDPC_TRY(edpc_session_run(s, UINT64_MAX, 1, &done));
+  EDPC_TRY(check_device_errors(s));
+  uint64_t h = 0;
+  EDPC_TRY(device_checksum(s->data, s->n, s->scratch, s->st, &h));
+  if (h != s->checksum_expected) return fail(EDPC_ECORRUPT, "checksum of the decoded data does not match");
+  if (out_host && s->n) {
+    EDPC_CUDA(cudaMemcpyAsync(out_host, s->data, s->n, cudaMemcpyDeviceToHost, s->st));
+    EDPC_CUDA(cudaStreamSynchronize(s->st));
+  }
+  s->finished = true;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_session_stats(const edpc_session* s, edpc_stats* o) {
+  if (!s || !o) return fail(EDPC_EINVAL, "NULL argument");
+  memset(o, 0, sizeof(*o));
+  o->steps_run = s->steps_run;
+  o->steps_total = s->steps_total;
+  o->streams = (uint32_t)s->b;
+  o->launches_per_step = (uint32_t)(s->graph_kernels ? s->graph_kernels : s->model.launches_per_step());
+  o->fdm_samples = s->samples;
+  o->fdm_fwd_ms = s->samples ? s->fwd_ms / s->samples : 0;
+  o->fdm_bwd_ms = s->samples ? s->bwd_ms / s->samples : 0;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_session_profile(edpc_session* s, int on) {
+  if (!s) return fail(EDPC_EINVAL, "session is NULL");
+  if (!on && s->profiling) {
+    for (int k = 0; k < edpc_session::kEvSets; ++k) EDPC_TRY(s->harvest(k));
+  }
+  if (on && !s->profiling) {
+    s->fwd_ms = s->bwd_ms = 0;
+    s->samples = 0;
+  }
+  s->profiling = on != 0;
+  return EDPC_OK;
+}
+
+extern "C" void edpc_session_close(edpc_session* s) { delete s; }
+
+extern "C" int edpc_compress(const uint8_t* buf, size_t len, const edpc_cfg* cfg, uint8_t** out, size_t* out_len) {
+  if (!out || !out_len) return fail(EDPC_EINVAL, "NULL output pointer");
+  edpc_session* s = nullptr;
+  EDPC_TRY(edpc_encoder_open(cfg, buf, len, 0, nullptr, &s));
+  int r = edpc_encoder_finish(s, out, out_len);
+  edpc_session_close(s);
+  return r;
+}
+
+extern "C" int edpc_decompress(const uint8_t* bits, size_t bits_len, uint8_t** out, size_t* out_len) {
+  if (!out || !out_len) return fail(EDPC_EINVAL, "NULL output pointer");
+  *out = nullptr;
+  *out_len = 0;
+  uint64_t n = 0;
+  EDPC_TRY(edpc_peek(bits, bits_len, nullptr, &n, nullptr));
+  uint8_t* buf = static_cast<uint8_t*>(malloc(std::max<uint64_t>(n, 1)));
+  if (!buf) return fail(EDPC_ENOMEM, "output buffer");
+  edpc_session* s = nullptr;
+  int r = edpc_decoder_open(bits, bits_len, nullptr, nullptr, &s);
+  if (r == EDPC_OK) r = edpc_decoder_finish(s, buf);
+  edpc_session_close(s);
+  if (r != EDPC_OK) {
+    free(buf);
+    return r;
+  }
+  *out = buf;
+  *out_len = n;
+  return EDPC_OK;
+}
+
+// ==========================================================================================
+// single-kernel entry points
+// ==========================================================================================
+extern "C" int edpc_cdf_quantize(const float* p, uint32_t rows, uint32_t* freq, uint32_t* cum, void* stream) {
+  if ((!p || !freq || !cum) && rows) return fail(EDPC_EINVAL, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  EDPC_CUDA(launch_cdf_quantize(p, (int)rows, freq, cum, st));
+  EDPC_CUDA(cudaStreamSynchronize(st));
+  return EDPC_OK;
+}
+
+extern "C" int edpc_range_encode(const uint32_t* sym, uint32_t nsym, uint32_t streams, uint8_t* out, uint32_t cap,
+                                 uint32_t* out_len, void* stream) {
+  if (!sym || !out || !out_len || streams == 0) return fail(EDPC_EINVAL, "NULL argument or no streams");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  EncState* es = nullptr;
+  unsigned long long* off = nullptr;
+  uint32_t* caps = nullptr;
+  std::vector<unsigned long long> h_off(streams);
+  std::vector<uint32_t> h_cap(streams, cap);
+  for (uint32_t s = 0; s < streams; ++s) h_off[s] = (unsigned long long)s * cap;
+  int r = EDPC_OK;
+  if (cudaMalloc(&es, sizeof(EncState) * streams) != cudaSuccess || cudaMalloc(&off, 8 * (size_t)streams) != cudaSuccess ||
+      cudaMalloc(&caps, 4 * (size_t)streams) != cudaSuccess) {
+    r = fail(EDPC_ENOMEM, "coder state");
+  } else {
+    cudaMemcpyAsync(off, h_off.data(), 8 * (size_t)streams, cudaMemcpyHostToDevice, st);
+    cudaMemcpyAsync(caps, h_cap.data(), 4 * (size_t)streams, cudaMemcpyHostToDevice, st);
+    Split none{0, 0, 0};
+    cudaError_t e = launch_prefix_encode(es, nullptr, none, 0, (int)streams, out, off, caps, st);
+    if (e == cudaSuccess) e = launch_range_encode(es, sym, (int)nsym, 0, (int)nsym, (int)streams, out, off, caps, st);
+    if (e == cudaSuccess) e = launch_encode_flush(es, (int)streams, out, off, caps, out_len, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) r = fail(EDPC_ECUDA, std::string("range encode: ") + cudaGetErrorString(e));
+    if (r == EDPC_OK) {
+      std::vector<uint32_t> l(streams);
+      cudaMemcpy(l.data(), out_len, 4 * (size_t)streams, cudaMemcpyDeviceToHost);
+      bool over = false;
+      for (auto& v : l)
+        if (v == 0xFFFFFFFFu) {
+          v = cap;
+          over = true;
+        }
+      if (over) {
+        cudaMemcpy(out_len, l.data(), 4 * (size_t)streams, cudaMemcpyHostToDevice);
+        r = fail(EDPC_EINVAL, "a stream needs more than cap bytes");
+      }
+    }
+  }
+  cudaFree(es);
+  cudaFree(off);
+  cudaFree(caps);
+  return r;
+}
+
+// ==========================================================================================
+// model API
+// ==========================================================================================
+struct edpc_model {
+  Model m;
+  edpc_cfg cfg{};
+  uint8_t* tgt = nullptr;
+  uint8_t* act = nullptr;
+  uint32_t t = 0;
+  ~edpc_model() {
+    cudaFree(tgt);
+    cudaFree(act);
+  }
+};
+
+extern "C" int edpc_model_create(const edpc_cfg* cfg, uint32_t streams, edpc_model** out) {
+  if (!out) return fail(EDPC_EINVAL, "out is NULL");
+  *out = nullptr;
+  EDPC_TRY(check_cfg(cfg));
+  if (streams < 1 || streams > 65536) return fail(EDPC_EINVAL, "streams must be in [1, 65536]");
+  EDPC_TRY(current_device_ok());
+  edpc_model* m = new (std::nothrow) edpc_model();
+  if (!m) return fail(EDPC_ENOMEM, "host allocation failed");
+  m->cfg = *cfg;
+  int r = m->m.init(*cfg, (int)streams);
+  if (r == EDPC_OK && (cudaMalloc(&m->tgt, streams) != cudaSuccess || cudaMalloc(&m->act, streams) != cudaSuccess))
+    r = fail(EDPC_ENOMEM, "model buffers");
+  if (r != EDPC_OK) {
+    delete m;
+    return r;
+  }
+  *out = m;
+  return EDPC_OK;
+}
+
+extern "C" void edpc_model_destroy(edpc_model* m) { delete m; }
+
+extern "C" int edpc_model_get_state(const edpc_model* mm, float* shared, float* fdm, float* m_shared, float* v_shared,
+                                    float* m_fdm, float* v_fdm, uint32_t* t) {
+  if (!mm) return fail(EDPC_EINVAL, "model is NULL");
+  const Model& m = mm->m;
+  const size_t np = m.nparam * 4, nf = (size_t)m.d.b * m.d.Fp * m.d.Fp * 4;
+  EDPC_CUDA(cudaDeviceSynchronize());
+  if (shared) EDPC_CUDA(cudaMemcpy(shared, m.P, np, cudaMemcpyDeviceToHost));
+  if (m_shared) EDPC_CUDA(cudaMemcpy(m_shared, m.M, np, cudaMemcpyDeviceToHost));
+  if (v_shared) EDPC_CUDA(cudaMemcpy(v_shared, m.V, np, cudaMemcpyDeviceToHost));
+  if (fdm) EDPC_CUDA(cudaMemcpy(fdm, m.U, nf, cudaMemcpyDeviceToHost));
+  if (m_fdm) EDPC_CUDA(cudaMemcpy(m_fdm, m.Um, nf, cudaMemcpyDeviceToHost));
+  if (v_fdm) EDPC_CUDA(cudaMemcpy(v_fdm, m.Uv, nf, cudaMemcpyDeviceToHost));
+  if (t) *t = mm->t;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_model_set_state(edpc_model* mm, const float* shared, const float* fdm, const float* m_shared,
+                                    const float* v_shared, const float* m_fdm, const float* v_fdm, uint32_t t) {
+  if (!mm) return fail(EDPC_EINVAL, "model is NULL");
+  Model& m = mm->m;
+  const size_t np = m.nparam * 4, nf = (size_t)m.d.b * m.d.Fp * m.d.Fp * 4;
+  if (shared) EDPC_CUDA(cudaMemcpy(m.P, shared, np, cudaMemcpyHostToDevice));
+  if (m_shared) EDPC_CUDA(cudaMemcpy(m.M, m_shared, np, cudaMemcpyHostToDevice));
+  if (v_shared) EDPC_CUDA(cudaMemcpy(m.V, v_shared, np, cudaMemcpyHostToDevice));
+  if (fdm) EDPC_CUDA(cudaMemcpy(m.U, fdm, nf, cudaMemcpyHostToDevice));
+  if (m_fdm) EDPC_CUDA(cudaMemcpy(m.Um, m_fdm, nf, cudaMemcpyHostToDevice));
+  if (v_fdm) EDPC_CUDA(cudaMemcpy(m.Uv, v_fdm, nf, cudaMemcpyHostToDevice));
+  mm->t = t;
+  if (shared && m.precision == EDPC_BF16) {
+    EDPC_TRY(m.refresh_bf16_weights(0));
+    EDPC_CUDA(cudaDeviceSynchronize());
+  }
+  return EDPC_OK;
+}
+
+static int model_prepare(edpc_model* mm, const uint8_t* ctx, const uint8_t* targets, const uint8_t* active,
+                         uint32_t t, Model::StepIO* io) {
+  Model& m = mm->m;
+  const int b = m.d.b;
+  std::vector<uint8_t> zeros(b, 0);
+  EDPC_CUDA(cudaMemcpy(m.ctx, ctx, (size_t)b * m.d.K, cudaMemcpyHostToDevice));
+  EDPC_CUDA(cudaMemcpy(mm->tgt, targets ? targets : zeros.data(), b, cudaMemcpyHostToDevice));
+  EDPC_CUDA(cudaMemcpy(mm->act, active ? active : zeros.data(), b, cudaMemcpyHostToDevice));
+  int bact = 0;
+  if (active)
+    for (int i = 0; i < b; ++i) bact += active[i] != 0;
+  EDPC_TRY(m.set_ctl_for_step(0, (int)t, bact, 1, 0));
+  io->mode = 2;
+  io->targets = mm->tgt;
+  io->active = mm->act;
+  io->advance = false;
+  io->ring_slots = 1;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_model_forward(edpc_model* mm, const uint8_t* ctx, float* logits, float* probs) {
+  if (!mm || !ctx) return fail(EDPC_EINVAL, "NULL argument");
+  Model::StepIO io;
+  EDPC_TRY(model_prepare(mm, ctx, nullptr, nullptr, mm->t + 1, &io));
+  Model& m = mm->m;
+  EDPC_TRY(m.forward(io, 0));
+  EDPC_TRY(m.head(io, 0));
+  EDPC_CUDA(cudaDeviceSynchronize());
+  const size_t nb = (size_t)m.d.b * 256 * 4;
+  if (logits) EDPC_CUDA(cudaMemcpy(logits, m.z, nb, cudaMemcpyDeviceToHost));
+  if (probs) EDPC_CUDA(cudaMemcpy(probs, m.p, nb, cudaMemcpyDeviceToHost));
+  return EDPC_OK;
+}
+
+extern "C" int edpc_model_backward(edpc_model* mm, const uint8_t* ctx, const uint8_t* targets, const uint8_t* active,
+                                   float* g_shared, float* g_fdm) {
+  if (!mm || !ctx || !targets || !active) return fail(EDPC_EINVAL, "NULL argument");
+  Model& m = mm->m;
+  if (!m.gU) {
+    size_t nf = (size_t)m.d.b * m.d.Fp * m.d.Fp * 4;
+    if (cudaMalloc(&m.gU, nf) != cudaSuccess) return fail(EDPC_ENOMEM, "FDM gradient buffer");
+  }
+  Model::StepIO io;
+  EDPC_TRY(model_prepare(mm, ctx, targets, active, mm->t + 1, &io));
+  io.update = 0;
+  EDPC_TRY(m.forward(io, 0));
+  EDPC_TRY(m.head(io, 0));
+  EDPC_TRY(m.backward(io, 0));
+  EDPC_CUDA(cudaDeviceSynchronize());
+  if (g_shared) EDPC_CUDA(cudaMemcpy(g_shared, m.G, m.nparam * 4, cudaMemcpyDeviceToHost));
+  if (g_fdm) EDPC_CUDA(cudaMemcpy(g_fdm, m.gU, (size_t)m.d.b * m.d.Fp * m.d.Fp * 4, cudaMemcpyDeviceToHost));
+  return EDPC_OK;
+}
+
+extern "C" int edpc_model_train_step(edpc_model* mm, const uint8_t* ctx, const uint8_t* targets, const uint8_t* active) {
+  if (!mm || !ctx || !targets || !active) return fail(EDPC_EINVAL, "NULL argument");
+  Model& m = mm->m;
+  Model::StepIO io;
+  EDPC_TRY(model_prepare(mm, ctx, targets, active, mm->t + 1, &io));
+  io.update = 1;
+  EDPC_TRY(m.step(io, 0));
+  EDPC_CUDA(cudaDeviceSynchronize());
+  mm->t += 1;
+  return EDPC_OK;
+}

@@ -1,0 +1,111 @@
+// Shared definitions of the EDPC CUDA library (device and host).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/edpc.h"
+
+namespace edpc {
+
+constexpr int kT = 1 << 16;          // CDF total (quantized probabilities sum to 2^16)
+constexpr int kTBits = 16;
+constexpr uint32_t kTop = 1u << 24;  // range coder renormalisation threshold
+constexpr uint32_t kSkip = 0xFFFFFFFFu;
+constexpr int kMaxBlocks = 16;
+constexpr float kLnEps = 1e-5f;
+constexpr float kB1 = 0.9f, kB2 = 0.999f, kAdamEps = 1e-8f;
+constexpr int kFdmTid = 1023;        // tensor id of the FDM in the initial-value rule
+
+// Error bits written by kernels into StepCtl::err.
+constexpr int kErrCoderOverflow = 1;
+constexpr int kErrDecodeOverrun = 2;
+
+// Model dimensions of one session (derived from edpc_cfg).
+struct Dims {
+  int b;      // rows = streams
+  int K, D, F;
+  int Fp, H, n, nloc, k;
+  int ldT;    // leading dimension of transposed [feature][row] operands (b rounded up to 8)
+};
+
+// Offsets (in floats) of each shared tensor inside the flat parameter buffer.
+// Order: E, blocks 0..n-1 (ln_g, ln_b, W, c, Wo, co), LTE (W1, b1, W2, b2), head (Wh, bh).
+struct BlockOff {
+  size_t ln_g, ln_b, W, c, Wo, co;
+};
+struct ParamOff {
+  size_t E;
+  BlockOff blk[kMaxBlocks];
+  size_t W1, b1, W2, b2, Wh, bh;
+  size_t total;
+};
+
+// Per-step scalars, read by every kernel of a step from device memory so the
+// step's launches are identical from step to step (CUDA-graph friendly).
+struct StepCtl {
+  int i;          // time index of the current step (0-based position in each stream)
+  int t;          // Adam step number of the current step (1-based)
+  int bact;       // streams active at this step
+  int slot;       // coder ring slot of this step
+  float inv_bact; // 1 / bact
+  float bc1;      // 1 - beta1^t
+  float bc2;      // 1 - beta2^t
+  float lr;
+  int err;        // sticky error bits
+  int pad[7];
+};
+
+// Balanced split of n bytes into b streams: q or q+1 bytes each.
+struct Split {
+  long long n;
+  long long q;
+  int rem;
+  __host__ __device__ long long off(int s) const { return (long long)s * q + (s < rem ? s : rem); }
+  __host__ __device__ long long len(int s) const { return q + (s < rem ? 1 : 0); }
+};
+
+// Range coder states (one per stream), kept in device memory between launches.
+struct EncState {
+  unsigned long long low;
+  uint32_t range;
+  uint32_t cache;
+  uint32_t pending;
+  uint32_t started;
+  uint32_t pos;
+  uint32_t err;
+};
+struct DecState {
+  uint32_t code;
+  uint32_t range;
+  uint32_t pos;
+  uint32_t err;
+};
+
+Dims make_dims(const edpc_cfg& c, int b);
+ParamOff make_offsets(const Dims& d);
+
+// ---- error plumbing (host) ----------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define EDPC_CUDA(call)                                                                \
+  do {                                                                                 \
+    cudaError_t e__ = (call);                                                          \
+    if (e__ != cudaSuccess)                                                            \
+      return ::edpc::fail(EDPC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+  } while (0)
+
+#define EDPC_TRY(expr)             \
+  do {                             \
+    int r__ = (expr);              \
+    if (r__ != EDPC_OK) return r__; \
+  } while (0)
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+inline long long round_up(long long a, long long b) { return (a + b - 1) / b * b; }
+
+}  // namespace edpc

@@ -1,0 +1,126 @@
+// Kernel launchers of the EDPC library. Every launcher is asynchronous on
+// `st` and returns the launch status.
+#pragma once
+
+#include "common.cuh"
+
+namespace edpc {
+
+// ---- initial values -------------------------------------------------------------------
+// dst[j] = value (start + j) of tensor `tid` (SplitMix64 counter rule), or `fill`
+// when bound < 0.
+cudaError_t launch_init_values(float* dst, size_t n, uint64_t seed, int tid, float bound,
+                               size_t start, float fill, cudaStream_t st);
+
+// ---- forward ------------------------------------------------------------------------------
+// X[s][k*D + d] = E[ctx(s,k)][d]. With data != nullptr the context is gathered
+// from the stream bytes at the step's position and also written to ctx;
+// otherwise ctx (b x K) is read.
+cudaError_t launch_embed(const uint8_t* data, Split sp, const StepCtl* ctl, const float* E, int b,
+                         int K, int D, float* X, uint8_t* ctx, cudaStream_t st);
+// Row-wise LayerNorm: xhat, rstd, X0 = g * xhat + beta.
+cudaError_t launch_ln_fwd(const float* X, const float* g, const float* be, float* xhat, float* rstd,
+                          float* X0, int b, int F, cudaStream_t st);
+// G = GELU(prod_i A[:, iH:(i+1)H]).
+cudaError_t launch_branch_gelu(const float* A, int b, int H, int k, float* G, cudaStream_t st);
+// Per-stream FDM product y_s = x'_s U_s.
+cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int Fp, cudaStream_t st);
+
+// Softmax, CDF quantization, coding and the CE gradient of one step.
+struct HeadArgs {
+  const float* z;            // b x 256 logits
+  int b;
+  const StepCtl* ctl;
+  Split sp;
+  int mode;                  // 0 encode, 1 decode, 2 model API (targets/active given)
+  uint8_t* data;             // stream bytes (read at encode, written at decode)
+  const uint8_t* targets;    // mode 2
+  const uint8_t* active;     // mode 2
+  float* p;                  // b x 256 out (may be null)
+  float* dz;                 // b x 256 out
+  uint32_t* ring;            // mode 0: ring[slot*b + s] = cum | (f-1) << 16 or kSkip
+  DecState* dec;             // mode 1
+  const uint8_t* bits;       // mode 1: concatenated substreams
+  const unsigned long long* bits_off;
+  const uint32_t* bits_len;
+  uint32_t* freq_out;        // optional b x 256
+  uint32_t* cum_out;         // optional b x 257
+  int* err;
+};
+cudaError_t launch_head(const HeadArgs& a, cudaStream_t st);
+
+// ---- backward -----------------------------------------------------------------------------
+cudaError_t launch_branch_gelu_bwd(const float* dG, const float* A, int b, int H, int k, float* dA,
+                                   cudaStream_t st);
+// out[c] = sum_r X[r][c] (or sum_r X[r][c] * Y[r][c] when Y != nullptr), fixed order.
+cudaError_t launch_colsum(const float* X, const float* Y, int rows, int cols, int ld, float* out,
+                          cudaStream_t st);
+// dX = dRes + LN backward of dX0.
+cudaError_t launch_ln_bwd(const float* dX0, const float* xhat, const float* rstd, const float* g,
+                          const float* dRes, float* dX, int b, int F, cudaStream_t st);
+// FDM adjoint: dx'_s = U_s dy_s with the pre-update U, then (update=1) Adam on
+// U_s, m, v with the rank-1 gradient x'_s dy_s^T; inactive streams are skipped.
+// With update=0 the gradient is written to gU instead (no state change).
+struct FdmBwdArgs {
+  const float* Xp;
+  const float* dY;
+  float* U;
+  float* Um;
+  float* Uv;
+  float* dXp;
+  float* gU;
+  const StepCtl* ctl;
+  Split sp;
+  const uint8_t* active;     // optional mask; else active = (ctl->i < len_s)
+  int b, Fp;
+  int update;
+};
+cudaError_t launch_fdm_bwd(const FdmBwdArgs& a, cudaStream_t st);
+// dE[c][d] = sum over positions with ctx == c of dX[s][k*D + d], fixed order.
+cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE,
+                             cudaStream_t st);
+// Adam over the flat shared parameters; bf16 != nullptr also refreshes the BF16 copy.
+cudaError_t launch_adam(float* P, const float* G, float* M, float* V, size_t n, const StepCtl* ctl,
+                        cudaStream_t st);
+// i += 1 and the derived per-step scalars.
+cudaError_t launch_step_advance(StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st);
+
+// ---- coder --------------------------------------------------------------------------------
+cudaError_t launch_prefix_encode(EncState* es, const uint8_t* data, Split sp, int K, int b,
+                                 uint8_t* out, const unsigned long long* out_off,
+                                 const uint32_t* out_cap, cudaStream_t st);
+cudaError_t launch_range_encode(EncState* es, const uint32_t* ring, int ring_slots, int slot0,
+                                int nsteps, int b, uint8_t* out, const unsigned long long* out_off,
+                                const uint32_t* out_cap, cudaStream_t st);
+cudaError_t launch_encode_flush(EncState* es, int b, uint8_t* out, const unsigned long long* out_off,
+                                const uint32_t* out_cap, uint32_t* out_len, cudaStream_t st);
+cudaError_t launch_dec_init(DecState* ds, const uint8_t* bits, const unsigned long long* off,
+                            const uint32_t* len, int b, cudaStream_t st);
+cudaError_t launch_prefix_decode(DecState* ds, const uint8_t* bits, const unsigned long long* off,
+                                 const uint32_t* len, Split sp, int K, int b, uint8_t* data,
+                                 cudaStream_t st);
+// Standalone quantizer (one warp per row).
+cudaError_t launch_cdf_quantize(const float* p, int rows, uint32_t* freq, uint32_t* cum,
+                                cudaStream_t st);
+
+// ---- GEMM (FP32 SIMT) ------------------------------------------------------------------------
+// C[m][n] = sum_k A(m,k) B(n,k) (+ bias[n]) (+ R[m][n]).
+// A(m,k) = a_kcont ? A[m*lda + k] : A[k*lda + m];  B(n,k) = b_kcont ? B[n*ldb + k] : B[k*ldb + n].
+enum Epi { EPI_STORE = 0, EPI_BIAS = 1, EPI_BIAS_RESID = 2 };
+struct GemmF32 {
+  int M, N, K;
+  const float* A; int lda; bool a_kcont;
+  const float* B; int ldb; bool b_kcont;
+  float* C; int ldc;
+  int epi;
+  const float* bias;
+  const float* R; int ldr;
+};
+cudaError_t launch_gemm_f32(const GemmF32& g, cudaStream_t st);
+
+// ---- BF16 operands ------------------------------------------------------------------------------
+// Y[r][c] = bf16(X[r][c]) (ld ldy) and/or YT[c][r] = bf16(X[r][c]) (ld ldt).
+cudaError_t launch_to_bf16(const float* X, int rows, int cols, int ldx, __nv_bfloat16* Y, int ldy,
+                           __nv_bfloat16* YT, int ldt, cudaStream_t st);
+
+}  // namespace edpc
