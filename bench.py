@@ -1,0 +1,426 @@
+"""Benchmark: EDPC compress / decompress throughput on the 64 MiB multimedia mix.
+
+Workload: 64 MiB of seeded synthetic multimedia-like bytes (8-bit images,
+16-bit PCM, order-3 Markov text in equal thirds), split into 512 streams;
+model K = 32, D = 16, F' = 256, 4 MBRBs of hidden 256; BF16 GEMMs with FP32
+accumulation (the plain FP32 path is timed beside it).
+
+A bench step is one coder chunk: 64 model steps of all 512 streams, i.e.
+64 x 512 = 32 KiB of input through every stage of the hot path (embedding,
+MBRBs, LTE/FDM, head, CDF, range coding on the coder stream, adjoint, Adam).
+W warm-up steps run first; then exactly K steps are timed with CUDA events on
+the launching stream, bracketed by a barrier and a device synchronize.
+
+value     compress MB/s (1e6 input bytes / s) with the input resident in HBM.
+e2e       the same metric through edpc_compress on a host (pinned) buffer:
+          host->device input copy, every step, flush, device->host container.
+          Timed on the first P bytes of each stream (P = K + (W + K + 2) * 64).
+Also      decompress MB/s (device-resident, same prefix input, lossless check),
+          FP32 compress MB/s, bits/byte, the FDM kernels' roofline, clocks.
+
+`--impl reference` times the CPU oracle (FP64 NumPy) on the same workload:
+each step is one model step of all 512 streams.
+
+With N GPUs (torchrun), each rank compresses its own replica (a different
+seed); the value is the total bytes of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(total_bytes=64 << 20, streams=512, context=32, embed_dim=16, latent=256, hidden=256, blocks=4,
+                branches=2, lr=1e-3, seed=1, data_seed=20250719)
+CHUNK = 64
+METRIC = "compress MB/s (BF16 batched; decompress and plain FP32 reported beside it)"
+FDM_PROFILE = os.path.join(ROOT, "profiles", "fdm_bwd_adam_c1.md")
+KERNEL_SRC = os.path.join(ROOT, "paper_2507_18969_gb300", "csrc", "kernels.cu")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="skip the FP32, decompress, e2e and CPU legs")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=0, help="oracle model steps for cpu_baseline (0 = auto)")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; replicas)
+# --------------------------------------------------------------------------------------------
+class Dist:
+    def __init__(self, n_gpus: int, backend: str | None = None):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            be = backend or ("nccl" if _cuda() else "gloo")
+            dist.init_process_group(be, rank=self.rank, world_size=self.world)
+            self.pg = dist
+            self.backend = be
+
+    def barrier(self):
+        if self.pg:
+            if getattr(self, "backend", "") == "nccl":
+                import torch
+                self.pg.barrier(device_ids=[self.local])
+                torch.cuda.synchronize()
+            else:
+                self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if getattr(self, "backend", "") == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        dev = "cuda" if getattr(self, "backend", "") == "nccl" else "cpu"
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+def _cuda() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def aggregate(bytes_per_rank: float, seconds: float, d: Dist) -> tuple[float, float]:
+    """Whole-job throughput: all ranks' bytes over the slowest rank's time (MB/s, s)."""
+    t = d.max(seconds)
+    total = d.sum(bytes_per_rank)
+    return total / t / 1e6, t
+
+
+# --------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# --------------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------------
+# helpers
+# --------------------------------------------------------------------------------------------
+def workload_input(rank: int) -> np.ndarray:
+    import synth
+    return synth.multimedia_mix(WORKLOAD["total_bytes"], WORKLOAD["data_seed"] + rank)
+
+
+def prefix_input(x: np.ndarray, per_stream: int) -> np.ndarray:
+    """The first `per_stream` bytes of each of the workload's streams, concatenated."""
+    b = WORKLOAD["streams"]
+    q = x.size // b
+    return np.ascontiguousarray(x[: q * b].reshape(b, q)[:, :per_stream]).reshape(-1)
+
+
+def make_cfg(prec):
+    import paper_2507_18969_gb300 as edpc
+    w = WORKLOAD
+    return edpc.make_cfg(streams=w["streams"], context=w["context"], embed_dim=w["embed_dim"], latent=w["latent"],
+                         hidden=w["hidden"], blocks=w["blocks"], branches=w["branches"], lr=w["lr"],
+                         precision=prec, seed=w["seed"])
+
+
+def fdm_traffic_from_profile():
+    """Per-launch DRAM bytes of the FDM adjoint+Adam kernel from the committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        txt = open(FDM_PROFILE).read()
+        want = re.search(r"kernels_cu_sha256:\s*([0-9a-f]{64})", txt).group(1)
+        have = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+        if want != have:
+            return None
+        return float(re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt).group(1))
+    except Exception:
+        return None
+
+
+def timed_session(sess, warmup_chunks, steps_chunks, stream, d: Dist, clocks=None, profile=False):
+    import torch
+    sess.run(warmup_chunks * CHUNK, sync=True)
+    if profile:
+        sess.profile(True)
+    d.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    done = sess.run(steps_chunks * CHUNK, sync=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    d.barrier()
+    ck = clocks.stop() if clocks else None
+    if profile:
+        sess.profile(False)
+    return e0.elapsed_time(e1) / 1e3, done, ck
+
+
+# --------------------------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and --impl reference)
+# --------------------------------------------------------------------------------------------
+def oracle_model(x: np.ndarray, n_steps: int):
+    """The oracle's configuration, a freshly initialised model and the prefix input."""
+    from oracle.model import Config, Model
+    w = WORKLOAD
+    cfg = Config(context=w["context"], embed_dim=w["embed_dim"], latent=w["latent"], hidden=w["hidden"],
+                 blocks=w["blocks"], branches=w["branches"], lr=w["lr"], seed=w["seed"])
+    xp = prefix_input(x, w["context"] + n_steps)
+    return cfg, Model(cfg, w["streams"]), xp
+
+
+def oracle_steps(cfg, model, xp, n_steps: int) -> float:
+    """Seconds the FP64 oracle takes for n_steps model steps of all 512 streams
+    (its own Algorithm 1 loop, coding included), with the model built beforehand."""
+    from oracle.compress import oracle_compress
+    t0 = time.perf_counter()
+    oracle_compress(xp, cfg, WORKLOAD["streams"], max_steps=n_steps, model=model)
+    return time.perf_counter() - t0
+
+
+def cpu_cores() -> int:
+    for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        if os.environ.get(k):
+            return int(os.environ[k])
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    """The CPU oracle on this arm's workload; under torchrun only rank 0 works."""
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    x = workload_input(0)
+    steps = args.steps
+    cfg, model, xp = oracle_model(x, 1)
+    times = []
+    for k in range(args.warmup + steps):
+        t = oracle_steps(cfg, model, xp, 1)
+        if k >= args.warmup:
+            times.append(t)
+    tot = sum(times)
+    value = WORKLOAD["streams"] * steps / tot / 1e6
+    sample = ("per bench step, one model step of all 512 streams of the 64 MiB workload (512 input bytes), "
+              "FP64 NumPy oracle with its uniform-prefix coding")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MB/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": tot / steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "multimedia mix 64 MiB (images/PCM/text thirds), 512 streams",
+                   "model": "K=32 D=16 F=512 F'=256 4xMBRB(H=256, 2 branches)", "global_batch": 512,
+                   "step": "one model step of all 512 streams"},
+        "cpu_baseline": {"value": value, "unit": "MB/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "MB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------------------------
+def run_ours(args, d: Dist):
+    import torch
+    import paper_2507_18969_gb300 as edpc
+
+    torch.cuda.set_device(d.local)
+    edpc.load()
+    x = workload_input(d.rank)
+    stream = torch.cuda.current_stream()
+    W, K = args.warmup, args.steps
+    out = {}
+
+    # ---- compress, BF16, input resident in HBM ------------------------------------------
+    xd = torch.from_numpy(x).cuda()
+    clocks = Clocks(d.local)
+    enc = edpc.Encoder(make_cfg(edpc.EDPC_BF16), device_ptr=xd.data_ptr(), length=x.size, stream=stream.cuda_stream)
+    t, done, ck = timed_session(enc, W, K, stream, d, clocks=clocks, profile=True)
+    st = enc.stats()
+    enc.close()
+    b = WORKLOAD["streams"]
+    bytes_rank = done * b
+    value, t_max = aggregate(bytes_rank, t, d)
+    launches = (st.launches_per_step * done + done // CHUNK) if st.launches_per_step else None
+    out.update(value=value, t=t_max, done=done, clocks=ck, stats=st, launches=launches)
+
+    fp32_value = decomp_value = e2e = bpb = None
+    if not args.quick:
+        # ---- plain FP32 path, same workload ----------------------------------------------
+        enc = edpc.Encoder(make_cfg(edpc.EDPC_FP32), device_ptr=xd.data_ptr(), length=x.size,
+                           stream=stream.cuda_stream)
+        t32, done32, _ = timed_session(enc, W, K, stream, d)
+        enc.close()
+        fp32_value, _ = aggregate(done32 * b, t32, d)
+
+        # ---- e2e through edpc_compress on pinned host memory (prefix input) --------------
+        per = WORKLOAD["context"] + (W + K + 2) * CHUNK
+        xp = prefix_input(x, per)
+        host = torch.from_numpy(xp).pin_memory()
+        cfg = make_cfg(edpc.EDPC_BF16)
+        import ctypes as C
+        lib = edpc.load()
+        outp = C.c_void_p()
+        outn = C.c_size_t()
+        d.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = lib.edpc_compress(C.c_void_p(host.data_ptr()), xp.size, C.byref(cfg), C.byref(outp), C.byref(outn))
+        t_e2e = time.perf_counter() - t0
+        edpc._lib.check(r, "edpc_compress")
+        bits = C.string_at(outp, outn.value)
+        lib.edpc_free(outp)
+        d.barrier()
+        e2e_value, _ = aggregate(xp.size, t_e2e, d)
+        n_chunks = (per - WORKLOAD["context"]) / CHUNK
+        e2e = {"value": e2e_value, "unit": "MB/s", "h2d_bytes_per_step": int(xp.size / n_chunks),
+               "d2h_bytes_per_step": int(len(bits) / n_chunks),
+               "input": f"first {per} bytes of each of the 512 streams ({xp.size} bytes), host pinned"}
+        _, n, be = edpc.peek(bits)
+        bpb = 8 * (len(bits) - (88 + 4 * be + 4)) / n
+
+        # ---- decompress, device-resident output, same prefix input ------------------------
+        outd = torch.empty(xp.size, dtype=torch.uint8, device="cuda")
+        dec = edpc.Decoder(bits, out_device_ptr=outd.data_ptr(), stream=stream.cuda_stream)
+        tdec, donedec, _ = timed_session(dec, W, K, stream, d)
+        dec.finish(to_host=False)  # runs the tail and checks the data checksum
+        dec.close()
+        assert torch.equal(outd.cpu(), host), "decompressed bytes differ from the input"
+        decomp_value, _ = aggregate(donedec * b, tdec, d)
+
+    # ---- roofline of the dominant kernel: FDM adjoint + Adam ---------------------------------
+    fdm_elems = b * WORKLOAD["latent"] ** 2
+    alg_bytes = 24 * fdm_elems  # read U, m, v + write U, m, v (FP32)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    st = out["stats"]
+    achieved = alg_bytes / (st.fdm_bwd_ms / 1e3) / 1e9 if st.fdm_bwd_ms else None
+    roof = {"kernel": "fdm_bwd_kernel (FDM adjoint + Adam)", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak if achieved else None, "traffic": fdm_traffic_from_profile(),
+            "alg_bytes_per_launch": alg_bytes, "mean_ms": st.fdm_bwd_ms, "launches_timed": st.fdm_samples,
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "fdm_fwd": {"alg_bytes_per_launch": 4 * fdm_elems, "mean_ms": st.fdm_fwd_ms,
+                        "achieved": 4 * fdm_elems / (st.fdm_fwd_ms / 1e3) / 1e9 if st.fdm_fwd_ms else None}}
+
+    # ---- CPU oracle baseline ------------------------------------------------------------------
+    cpu = None
+    if d.rank == 0 and d.world == 1 and not args.quick and not args.no_cpu_baseline:
+        n = args.cpu_steps or 8
+        ocfg, omodel, oxp = oracle_model(x, n)
+        tc = oracle_steps(ocfg, omodel, oxp, n)
+        cpu = {"value": b * n / tc / 1e6, "unit": "MB/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{n} model steps of all 512 streams (the first {WORKLOAD['context'] + n} bytes of each "
+                         f"stream), FP64 NumPy oracle, {tc:.1f} s"}
+
+    if d.rank == 0:
+        ms_step = out["t"] / (out["done"] / CHUNK) * 1e3 if out["done"] else None
+        line = {
+            "metric": METRIC, "value": out["value"], "unit": "MB/s", "n_gpus": d.world, "steps": K, "warmup": W,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "multimedia mix 64 MiB (images/PCM/text thirds), 512 streams",
+                       "model": "K=32 D=16 F=512 F'=256 4xMBRB(H=256, 2 branches)", "global_batch": b,
+                       "step": f"{CHUNK} model steps x {b} streams = {CHUNK * b} input bytes",
+                       "l2": "inputs larger than L2: FDM state 403 MB per step pass, no flush",
+                       "parallelism": "replicas" if d.world > 1 else "single"},
+            "decompress_mbs": decomp_value, "fp32_compress_mbs": fp32_value,
+            "bf16_vs_fp32": (out["value"] / fp32_value) if fp32_value else None,
+            "bits_per_byte": bpb,
+            "bits_per_byte_input": "the e2e prefix input (early, still-learning part of each stream)",
+            "e2e": e2e, "gpu_launches": out["launches"],
+            "roofline": roof, "cpu_baseline": cpu, "clocks": out["clocks"],
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    d = Dist(args.gpus)
+    try:
+        run_ours(args, d)
+    finally:
+        d.close()
+
+
+if __name__ == "__main__":
+    main()
