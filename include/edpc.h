@@ -245,6 +245,31 @@ int edpc_cdf_quantize(const float* p, uint32_t rows, uint32_t* freq, uint32_t* c
 int edpc_range_encode(const uint32_t* sym, uint32_t nsym, uint32_t streams, uint8_t* out,
                       uint32_t cap, uint32_t* out_len, void* cuda_stream);
 
+/*
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot allocate device memory per call, such as services that reserve
+ * their whole GPU memory budget at start-up and refuse later allocations, or
+ * loops that cannot absorb the device-wide synchronisation cudaFree may do.
+ *
+ * Same arguments, layout and result as edpc_range_encode, but the per-stream
+ * coder state, output offsets and capacities live in a fixed scratch array
+ * compiled into the library (EDPC_NOALLOC_MAX_STREAMS streams, about 176 KiB,
+ * held on every GPU that loads the library until the process exits). The
+ * call makes no device or host allocation.
+ *   - streams must be <= EDPC_NOALLOC_MAX_STREAMS; larger counts return
+ *     EDPC_EINVAL before any GPU work.
+ *   - The first call on each device looks up the scratch's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture on the device.
+ *   - Every call on a device uses the same scratch and re-initialises it.
+ *     Calls whose GPU work overlaps (different streams or threads, same
+ *     device) race on it and must be serialised by the caller.
+ *   - Returns after the work on cuda_stream has completed.
+ */
+#define EDPC_NOALLOC_MAX_STREAMS 4096u
+int edpc_range_encode_noalloc(const uint32_t* sym, uint32_t nsym, uint32_t streams, uint8_t* out,
+                              uint32_t cap, uint32_t* out_len, void* cuda_stream);
+
 /* ------------------------------------------------------------------------ */
 /* Model: one training step at a given state (gradient and parity checks).  */
 /* ------------------------------------------------------------------------ */

@@ -18,7 +18,7 @@ from ._lib import (EDPC_BF16, EDPC_FLAG_NO_GRAPH, EDPC_FLAG_NO_PIPELINE, EDPC_FP
 __all__ = [
     "Cfg", "EdpcError", "EDPC_FP32", "EDPC_BF16", "EDPC_FLAG_NO_PIPELINE", "EDPC_FLAG_NO_GRAPH",
     "make_cfg", "compress", "decompress", "peek", "param_count", "Encoder", "Decoder", "Model",
-    "cdf_quantize", "range_encode", "load",
+    "cdf_quantize", "range_encode", "range_encode_noalloc", "NOALLOC_MAX_STREAMS", "load",
 ]
 
 
@@ -239,3 +239,15 @@ def range_encode(sym_dev: int, nsym: int, streams: int, out_dev: int, cap: int, 
     """Device pointers: sym (nsym x streams u32) -> out (streams x cap bytes), out_len (streams u32)."""
     check(load().edpc_range_encode(C.c_void_p(sym_dev), nsym, streams, C.c_void_p(out_dev), cap,
                                    C.c_void_p(out_len_dev), C.c_void_p(stream)), "edpc_range_encode")
+
+
+NOALLOC_MAX_STREAMS = 4096
+
+
+def range_encode_noalloc(sym_dev: int, nsym: int, streams: int, out_dev: int, cap: int, out_len_dev: int,
+                         stream: int = 0) -> None:
+    """As range_encode, with the library's fixed scratch instead of per-call
+    device allocations (streams <= NOALLOC_MAX_STREAMS)."""
+    check(load().edpc_range_encode_noalloc(C.c_void_p(sym_dev), nsym, streams, C.c_void_p(out_dev), cap,
+                                           C.c_void_p(out_len_dev), C.c_void_p(stream)),
+          "edpc_range_encode_noalloc")

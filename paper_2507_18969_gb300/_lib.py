@@ -78,6 +78,7 @@ PROTOS = {
     "edpc_session_close": (None, [P]),
     "edpc_cdf_quantize": (C.c_int, [P, C.c_uint32, P, P, P]),
     "edpc_range_encode": (C.c_int, [P, C.c_uint32, C.c_uint32, P, C.c_uint32, P, P]),
+    "edpc_range_encode_noalloc": (C.c_int, [P, C.c_uint32, C.c_uint32, P, C.c_uint32, P, P]),
     "edpc_model_create": (C.c_int, [C.POINTER(Cfg), C.c_uint32, C.POINTER(P)]),
     "edpc_model_destroy": (None, [P]),
     "edpc_model_get_state": (C.c_int, [P, P, P, P, P, P, P, C.POINTER(C.c_uint32)]),
