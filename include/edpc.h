@@ -193,18 +193,19 @@ int edpc_decoder_open(const uint8_t* bits, size_t bits_len, void* out_device, vo
  * copies them to `out_host` (orig_len bytes, caller-owned) if non-NULL. */
 int edpc_decoder_finish(edpc_session* s, uint8_t* out_host);
 
-/* Per-session counters. kernel_ms_* are CUDA-event times of the FDM
- * kernels, averaged over the launches recorded since profiling was
- * enabled (see edpc_session_profile). */
+/* Per-session counters. The fdm_*_ms fields are CUDA-event times of the
+ * FDM kernels, averaged over the steps recorded since profiling was enabled
+ * (see edpc_session_profile). */
 typedef struct {
   uint64_t steps_run;
   uint64_t steps_total;
   uint32_t streams;
   uint32_t launches_per_step;    /* kernels this library launches per model step */
-  double fdm_fwd_ms;             /* mean duration of one FDM forward launch */
-  double fdm_bwd_ms;             /* mean duration of one FDM backward+Adam launch */
+  double fdm_fwd_ms;             /* FDM forward (Eq. 15) */
+  double fdm_bwd_ms;             /* FDM adjoint: dx' alone when the update is split off, else dx' + Adam */
   uint64_t fdm_samples;
   uint64_t coded_bytes;          /* substream bytes so far (after finish: final) */
+  double fdm_adam_ms;            /* FDM Adam update when it runs as its own kernel, else 0 */
 } edpc_stats;
 
 int edpc_session_stats(const edpc_session* s, edpc_stats* st);

@@ -50,6 +50,7 @@ class Stats(C.Structure):
         ("fdm_bwd_ms", C.c_double),
         ("fdm_samples", C.c_uint64),
         ("coded_bytes", C.c_uint64),
+        ("fdm_adam_ms", C.c_double),
     ]
 
 

@@ -304,15 +304,17 @@ struct edpc_session {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int graph_kernels = 0;
-  cudaGraphNode_t ev_nodes[4] = {};
+  cudaGraphNode_t ev_nodes[6] = {};
 
   // FDM kernel timing
   bool profiling = false;
   static constexpr int kEvSets = 64;
-  cudaEvent_t tev[kEvSets][4] = {};
+  static constexpr int kEv = 6;  // FDM forward, adjoint (dx'), side Adam: start/end each
+  cudaEvent_t tev[kEvSets][kEv] = {};
+  bool has_adam_ev = false;
   uint64_t tev_step[kEvSets] = {};
   bool tev_live[kEvSets] = {};
-  double fwd_ms = 0, bwd_ms = 0;
+  double fwd_ms = 0, bwd_ms = 0, adam_ms = 0;
   uint64_t samples = 0;
 
   Model::StepIO io;
@@ -388,7 +390,7 @@ int edpc_session::capture_graph() {
   if (!use_graph || steps_total == 0) return EDPC_OK;
   // Four FDM timing events are recorded in the graph; their nodes are re-pointed
   // at per-step event sets when profiling (cudaGraphExecEventRecordNodeSetEvent).
-  for (int k = 0; k < 4; ++k) model.ev_fdm[k] = tev[0][k];
+  for (int k = 0; k < kEv; ++k) model.ev_fdm[k] = tev[0][k];
   model.timing = true;
   EDPC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
   int r = model.step(io, st);
@@ -407,6 +409,7 @@ int edpc_session::capture_graph() {
   std::vector<cudaGraphNode_t> nodes(nn);
   EDPC_CUDA(cudaGraphGetNodes(graph, nodes.data(), &nn));
   graph_kernels = 0;
+  for (auto& nd : ev_nodes) nd = nullptr;
   for (auto nd : nodes) {
     cudaGraphNodeType t;
     EDPC_CUDA(cudaGraphNodeGetType(nd, &t));
@@ -414,21 +417,27 @@ int edpc_session::capture_graph() {
     if (t == cudaGraphNodeTypeEventRecord) {
       cudaEvent_t e;
       EDPC_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &e));
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < kEv; ++k)
         if (e == tev[0][k]) ev_nodes[k] = nd;
     }
   }
+  has_adam_ev = ev_nodes[4] && ev_nodes[5];
   return EDPC_OK;
 }
 
 int edpc_session::harvest(int k) {
   if (!tev_live[k]) return EDPC_OK;
   EDPC_CUDA(cudaEventSynchronize(tev[k][3]));
-  float a = 0, c = 0;
+  float a = 0, c = 0, m = 0;
   EDPC_CUDA(cudaEventElapsedTime(&a, tev[k][0], tev[k][1]));
   EDPC_CUDA(cudaEventElapsedTime(&c, tev[k][2], tev[k][3]));
+  if (has_adam_ev) {
+    EDPC_CUDA(cudaEventSynchronize(tev[k][5]));
+    EDPC_CUDA(cudaEventElapsedTime(&m, tev[k][4], tev[k][5]));
+  }
   fwd_ms += a;
   bwd_ms += c;
+  adam_ms += m;
   ++samples;
   tev_live[k] = false;
   return EDPC_OK;
@@ -442,10 +451,12 @@ int edpc_session::launch_step() {
   if (profiling) {
     EDPC_TRY(harvest(k));
     if (exec) {
-      for (int q = 0; q < 4; ++q) EDPC_CUDA(cudaGraphExecEventRecordNodeSetEvent(exec, ev_nodes[q], tev[k][q]));
+      for (int q = 0; q < kEv; ++q)
+        if (ev_nodes[q]) EDPC_CUDA(cudaGraphExecEventRecordNodeSetEvent(exec, ev_nodes[q], tev[k][q]));
     } else {
-      for (int q = 0; q < 4; ++q) model.ev_fdm[q] = tev[k][q];
+      for (int q = 0; q < kEv; ++q) model.ev_fdm[q] = tev[k][q];
       model.timing = true;
+      has_adam_ev = model.side && model.d.Fp % 128 == 0;
     }
   }
   if (exec) {
@@ -493,7 +504,7 @@ int edpc_session::join() {
 
 static int session_prepare_events(edpc_session* s) {
   for (int k = 0; k < edpc_session::kEvSets; ++k)
-    for (int q = 0; q < 4; ++q) EDPC_CUDA(cudaEventCreate(&s->tev[k][q]));
+    for (int q = 0; q < edpc_session::kEv; ++q) EDPC_CUDA(cudaEventCreate(&s->tev[k][q]));
   return EDPC_OK;
 }
 
@@ -747,6 +758,7 @@ extern "C" int edpc_session_stats(const edpc_session* s, edpc_stats* o) {
   o->fdm_samples = s->samples;
   o->fdm_fwd_ms = s->samples ? s->fwd_ms / s->samples : 0;
   o->fdm_bwd_ms = s->samples ? s->bwd_ms / s->samples : 0;
+  o->fdm_adam_ms = s->samples ? s->adam_ms / s->samples : 0;
   return EDPC_OK;
 }
 
@@ -756,7 +768,7 @@ extern "C" int edpc_session_profile(edpc_session* s, int on) {
     for (int k = 0; k < edpc_session::kEvSets; ++k) EDPC_TRY(s->harvest(k));
   }
   if (on && !s->profiling) {
-    s->fwd_ms = s->bwd_ms = 0;
+    s->fwd_ms = s->bwd_ms = s->adam_ms = 0;
     s->samples = 0;
   }
   s->profiling = on != 0;

@@ -9,10 +9,20 @@
 //   stage; decode: symbol search inline), CE gradient (Eq. 2).
 // Backward: the hand-written adjoint of every forward op in reverse; the FDM
 //   adjoint is fused with the FDM's Adam update. Adam on the shared params.
+//
+// Two arithmetic paths share this sequence:
+//   FP32  SIMT GEMMs and separate element-wise kernels.
+//   BF16  tcgen05 GEMMs whose epilogues fuse the MBRB element-wise ops and
+//         write the BF16 (and transposed BF16) operands of the next GEMMs; the
+//         weight-gradient GEMMs and column sums, which nothing on the step's
+//         critical path waits for, run on a side stream forked per layer and
+//         joined before Adam.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 
 #include "engine.cuh"
+#include "launch.cuh"
 
 namespace edpc {
 
@@ -27,7 +37,7 @@ Dims make_dims(const edpc_cfg& c, int b) {
   d.n = (int)c.blocks;
   d.nloc = d.n / 2;
   d.k = (int)c.branches;
-  d.ldT = (int)round_up(b, 8);
+  d.ldT = (int)round_up(b, kRowsT);
   return d;
 }
 
@@ -114,6 +124,11 @@ __global__ void set_ctl_kernel(StepCtl* ctl, int i, int t, int bact, int slot, f
 Model::~Model() {
   for (auto& e : ev_fdm)
     if (e) cudaEventDestroy(e);
+  for (auto& e : fork)
+    if (e) cudaEventDestroy(e);
+  if (join_ev) cudaEventDestroy(join_ev);
+  if (tr_ev) cudaEventDestroy(tr_ev);
+  if (side) cudaStreamDestroy(side);
   if (gU) cudaFree(gU);
   if (arena_) cudaFree(arena_);
 }
@@ -126,10 +141,27 @@ int Model::init(const edpc_cfg& cfg, int streams) {
   lr = cfg.lr;
   nparam = po.total;
   const size_t bF = (size_t)d.b * d.F, bFp = (size_t)d.b * d.Fp, bH = (size_t)d.b * d.H;
-  const size_t bkH = (size_t)d.b * d.k * d.H, fdm = (size_t)d.b * d.Fp * d.Fp;
+  const int kH = d.k * d.H;
+  const size_t bkH = (size_t)d.b * kH, fdm = (size_t)d.b * d.Fp * d.Fp;
   const bool bf16 = precision == EDPC_BF16;
-  // Largest activation operand copies (row-major b x max and transposed max x ldT).
-  const int maxw = std::max(std::max(d.F, d.k * d.H), std::max(256, d.Fp));
+  const size_t T = d.ldT;
+
+  // weight matrices that need transposed BF16 copies (32 x 32 tiles)
+  std::vector<TransposeTile> th;
+  if (bf16) {
+    auto mat = [&](size_t off, int rows, int cols) {
+      for (int r0 = 0; r0 < rows; r0 += 32)
+        for (int c0 = 0; c0 < cols; c0 += 32) th.push_back({off, rows, cols, r0, c0});
+    };
+    for (int j = 0; j < d.n; ++j) {
+      mat(po.blk[j].W, kH, d.F);
+      mat(po.blk[j].Wo, d.F, d.H);
+    }
+    mat(po.W1, d.Fp, d.F);
+    mat(po.W2, d.F, d.Fp);
+    mat(po.Wh, 256, d.F);
+  }
+  ntiles = (int)th.size();
 
   for (int pass = 0; pass < 2; ++pass) {
     Arena a;
@@ -147,29 +179,58 @@ int Model::init(const edpc_cfg& cfg, int streams) {
     for (int j = 0; j < d.n; ++j) {
       ba[j].xhat = a.take<float>(bF);
       ba[j].rstd = a.take<float>(d.b);
-      ba[j].X0 = a.take<float>(bF);
       ba[j].A = a.take<float>(bkH);
-      ba[j].G = a.take<float>(bH);
+      if (!bf16) {
+        ba[j].X0 = a.take<float>(bF);
+        ba[j].G = a.take<float>(bH);
+      }
     }
     Xp = a.take<float>(bFp);
     Y = a.take<float>(bFp);
     z = a.take<float>((size_t)d.b * 256);
     p = a.take<float>((size_t)d.b * 256);
     dz = a.take<float>((size_t)d.b * 256);
-    dXa = a.take<float>(bF);
-    dXb = a.take<float>(bF);
-    dX0 = a.take<float>(bF);
-    dA = a.take<float>(bkH);
-    dG = a.take<float>(bH);
     dY = a.take<float>(bFp);
     dXp = a.take<float>(bFp);
-    if (bf16) {
+    emb_part = a.take<float>((size_t)embed_bwd_chunks(d.b, d.K) * 256 * d.D);
+    if (!bf16) {
+      dXa = a.take<float>(bF);
+      dXb = a.take<float>(bF);
+      dX0 = a.take<float>(bF);
+      dA = a.take<float>(bkH);
+      dG = a.take<float>(bH);
+    } else {
       Pb = a.take<__nv_bfloat16>(nparam);
       PbT = a.take<__nv_bfloat16>(nparam);
-      xa = a.take<__nv_bfloat16>((size_t)d.b * maxw);
-      xb = a.take<__nv_bfloat16>((size_t)d.b * maxw);
-      xaT = a.take<__nv_bfloat16>((size_t)d.ldT * maxw);
-      xbT = a.take<__nv_bfloat16>((size_t)d.ldT * maxw);
+      tiles = a.take<TransposeTile>(std::max(1, ntiles));
+      for (int j = 0; j < d.n; ++j) {
+        BlockBf16& q = bb[j];
+        q.X0b = a.take<__nv_bfloat16>(bF);
+        q.X0bT = a.take<__nv_bfloat16>((size_t)d.F * T);
+        q.Gb = a.take<__nv_bfloat16>(bH);
+        q.GbT = a.take<__nv_bfloat16>((size_t)d.H * T);
+        q.dOut = a.take<float>(bF);
+        q.dOutb = a.take<__nv_bfloat16>(bF);
+        q.dOutbT = a.take<__nv_bfloat16>((size_t)d.F * T);
+        q.dA = a.take<float>(bkH);
+        q.dAb = a.take<__nv_bfloat16>(bkH);
+        q.dAbT = a.take<__nv_bfloat16>((size_t)kH * T);
+        q.dX0 = a.take<float>(bF);
+      }
+      Slte_b = a.take<__nv_bfloat16>(bF);
+      Slte_bT = a.take<__nv_bfloat16>((size_t)d.F * T);
+      Shead_b = a.take<__nv_bfloat16>(bF);
+      Shead_bT = a.take<__nv_bfloat16>((size_t)d.F * T);
+      Yb = a.take<__nv_bfloat16>(bFp);
+      YbT = a.take<__nv_bfloat16>((size_t)d.Fp * T);
+      dzb = a.take<__nv_bfloat16>((size_t)d.b * 256);
+      dzbT = a.take<__nv_bfloat16>((size_t)256 * T);
+      dLte = a.take<float>(bF);
+      dLteb = a.take<__nv_bfloat16>(bF);
+      dLtebT = a.take<__nv_bfloat16>((size_t)d.F * T);
+      dXpb = a.take<__nv_bfloat16>(bFp);
+      dXpbT = a.take<__nv_bfloat16>((size_t)d.Fp * T);
+      dh0 = a.take<float>(bF);
     }
     if (pass == 0) {
       arena_bytes_ = a.off + 256;
@@ -181,21 +242,23 @@ int Model::init(const edpc_cfg& cfg, int streams) {
     }
   }
   cudaStream_t st = 0;
+  // zero everything once (transposed copies keep zero padding columns)
+  EDPC_CUDA(cudaMemsetAsync(arena_, 0, arena_bytes_, st));
   // Initial values (counter-based SplitMix64 rule, tensor id = canonical order).
   const double F = d.F, H = d.H, Fp = d.Fp;
-  struct T {
+  struct Tn {
     size_t off, n;
     float bound;
     float fill;
   };
-  std::vector<T> ts;
+  std::vector<Tn> ts;
   ts.push_back({po.E, (size_t)256 * d.D, (float)std::sqrt(3.0), 0.f});
   for (int j = 0; j < d.n; ++j) {
     const BlockOff& b = po.blk[j];
     ts.push_back({b.ln_g, (size_t)d.F, -1.f, 1.f});
     ts.push_back({b.ln_b, (size_t)d.F, -1.f, 0.f});
-    ts.push_back({b.W, (size_t)d.k * d.H * d.F, (float)(1.0 / std::sqrt(F)), 0.f});
-    ts.push_back({b.c, (size_t)d.k * d.H, (float)(1.0 / std::sqrt(F)), 0.f});
+    ts.push_back({b.W, (size_t)kH * d.F, (float)(1.0 / std::sqrt(F)), 0.f});
+    ts.push_back({b.c, (size_t)kH, (float)(1.0 / std::sqrt(F)), 0.f});
     ts.push_back({b.Wo, (size_t)d.F * d.H, (float)(1.0 / std::sqrt(H)), 0.f});
     ts.push_back({b.co, (size_t)d.F, (float)(1.0 / std::sqrt(H)), 0.f});
   }
@@ -208,16 +271,14 @@ int Model::init(const edpc_cfg& cfg, int streams) {
   for (size_t tid = 0; tid < ts.size(); ++tid)
     EDPC_CUDA(launch_init_values(P + ts[tid].off, ts[tid].n, seed, (int)tid, ts[tid].bound, 0, ts[tid].fill, st));
   EDPC_CUDA(launch_init_values(U, fdm, seed, kFdmTid, (float)std::sqrt(3.0 / Fp), 0, 0.f, st));
-  EDPC_CUDA(cudaMemsetAsync(M, 0, nparam * sizeof(float), st));
-  EDPC_CUDA(cudaMemsetAsync(V, 0, nparam * sizeof(float), st));
-  EDPC_CUDA(cudaMemsetAsync(G, 0, nparam * sizeof(float), st));
-  EDPC_CUDA(cudaMemsetAsync(Um, 0, fdm * sizeof(float), st));
-  EDPC_CUDA(cudaMemsetAsync(Uv, 0, fdm * sizeof(float), st));
   if (bf16) {
-    EDPC_CUDA(cudaMemsetAsync(xaT, 0, (size_t)d.ldT * maxw * 2, st));
-    EDPC_CUDA(cudaMemsetAsync(xbT, 0, (size_t)d.ldT * maxw * 2, st));
+    if (ntiles) EDPC_CUDA(cudaMemcpyAsync(tiles, th.data(), th.size() * sizeof(TransposeTile), cudaMemcpyHostToDevice, st));
     EDPC_TRY(refresh_bf16_weights(st));
     EDPC_TRY(build_tc_plan());
+    EDPC_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    for (auto& e : fork) EDPC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    EDPC_CUDA(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
+    EDPC_CUDA(cudaEventCreateWithFlags(&tr_ev, cudaEventDisableTiming));
   }
   EDPC_CUDA(cudaStreamSynchronize(st));
   return EDPC_OK;
@@ -231,163 +292,478 @@ int Model::set_ctl_for_step(int i, int t, int bact, int ring_slots, cudaStream_t
   return EDPC_OK;
 }
 
-// ------------------------------------------------------------------------------------------
-// BF16: weight copies and the tensor-map plan
-// ------------------------------------------------------------------------------------------
 int Model::refresh_bf16_weights(cudaStream_t st) {
-  auto mat = [&](size_t off, int rows, int cols) -> cudaError_t {
-    return launch_to_bf16(P + off, rows, cols, cols, Pb + off, cols, PbT + off, rows, st);
-  };
-  for (int j = 0; j < d.n; ++j) {
-    EDPC_CUDA(mat(po.blk[j].W, d.k * d.H, d.F));
-    EDPC_CUDA(mat(po.blk[j].Wo, d.F, d.H));
-  }
-  EDPC_CUDA(mat(po.W1, d.Fp, d.F));
-  EDPC_CUDA(mat(po.W2, d.F, d.Fp));
-  EDPC_CUDA(mat(po.Wh, 256, d.F));
+  EDPC_CUDA(launch_to_bf16(P, 1, (int)nparam, (int)nparam, Pb, (int)nparam, nullptr, 0, st));
+  EDPC_CUDA(launch_transpose_tiles(Pb, PbT, tiles, ntiles, st));
   return EDPC_OK;
 }
 
-static int pick_bn(int N) { return N <= 128 ? 64 : (N <= 512 ? 64 : 128); }
-
-int Model::build_tc_plan() {
-  auto fwd = [&](int site, int in, size_t w_off, int out) -> int {
-    TcGemm& g = tc.site[site];
-    g.M = d.b;
-    g.N = out;
-    g.K = in;
-    g.bn = pick_bn(out);
-    EDPC_TRY(make_tmap_bf16(&g.ta, xa, d.b, in, in, 128));
-    EDPC_TRY(make_tmap_bf16(&g.tb, Pb + w_off, out, in, in, g.bn));
-    return EDPC_OK;
-  };
-  auto dx = [&](int site, int out, size_t w_off, int in) -> int {
-    TcGemm& g = tc.site[site];
-    g.M = d.b;
-    g.N = in;
-    g.K = out;
-    g.bn = pick_bn(in);
-    EDPC_TRY(make_tmap_bf16(&g.ta, xa, d.b, out, out, 128));
-    EDPC_TRY(make_tmap_bf16(&g.tb, PbT + w_off, in, out, out, g.bn));
-    return EDPC_OK;
-  };
-  auto dw = [&](int site, int out, int in) -> int {
-    TcGemm& g = tc.site[site];
-    g.M = out;
-    g.N = in;
-    g.K = d.b;
-    g.bn = pick_bn(in);
-    EDPC_TRY(make_tmap_bf16(&g.ta, xaT, out, d.b, d.ldT, 128));
-    EDPC_TRY(make_tmap_bf16(&g.tb, xbT, in, d.b, d.ldT, g.bn));
-    return EDPC_OK;
-  };
-  const int kH = d.k * d.H;
-  for (int j = 0; j < d.n; ++j) {
-    EDPC_TRY(fwd(blk_site(BR_FWD, j), d.F, po.blk[j].W, kH));
-    EDPC_TRY(fwd(blk_site(OUT_FWD, j), d.H, po.blk[j].Wo, d.F));
-    EDPC_TRY(dw(blk_site(OUT_DW, j), d.F, d.H));
-    EDPC_TRY(dx(blk_site(OUT_DX, j), d.F, po.blk[j].Wo, d.H));
-    EDPC_TRY(dw(blk_site(BR_DW, j), kH, d.F));
-    EDPC_TRY(dx(blk_site(BR_DX, j), kH, po.blk[j].W, d.F));
-  }
-  EDPC_TRY(fwd(kSiteLteDownFwd, d.F, po.W1, d.Fp));
-  EDPC_TRY(fwd(kSiteLteUpFwd, d.Fp, po.W2, d.F));
-  EDPC_TRY(fwd(kSiteHeadFwd, d.F, po.Wh, 256));
-  EDPC_TRY(dx(kSiteHeadDx, 256, po.Wh, d.F));
-  EDPC_TRY(dw(kSiteHeadDw, 256, d.F));
-  EDPC_TRY(dw(kSiteLteUpDw, d.F, d.Fp));
-  EDPC_TRY(dx(kSiteLteUpDx, d.F, po.W2, d.Fp));
-  EDPC_TRY(dw(kSiteLteDownDw, d.Fp, d.F));
-  EDPC_TRY(dx(kSiteLteDownDx, d.Fp, po.W1, d.F));
-  tc.ready = true;
-  return EDPC_OK;
-}
-
-// ------------------------------------------------------------------------------------------
-// Linear layers (Y = X W^T + b) and their adjoints, in FP32 SIMT or BF16 tcgen05.
-// ------------------------------------------------------------------------------------------
-int Model::linear_fwd(int site, const float* X, int rows, int in, size_t w_off, size_t b_off, int out,
-                      const float* resid, float* Yo, cudaStream_t st) {
+// ==========================================================================================
+// FP32 path
+// ==========================================================================================
+int Model::linear_fwd(const float* X, int rows, int in, size_t w_off, size_t b_off, int out, const float* resid,
+                      float* Yo, cudaStream_t st) {
   const int epi = resid ? EPI_BIAS_RESID : EPI_BIAS;
-  if (precision == EDPC_BF16) {
-    EDPC_CUDA(launch_to_bf16(X, rows, in, in, xa, in, nullptr, 0, st));
-    TcGemm g = tc.site[site];
-    g.C = Yo;
-    g.ldc = out;
-    g.epi = epi;
-    g.bias = P + b_off;
-    g.R = resid;
-    g.ldr = out;
-    g.err = &ctl->err;
-    EDPC_CUDA(launch_gemm_tc(g, st));
-    return EDPC_OK;
-  }
   GemmF32 g{rows, out, in, X, in, true, P + w_off, in, true, Yo, out, epi, P + b_off, resid, out};
   EDPC_CUDA(launch_gemm_f32(g, st));
   return EDPC_OK;
 }
 
-int Model::linear_dx(int site, const float* dOut, int rows, int out, size_t w_off, int in, float* dX,
-                     cudaStream_t st) {
-  if (precision == EDPC_BF16) {
-    EDPC_CUDA(launch_to_bf16(dOut, rows, out, out, xa, out, nullptr, 0, st));
-    TcGemm g = tc.site[site];
-    g.C = dX;
-    g.ldc = in;
-    g.epi = EPI_STORE;
-    g.err = &ctl->err;
-    EDPC_CUDA(launch_gemm_tc(g, st));
-    return EDPC_OK;
-  }
+int Model::linear_dx(const float* dOut, int rows, int out, size_t w_off, int in, float* dX, cudaStream_t st) {
   GemmF32 g{rows, in, out, dOut, out, true, P + w_off, in, false, dX, in, EPI_STORE, nullptr, nullptr, 0};
   EDPC_CUDA(launch_gemm_f32(g, st));
   return EDPC_OK;
 }
 
-int Model::linear_dw(int site, const float* dOut, int rows, int out, const float* X, int in, size_t w_off,
-                     cudaStream_t st) {
-  if (precision == EDPC_BF16) {
-    EDPC_CUDA(launch_to_bf16(dOut, rows, out, out, nullptr, 0, xaT, d.ldT, st));
-    EDPC_CUDA(launch_to_bf16(X, rows, in, in, nullptr, 0, xbT, d.ldT, st));
-    TcGemm g = tc.site[site];
-    g.C = G + w_off;
-    g.ldc = in;
-    g.epi = EPI_STORE;
-    g.err = &ctl->err;
-    EDPC_CUDA(launch_gemm_tc(g, st));
-    return EDPC_OK;
-  }
+int Model::linear_dw(const float* dOut, int rows, int out, const float* X, int in, size_t w_off, cudaStream_t st) {
   GemmF32 g{out, in, rows, dOut, out, false, X, in, false, G + w_off, in, EPI_STORE, nullptr, nullptr, 0};
   EDPC_CUDA(launch_gemm_f32(g, st));
   return EDPC_OK;
 }
 
-// ------------------------------------------------------------------------------------------
-// Forward
-// ------------------------------------------------------------------------------------------
 int Model::block_fwd(int j, const float* Xin, float* Xout, cudaStream_t st) {
   const BlockOff& o = po.blk[j];
   BlockAct& a = ba[j];
   const int kH = d.k * d.H;
-  EDPC_CUDA(launch_ln_fwd(Xin, P + o.ln_g, P + o.ln_b, a.xhat, a.rstd, a.X0, d.b, d.F, st));   // Eq. 9
-  EDPC_TRY(linear_fwd(blk_site(BR_FWD, j), a.X0, d.b, d.F, o.W, o.c, kH, nullptr, a.A, st));   // Eq. 10
-  EDPC_CUDA(launch_branch_gelu(a.A, d.b, d.H, d.k, a.G, st));                                  // Eqs. 11-12
-  EDPC_TRY(linear_fwd(blk_site(OUT_FWD, j), a.G, d.b, d.H, o.Wo, o.co, d.F, Xin, Xout, st));   // Eq. 13
+  EDPC_CUDA(launch_ln_fwd(Xin, P + o.ln_g, P + o.ln_b, a.xhat, a.rstd, a.X0, d.b, d.F, st));  // Eq. 9
+  EDPC_TRY(linear_fwd(a.X0, d.b, d.F, o.W, o.c, kH, nullptr, a.A, st));                       // Eq. 10
+  EDPC_CUDA(launch_branch_gelu(a.A, d.b, d.H, d.k, a.G, st));                                 // Eqs. 11-12
+  EDPC_TRY(linear_fwd(a.G, d.b, d.H, o.Wo, o.co, d.F, Xin, Xout, st));                        // Eq. 13
   return EDPC_OK;
 }
 
-int Model::forward(const StepIO& io, cudaStream_t st) {
+int Model::fdm_fwd_call(cudaStream_t st) {
+  if (timing && ev_fdm[0]) EDPC_CUDA(record_timing(ev_fdm[0], st));
+  EDPC_CUDA(launch_fdm_fwd(Xp, U, Y, d.b, d.Fp, st, Yb, YbT, d.ldT, &ctl->err));  // Eq. 15
+  if (timing && ev_fdm[1]) EDPC_CUDA(record_timing(ev_fdm[1], st));
+  return EDPC_OK;
+}
+
+int Model::forward_f32(const StepIO& io, cudaStream_t st) {
   EDPC_CUDA(launch_embed(io.mode == 2 ? nullptr : io.data, io.sp, ctl, P + po.E, d.b, d.K, d.D, S[0], ctx, st));
   for (int j = 0; j < d.nloc; ++j) EDPC_TRY(block_fwd(j, S[j], S[j + 1], st));
-  const float* lte_in = S[d.nloc];
-  EDPC_TRY(linear_fwd(kSiteLteDownFwd, lte_in, d.b, d.F, po.W1, po.b1, d.Fp, nullptr, Xp, st));  // Eq. 14
-  if (timing && ev_fdm[0]) EDPC_CUDA(record_timing(ev_fdm[0], st));
-  EDPC_CUDA(launch_fdm_fwd(Xp, U, Y, d.b, d.Fp, st));                                              // Eq. 15
-  if (timing && ev_fdm[1]) EDPC_CUDA(record_timing(ev_fdm[1], st));
-  EDPC_TRY(linear_fwd(kSiteLteUpFwd, Y, d.b, d.Fp, po.W2, po.b2, d.F, nullptr, S[d.nloc + 1], st));  // Eq. 16
+  EDPC_TRY(linear_fwd(S[d.nloc], d.b, d.F, po.W1, po.b1, d.Fp, nullptr, Xp, st));  // Eq. 14
+  EDPC_TRY(fdm_fwd_call(st));
+  EDPC_TRY(linear_fwd(Y, d.b, d.Fp, po.W2, po.b2, d.F, nullptr, S[d.nloc + 1], st));  // Eq. 16
   for (int j = d.nloc; j < d.n; ++j) EDPC_TRY(block_fwd(j, S[j + 1], S[j + 2], st));
-  EDPC_TRY(linear_fwd(kSiteHeadFwd, S[d.n + 1], d.b, d.F, po.Wh, po.bh, 256, nullptr, z, st));
+  EDPC_TRY(linear_fwd(S[d.n + 1], d.b, d.F, po.Wh, po.bh, 256, nullptr, z, st));
   return EDPC_OK;
+}
+
+int Model::block_bwd(int j, const float* dOut, float* dXnew, cudaStream_t st) {
+  const BlockOff& o = po.blk[j];
+  BlockAct& a = ba[j];
+  const int kH = d.k * d.H;
+  // Eq. 13: out = G Wo^T + co + X
+  EDPC_TRY(linear_dw(dOut, d.b, d.F, a.G, d.H, o.Wo, st));
+  EDPC_CUDA(launch_colsum(dOut, nullptr, d.b, d.F, d.F, G + o.co, st));
+  EDPC_TRY(linear_dx(dOut, d.b, d.F, o.Wo, d.H, dG, st));
+  // Eqs. 11-12: G = GELU(prod X_i)
+  EDPC_CUDA(launch_branch_gelu_bwd(dG, a.A, d.b, d.H, d.k, dA, st));
+  // Eq. 10: X_i = X0 W_i^T + c_i
+  EDPC_TRY(linear_dw(dA, d.b, kH, a.X0, d.F, o.W, st));
+  EDPC_CUDA(launch_colsum(dA, nullptr, d.b, kH, kH, G + o.c, st));
+  EDPC_TRY(linear_dx(dA, d.b, kH, o.W, d.F, dX0, st));
+  // Eq. 9: X0 = g * xhat + beta, plus the residual path of Eq. 13
+  EDPC_CUDA(launch_colsum(dX0, a.xhat, d.b, d.F, d.F, G + o.ln_g, st));
+  EDPC_CUDA(launch_colsum(dX0, nullptr, d.b, d.F, d.F, G + o.ln_b, st));
+  EDPC_CUDA(launch_ln_bwd(dX0, a.xhat, a.rstd, P + o.ln_g, dOut, dXnew, d.b, d.F, st));
+  return EDPC_OK;
+}
+
+int Model::fdm_bwd_call(const StepIO& io, cudaStream_t st) {
+  FdmBwdArgs fa{};
+  fa.Xp = Xp;
+  fa.dY = dY;
+  fa.U = U;
+  fa.Um = Um;
+  fa.Uv = Uv;
+  fa.dXp = dXp;
+  fa.gU = gU;
+  fa.ctl = ctl;
+  fa.sp = io.sp;
+  fa.active = io.mode == 2 ? io.active : nullptr;
+  fa.b = d.b;
+  fa.Fp = d.Fp;
+  fa.update = io.update;
+  fa.dXpb = dXpb;
+  fa.dXpbT = dXpbT;
+  fa.ldT = d.ldT;
+  if (timing && ev_fdm[2]) EDPC_CUDA(record_timing(ev_fdm[2], st));
+  EDPC_CUDA(launch_fdm_bwd(fa, st));
+  if (timing && ev_fdm[3]) EDPC_CUDA(record_timing(ev_fdm[3], st));
+  return EDPC_OK;
+}
+
+int Model::backward_f32(const StepIO& io, cudaStream_t st) {
+  const float* head_in = S[d.n + 1];
+  EDPC_TRY(linear_dw(dz, d.b, 256, head_in, d.F, po.Wh, st));
+  EDPC_CUDA(launch_colsum(dz, nullptr, d.b, 256, 256, G + po.bh, st));
+  EDPC_TRY(linear_dx(dz, d.b, 256, po.Wh, d.F, dXa, st));
+  float* cur = dXa;
+  float* nxt = dXb;
+  for (int j = d.n - 1; j >= d.nloc; --j) {
+    EDPC_TRY(block_bwd(j, cur, nxt, st));
+    std::swap(cur, nxt);
+  }
+  // LTE up (Eq. 16)
+  EDPC_TRY(linear_dw(cur, d.b, d.F, Y, d.Fp, po.W2, st));
+  EDPC_CUDA(launch_colsum(cur, nullptr, d.b, d.F, d.F, G + po.b2, st));
+  EDPC_TRY(linear_dx(cur, d.b, d.F, po.W2, d.Fp, dY, st));
+  // FDM (Eq. 15): adjoint fused with the FDM's Adam update
+  EDPC_TRY(fdm_bwd_call(io, st));
+  // LTE down (Eq. 14)
+  EDPC_TRY(linear_dw(dXp, d.b, d.Fp, S[d.nloc], d.F, po.W1, st));
+  EDPC_CUDA(launch_colsum(dXp, nullptr, d.b, d.Fp, d.Fp, G + po.b1, st));
+  EDPC_TRY(linear_dx(dXp, d.b, d.Fp, po.W1, d.F, cur, st));
+  for (int j = d.nloc - 1; j >= 0; --j) {
+    EDPC_TRY(block_bwd(j, cur, nxt, st));
+    std::swap(cur, nxt);
+  }
+  emb_in_adam = io.update != 0;
+  EDPC_CUDA(launch_embed_bwd(ctx, cur, d.b, d.K, d.D, G + po.E, emb_part, st, !emb_in_adam));
+  return EDPC_OK;
+}
+
+// ==========================================================================================
+// BF16 path
+// ==========================================================================================
+int Model::build_tc_plan() {
+  const int kH = d.k * d.H;
+  const int T = d.ldT;
+  // N tile: 32 while 64-wide tiles would leave the GPU mostly idle (small b), else 64.
+  auto bn_for = [&](int N) { return ((d.b + 127) / 128) * ((N + 63) / 64) < 2 * 152 ? 32 : 64; };
+  auto site = [&](int id, int M, int N, int K, const void* a, int a_rows, int a_cols, int a_ld, const void* b,
+                  int b_rows, int b_cols, int b_ld, int bn, int box_b) -> int {
+    TcGemm& g = tcp.site[id];
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.bn = bn;
+    g.box_b = box_b;
+    g.err = &ctl->err;
+    EDPC_TRY(make_tmap_bf16(&g.ta, a, a_rows, a_cols, a_ld, 128));
+    EDPC_TRY(make_tmap_bf16(&g.tb, b, b_rows, b_cols, b_ld, box_b));
+    return EDPC_OK;
+  };
+  const int b = d.b, F = d.F, H = d.H, Fp = d.Fp;
+  for (int j = 0; j < d.n; ++j) {
+    const BlockOff& o = po.blk[j];
+    BlockBf16& q = bb[j];
+    // Eqs. 10-12: branch GEMM, B loaded as k sections of 32 hidden units
+    {
+      int id = blk_site(BR_FWD, j);
+      EDPC_TRY(site(id, b, kH, F, q.X0b, b, F, F, Pb + o.W, kH, F, F, 32 * d.k, 32));
+      TcGemm& g = tcp.site[id];
+      g.mode = TC_BRANCH;
+      g.H = H;
+      g.k = d.k;
+      g.C = ba[j].A;
+      g.ldc = kH;
+      g.Cb = q.Gb;
+      g.ldcb = H;
+      g.CbT = q.GbT;
+      g.ldct = T;
+      g.bias = P + o.c;
+    }
+    // Eq. 13: out GEMM + residual (the output's BF16 copies when a GEMM reads it next)
+    {
+      int id = blk_site(OUT_FWD, j);
+      int bn = bn_for(F);
+      EDPC_TRY(site(id, b, F, H, q.Gb, b, H, H, Pb + o.Wo, F, H, H, bn, bn));
+      TcGemm& g = tcp.site[id];
+      int out = (j < d.nloc) ? j + 1 : j + 2;
+      int in = (j < d.nloc) ? j : j + 1;
+      g.C = S[out];
+      g.ldc = F;
+      g.bias = P + o.co;
+      g.R = S[in];
+      g.ldr = F;
+      if (j == d.nloc - 1) {
+        g.Cb = Slte_b;
+        g.ldcb = F;
+        g.CbT = Slte_bT;
+        g.ldct = T;
+      } else if (j == d.n - 1) {
+        g.Cb = Shead_b;
+        g.ldcb = F;
+        g.CbT = Shead_bT;
+        g.ldct = T;
+      }
+    }
+    // adjoint of Eq. 13 w.r.t. G, fused with the adjoint of Eqs. 11-12
+    {
+      int id = blk_site(OUT_DX, j);
+      EDPC_TRY(site(id, b, H, F, q.dOutb, b, F, F, PbT + o.Wo, H, F, F, 32, 32));
+      TcGemm& g = tcp.site[id];
+      g.mode = TC_BRANCH_BWD;
+      g.H = H;
+      g.k = d.k;
+      g.C = q.dA;
+      g.ldc = kH;
+      g.Cb = q.dAb;
+      g.ldcb = kH;
+      g.CbT = q.dAbT;
+      g.ldct = T;
+      g.Aux = ba[j].A;
+      g.ldaux = kH;
+    }
+    {  // dWo = dOut^T G
+      int id = blk_site(OUT_DW, j);
+      int bn = bn_for(H);
+      EDPC_TRY(site(id, F, H, b, q.dOutbT, F, b, T, q.GbT, H, b, T, bn, bn));
+      TcGemm& g = tcp.site[id];
+      g.C = G + o.Wo;
+      g.ldc = H;
+    }
+    {  // dX0 = dA W
+      int id = blk_site(BR_DX, j);
+      int bn = bn_for(F);
+      EDPC_TRY(site(id, b, F, kH, q.dAb, b, kH, kH, PbT + o.W, F, kH, kH, bn, bn));
+      TcGemm& g = tcp.site[id];
+      g.C = q.dX0;
+      g.ldc = F;
+    }
+    {  // dW = dA^T X0
+      int id = blk_site(BR_DW, j);
+      int bn = bn_for(F);
+      EDPC_TRY(site(id, kH, F, b, q.dAbT, kH, b, T, q.X0bT, F, b, T, bn, bn));
+      TcGemm& g = tcp.site[id];
+      g.C = G + o.W;
+      g.ldc = F;
+    }
+  }
+  {  // Eq. 14
+    int bn = bn_for(Fp);
+    EDPC_TRY(site(kSiteLteDownFwd, b, Fp, F, Slte_b, b, F, F, Pb + po.W1, Fp, F, F, bn, bn));
+    TcGemm& g = tcp.site[kSiteLteDownFwd];
+    g.C = Xp;
+    g.ldc = Fp;
+    g.bias = P + po.b1;
+  }
+  {  // Eq. 16
+    int bn = bn_for(F);
+    EDPC_TRY(site(kSiteLteUpFwd, b, F, Fp, Yb, b, Fp, Fp, Pb + po.W2, F, Fp, Fp, bn, bn));
+    TcGemm& g = tcp.site[kSiteLteUpFwd];
+    g.C = S[d.nloc + 1];
+    g.ldc = F;
+    g.bias = P + po.b2;
+  }
+  {  // head
+    EDPC_TRY(site(kSiteHeadFwd, b, 256, F, Shead_b, b, F, F, Pb + po.Wh, 256, F, F, 64, 64));
+    TcGemm& g = tcp.site[kSiteHeadFwd];
+    g.C = z;
+    g.ldc = 256;
+    g.bias = P + po.bh;
+  }
+  {  // head adjoint: dX = dz Wh -> gradient of the last block's output
+    int bn = bn_for(F);
+    EDPC_TRY(site(kSiteHeadDx, b, F, 256, dzb, b, 256, 256, PbT + po.Wh, F, 256, 256, bn, bn));
+    TcGemm& g = tcp.site[kSiteHeadDx];
+    BlockBf16& q = bb[d.n - 1];
+    g.C = q.dOut;
+    g.ldc = F;
+    g.Cb = q.dOutb;
+    g.ldcb = F;
+    g.CbT = q.dOutbT;
+    g.ldct = T;
+  }
+  {  // dWh = dz^T X
+    int bn = bn_for(F);
+    EDPC_TRY(site(kSiteHeadDw, 256, F, b, dzbT, 256, b, T, Shead_bT, F, b, T, bn, bn));
+    TcGemm& g = tcp.site[kSiteHeadDw];
+    g.C = G + po.Wh;
+    g.ldc = F;
+  }
+  {  // LTE up adjoint: dY = dX W2
+    int bn = bn_for(Fp);
+    EDPC_TRY(site(kSiteLteUpDx, b, Fp, F, dLteb, b, F, F, PbT + po.W2, Fp, F, F, bn, bn));
+    TcGemm& g = tcp.site[kSiteLteUpDx];
+    g.C = dY;
+    g.ldc = Fp;
+  }
+  {  // dW2 = dX^T Y
+    int bn = bn_for(Fp);
+    EDPC_TRY(site(kSiteLteUpDw, F, Fp, b, dLtebT, F, b, T, YbT, Fp, b, T, bn, bn));
+    TcGemm& g = tcp.site[kSiteLteUpDw];
+    g.C = G + po.W2;
+    g.ldc = Fp;
+  }
+  {  // LTE down adjoint: dX = dX' W1 -> gradient of the last Local block's output
+    int bn = bn_for(F);
+    EDPC_TRY(site(kSiteLteDownDx, b, F, Fp, dXpb, b, Fp, Fp, PbT + po.W1, F, Fp, Fp, bn, bn));
+    TcGemm& g = tcp.site[kSiteLteDownDx];
+    g.ldc = F;
+    if (d.nloc > 0) {
+      BlockBf16& q = bb[d.nloc - 1];
+      g.C = q.dOut;
+      g.Cb = q.dOutb;
+      g.ldcb = F;
+      g.CbT = q.dOutbT;
+      g.ldct = T;
+    } else {
+      g.C = dh0;
+    }
+  }
+  {  // dW1 = dX'^T X
+    int bn = bn_for(F);
+    EDPC_TRY(site(kSiteLteDownDw, Fp, F, b, dXpbT, Fp, b, T, Slte_bT, F, b, T, bn, bn));
+    TcGemm& g = tcp.site[kSiteLteDownDw];
+    g.C = G + po.W1;
+    g.ldc = F;
+  }
+  tcp.ready = true;
+  return EDPC_OK;
+}
+
+int Model::run_tc(int site, cudaStream_t st) {
+  if (st == side) {
+    NoPdl scope;
+    EDPC_CUDA(launch_gemm_tc(tcp.site[site], st));
+  } else {
+    EDPC_CUDA(launch_gemm_tc(tcp.site[site], st));
+  }
+  return EDPC_OK;
+}
+
+int Model::fork_side(cudaStream_t st) {
+  if (nfork_ >= kForks) return fail(EDPC_EINVAL, "too many side-stream forks in one step");
+  cudaEvent_t e = fork[nfork_++];
+  EDPC_CUDA(cudaEventRecord(e, st));
+  EDPC_CUDA(cudaStreamWaitEvent(side, e, 0));
+  return EDPC_OK;
+}
+
+int Model::forward_bf16(const StepIO& io, cudaStream_t st) {
+  nfork_ = 0;
+  // Transposed BF16 weight copies for this step's dX GEMMs, from the weights the
+  // previous Adam wrote, on the side stream while the forward pass runs.
+  EDPC_TRY(fork_side(st));
+  {
+    NoPdl scope;
+    EDPC_CUDA(launch_transpose_tiles(Pb, PbT, tiles, ntiles, side));
+  }
+  EDPC_CUDA(cudaEventRecord(tr_ev, side));
+  EDPC_CUDA(launch_embed(io.mode == 2 ? nullptr : io.data, io.sp, ctl, P + po.E, d.b, d.K, d.D, S[0], ctx, st));
+  if (d.nloc == 0) EDPC_CUDA(launch_to_bf16(S[0], d.b, d.F, d.F, Slte_b, d.F, Slte_bT, d.ldT, st));
+  for (int jj = 0; jj < d.n; ++jj) {
+    if (jj == d.nloc) {
+      EDPC_TRY(run_tc(kSiteLteDownFwd, st));  // Eq. 14
+      EDPC_TRY(fdm_fwd_call(st));             // Eq. 15
+      EDPC_TRY(run_tc(kSiteLteUpFwd, st));    // Eq. 16
+    }
+    const BlockOff& o = po.blk[jj];
+    const float* Xin = S[jj < d.nloc ? jj : jj + 1];
+    EDPC_CUDA(launch_ln_fwd_bf16(Xin, P + o.ln_g, P + o.ln_b, ba[jj].xhat, ba[jj].rstd, bb[jj].X0b, bb[jj].X0bT,
+                                 d.b, d.F, d.ldT, st));  // Eq. 9
+    EDPC_TRY(run_tc(blk_site(BR_FWD, jj), st));         // Eqs. 10-12
+    EDPC_TRY(run_tc(blk_site(OUT_FWD, jj), st));        // Eq. 13
+  }
+  EDPC_TRY(run_tc(kSiteHeadFwd, st));
+  return EDPC_OK;
+}
+
+int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
+  const int kH = d.k * d.H;
+  EDPC_CUDA(cudaStreamWaitEvent(st, tr_ev, 0));  // PbT is read by the dX GEMMs below
+  // side: head weight gradients
+  EDPC_TRY(fork_side(st));
+  EDPC_TRY(run_tc(kSiteHeadDw, side));
+  {
+    ColsumJobs cj{};
+    cj.job[0] = {dz, nullptr, d.b, 256, 256, G + po.bh};
+    cj.n = 1;
+    { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj, side)); }
+  }
+  {
+    NoPdl scope;  // the stream also waits on the transposes' event
+    EDPC_TRY(run_tc(kSiteHeadDx, st));  // dOut of the last block
+  }
+  for (int j = d.n - 1; j >= 0; --j) {
+    const BlockOff& o = po.blk[j];
+    BlockBf16& q = bb[j];
+    if (j == d.nloc - 1) {
+      // LTE (Eqs. 14-16) between the Global and the Local blocks
+      EDPC_TRY(fork_side(st));
+      EDPC_TRY(run_tc(kSiteLteUpDw, side));
+      ColsumJobs cj{};
+      cj.job[0] = {dLte, nullptr, d.b, d.F, d.F, G + po.b2};
+      cj.n = 1;
+      { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj, side)); }
+      EDPC_TRY(run_tc(kSiteLteUpDx, st));
+      EDPC_TRY(fdm_bwd_call(io, st));
+      EDPC_TRY(fork_side(st));
+      EDPC_TRY(run_tc(kSiteLteDownDw, side));
+      ColsumJobs cj2{};
+      cj2.job[0] = {dXp, nullptr, d.b, d.Fp, d.Fp, G + po.b1};
+      cj2.n = 1;
+      { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj2, side)); }
+      EDPC_TRY(run_tc(kSiteLteDownDx, st));
+    }
+    EDPC_TRY(fork_side(st));  // dOut_j is ready
+    EDPC_TRY(run_tc(blk_site(OUT_DW, j), side));
+    EDPC_TRY(run_tc(blk_site(OUT_DX, j), st));  // dA (adjoint of Eqs. 11-13)
+    EDPC_TRY(fork_side(st));
+    EDPC_TRY(run_tc(blk_site(BR_DW, j), side));
+    EDPC_TRY(run_tc(blk_site(BR_DX, j), st));  // dX0 (adjoint of Eq. 10)
+    EDPC_TRY(fork_side(st));
+    {
+      ColsumJobs cj{};
+      cj.job[0] = {q.dOut, nullptr, d.b, d.F, d.F, G + o.co};
+      cj.job[1] = {q.dA, nullptr, d.b, kH, kH, G + o.c};
+      cj.job[2] = {q.dX0, ba[j].xhat, d.b, d.F, d.F, G + o.ln_g};
+      cj.job[3] = {q.dX0, nullptr, d.b, d.F, d.F, G + o.ln_b};
+      cj.n = 4;
+      { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj, side)); }
+    }
+    // LN adjoint (Eq. 9) + residual path: gradient of the block input
+    float* out;
+    __nv_bfloat16 *outb = nullptr, *outbT = nullptr;
+    if (j == d.nloc) {
+      out = dLte;
+      outb = dLteb;
+      outbT = dLtebT;
+    } else if (j == 0) {
+      out = dh0;
+    } else {
+      out = bb[j - 1].dOut;
+      outb = bb[j - 1].dOutb;
+      outbT = bb[j - 1].dOutbT;
+    }
+    EDPC_CUDA(launch_ln_bwd_bf16(q.dX0, ba[j].xhat, ba[j].rstd, P + o.ln_g, q.dOut, out, outb, outbT, d.b, d.F,
+                                 d.ldT, st));
+  }
+  if (d.nloc == 0) {
+    // LTE before any Local block: its adjoint runs after the Global blocks.
+    EDPC_TRY(fork_side(st));
+    EDPC_TRY(run_tc(kSiteLteUpDw, side));
+    ColsumJobs cj{};
+    cj.job[0] = {dLte, nullptr, d.b, d.F, d.F, G + po.b2};
+    cj.n = 1;
+    { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj, side)); }
+    EDPC_TRY(run_tc(kSiteLteUpDx, st));
+    EDPC_TRY(fdm_bwd_call(io, st));
+    EDPC_TRY(fork_side(st));
+    EDPC_TRY(run_tc(kSiteLteDownDw, side));
+    ColsumJobs cj2{};
+    cj2.job[0] = {dXp, nullptr, d.b, d.Fp, d.Fp, G + po.b1};
+    cj2.n = 1;
+    { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj2, side)); }
+    EDPC_TRY(run_tc(kSiteLteDownDx, st));  // writes dh0
+  }
+  emb_in_adam = io.update != 0;
+  EDPC_CUDA(launch_embed_bwd(ctx, dh0, d.b, d.K, d.D, G + po.E, emb_part, st, !emb_in_adam));
+  // join the side stream
+  EDPC_CUDA(cudaEventRecord(join_ev, side));
+  EDPC_CUDA(cudaStreamWaitEvent(st, join_ev, 0));
+  return EDPC_OK;
+}
+
+// ==========================================================================================
+// step
+// ==========================================================================================
+int Model::forward(const StepIO& io, cudaStream_t st) {
+  return precision == EDPC_BF16 ? forward_bf16(io, st) : forward_f32(io, st);
 }
 
 int Model::head(const StepIO& io, cudaStream_t st) {
@@ -407,86 +783,28 @@ int Model::head(const StepIO& io, cudaStream_t st) {
   h.bits = io.bits;
   h.bits_off = io.bits_off;
   h.bits_len = io.bits_len;
+  h.dzb = dzb;
+  h.dzbT = dzbT;
+  h.ldT = d.ldT;
   h.err = &ctl->err;
   EDPC_CUDA(launch_head(h, st));
   return EDPC_OK;
 }
 
-// ------------------------------------------------------------------------------------------
-// Backward (adjoint of the forward, in reverse order)
-// ------------------------------------------------------------------------------------------
-int Model::block_bwd(int j, const float* dOut, const float* Xin, float* dXnew, cudaStream_t st) {
-  const BlockOff& o = po.blk[j];
-  BlockAct& a = ba[j];
-  const int kH = d.k * d.H;
-  // Eq. 13: out = G Wo^T + co + X
-  EDPC_TRY(linear_dw(blk_site(OUT_DW, j), dOut, d.b, d.F, a.G, d.H, o.Wo, st));
-  EDPC_CUDA(launch_colsum(dOut, nullptr, d.b, d.F, d.F, G + o.co, st));
-  EDPC_TRY(linear_dx(blk_site(OUT_DX, j), dOut, d.b, d.F, o.Wo, d.H, dG, st));
-  // Eqs. 11-12: G = GELU(prod X_i)
-  EDPC_CUDA(launch_branch_gelu_bwd(dG, a.A, d.b, d.H, d.k, dA, st));
-  // Eq. 10: X_i = X0 W_i^T + c_i
-  EDPC_TRY(linear_dw(blk_site(BR_DW, j), dA, d.b, kH, a.X0, d.F, o.W, st));
-  EDPC_CUDA(launch_colsum(dA, nullptr, d.b, kH, kH, G + o.c, st));
-  EDPC_TRY(linear_dx(blk_site(BR_DX, j), dA, d.b, kH, o.W, d.F, dX0, st));
-  // Eq. 9: X0 = g * xhat + beta, plus the residual path of Eq. 13
-  EDPC_CUDA(launch_colsum(dX0, a.xhat, d.b, d.F, d.F, G + o.ln_g, st));
-  EDPC_CUDA(launch_colsum(dX0, nullptr, d.b, d.F, d.F, G + o.ln_b, st));
-  EDPC_CUDA(launch_ln_bwd(dX0, a.xhat, a.rstd, P + o.ln_g, dOut, dXnew, d.b, d.F, st));
-  (void)Xin;
-  return EDPC_OK;
-}
-
 int Model::backward(const StepIO& io, cudaStream_t st) {
-  // head: z = X Wh^T + bh
-  const float* head_in = S[d.n + 1];
-  EDPC_TRY(linear_dw(kSiteHeadDw, dz, d.b, 256, head_in, d.F, po.Wh, st));
-  EDPC_CUDA(launch_colsum(dz, nullptr, d.b, 256, 256, G + po.bh, st));
-  EDPC_TRY(linear_dx(kSiteHeadDx, dz, d.b, 256, po.Wh, d.F, dXa, st));
-  float* cur = dXa;
-  float* nxt = dXb;
-  for (int j = d.n - 1; j >= d.nloc; --j) {
-    EDPC_TRY(block_bwd(j, cur, S[j + 1], nxt, st));
-    std::swap(cur, nxt);
-  }
-  // LTE up (Eq. 16)
-  EDPC_TRY(linear_dw(kSiteLteUpDw, cur, d.b, d.F, Y, d.Fp, po.W2, st));
-  EDPC_CUDA(launch_colsum(cur, nullptr, d.b, d.F, d.F, G + po.b2, st));
-  EDPC_TRY(linear_dx(kSiteLteUpDx, cur, d.b, d.F, po.W2, d.Fp, dY, st));
-  // FDM (Eq. 15): adjoint fused with the FDM's Adam update
-  FdmBwdArgs fa{};
-  fa.Xp = Xp;
-  fa.dY = dY;
-  fa.U = U;
-  fa.Um = Um;
-  fa.Uv = Uv;
-  fa.dXp = dXp;
-  fa.gU = gU;
-  fa.ctl = ctl;
-  fa.sp = io.sp;
-  fa.active = io.mode == 2 ? io.active : nullptr;
-  fa.b = d.b;
-  fa.Fp = d.Fp;
-  fa.update = io.update;
-  if (timing && ev_fdm[2]) EDPC_CUDA(record_timing(ev_fdm[2], st));
-  EDPC_CUDA(launch_fdm_bwd(fa, st));
-  if (timing && ev_fdm[3]) EDPC_CUDA(record_timing(ev_fdm[3], st));
-  // LTE down (Eq. 14)
-  EDPC_TRY(linear_dw(kSiteLteDownDw, dXp, d.b, d.Fp, S[d.nloc], d.F, po.W1, st));
-  EDPC_CUDA(launch_colsum(dXp, nullptr, d.b, d.Fp, d.Fp, G + po.b1, st));
-  EDPC_TRY(linear_dx(kSiteLteDownDx, dXp, d.b, d.Fp, po.W1, d.F, cur, st));
-  for (int j = d.nloc - 1; j >= 0; --j) {
-    EDPC_TRY(block_bwd(j, cur, S[j], nxt, st));
-    std::swap(cur, nxt);
-  }
-  // embedding: scatter-add into E's rows
-  EDPC_CUDA(launch_embed_bwd(ctx, cur, d.b, d.K, d.D, G + po.E, st));
-  return EDPC_OK;
+  return precision == EDPC_BF16 ? backward_bf16(io, st) : backward_f32(io, st);
 }
 
 int Model::adam(cudaStream_t st) {
-  EDPC_CUDA(launch_adam(P, G, M, V, nparam, ctl, st));
-  if (precision == EDPC_BF16) EDPC_TRY(refresh_bf16_weights(st));
+  EmbGrad eg{nullptr, 0, 0, 0};
+  if (emb_in_adam) eg = EmbGrad{emb_part, embed_bwd_chunks(d.b, d.K), po.E, (size_t)256 * d.D};
+  if (precision == EDPC_BF16) {
+    NoPdl scope;  // follows the join of the side stream
+    EDPC_CUDA(launch_adam_bf16(P, G, M, V, Pb, nparam, ctl, st, eg));
+  } else {
+    EDPC_CUDA(launch_adam(P, G, M, V, nparam, ctl, st, eg));
+  }
+  emb_in_adam = false;
   return EDPC_OK;
 }
 
@@ -500,21 +818,16 @@ int Model::step(const StepIO& io, cudaStream_t st) {
 }
 
 int Model::launches_per_step() const {
-  const bool bf = precision == EDPC_BF16;
-  // forward: embed + per block (ln, 2 GEMMs, gelu) + LTE (2 GEMMs + fdm) + head GEMM
-  int fwd_gemms = 2 * d.n + 3;
-  int n = 1 + 2 * d.n + fwd_gemms + 1;
-  n += 1;  // head
-  // backward: head (dw, colsum, dx); per block (2 dw, 2 dx, 4 colsum, gelu, ln) ; LTE (2 dw, 2 dx, 2 colsum) + fdm + embed
-  int bwd_gemms = 2 + 4 * d.n + 4;
-  n += bwd_gemms + 1 + 6 * d.n + 2 + 2;
-  n += 1 + 1;  // adam, advance
-  if (bf) {
-    n += fwd_gemms;             // operand copies before forward GEMMs
-    n += bwd_gemms / 2 * 2 + bwd_gemms / 2;  // dx: 1 copy, dw: 2 copies
-    n += 2 * d.n + 3;           // weight refresh after Adam
+  if (precision == EDPC_BF16) {
+    // forward: embed + 3 per block + LTE (2 GEMMs + FDM) + head GEMM + head
+    int n = 1 + 3 * d.n + 3 + 1 + 1;
+    // backward: head dW/colsum/dX, per block 3 main + 3 side, LTE 3 + 2 side ... + embed
+    n += 3 + 6 * d.n + 3 + 4 + 1;
+    return n + 3;  // adam, transpose, advance
   }
-  return n;
+  int n = 1 + 4 * d.n + 3 + 1 + 1;
+  n += 3 + 10 * d.n + 3 + 1 + 3 + 1;
+  return n + 2;
 }
 
 }  // namespace edpc

@@ -5,27 +5,29 @@
 #include <vector>
 
 #include "common.cuh"
-#include "kernels.cuh"
 #include "gemm_tc.cuh"
+#include "kernels.cuh"
 
 namespace edpc {
 
 struct BlockAct {
   float* xhat;  // b x F  normalised input
   float* rstd;  // b
-  float* X0;    // b x F  LN output (Eq. 9)
+  float* X0;    // b x F  LN output (Eq. 9), FP32 path
   float* A;     // b x kH branch outputs [X_1 | ... | X_k] (Eq. 10)
-  float* G;     // b x H  GELU(X_fused) (Eq. 12)
+  float* G;     // b x H  GELU(X_fused) (Eq. 12), FP32 path
 };
 
-// BF16 copies of GEMM operands (BF16 mode only). Row-major copies are
-// K-major A operands of forward/dX GEMMs; transposed copies [feature][b]
-// are the K-major operands of the dW GEMMs (contraction over streams).
-struct Bf16Ops {
-  __nv_bfloat16* P;    // weights, row-major, same flat layout as the FP32 params
-  __nv_bfloat16* PT;   // weights, transposed per matrix (same offsets)
-  __nv_bfloat16* act;  // activation copies (arena)
-  __nv_bfloat16* actT;
+// BF16-path buffers of one MBRB block. "T" buffers are transposed copies
+// [feature][ldT], the K-major operands of the dW GEMMs (contraction over streams).
+struct BlockBf16 {
+  __nv_bfloat16 *X0b, *X0bT;      // LN output
+  __nv_bfloat16 *Gb, *GbT;        // GELU output
+  float* dOut;                    // gradient w.r.t. the block output (b x F)
+  __nv_bfloat16 *dOutb, *dOutbT;
+  float* dA;                      // gradient w.r.t. the branch outputs (b x kH)
+  __nv_bfloat16 *dAb, *dAbT;
+  float* dX0;                     // gradient w.r.t. the LN output (b x F)
 };
 
 class Model {
@@ -49,15 +51,32 @@ class Model {
   float *Xp = nullptr, *Y = nullptr, *z = nullptr, *p = nullptr, *dz = nullptr;
   float *dXa = nullptr, *dXb = nullptr, *dX0 = nullptr, *dA = nullptr, *dG = nullptr;
   float *dY = nullptr, *dXp = nullptr;
+  float* emb_part = nullptr;              // embedding-adjoint partial sums
 
   // BF16 mode
-  __nv_bfloat16* Pb = nullptr;   // row-major weight copies
-  __nv_bfloat16* PbT = nullptr;  // transposed weight copies
-  __nv_bfloat16 *xa = nullptr, *xaT = nullptr, *xb = nullptr, *xbT = nullptr;  // activation operand copies
-  TcPlan tc;                     // tensor maps and tile choices of every tcgen05 GEMM
+  __nv_bfloat16* Pb = nullptr;   // row-major weight copies (flat layout of P)
+  __nv_bfloat16* PbT = nullptr;  // transposed weight copies (same offsets)
+  TransposeTile* tiles = nullptr;
+  int ntiles = 0;
+  BlockBf16 bb[kMaxBlocks] = {};
+  __nv_bfloat16 *Slte_b = nullptr, *Slte_bT = nullptr;    // LTE-down input copies
+  __nv_bfloat16 *Shead_b = nullptr, *Shead_bT = nullptr;  // head input copies
+  __nv_bfloat16 *Yb = nullptr, *YbT = nullptr;
+  __nv_bfloat16 *dzb = nullptr, *dzbT = nullptr;
+  float* dLte = nullptr;                                   // gradient w.r.t. the LTE-up output
+  __nv_bfloat16 *dLteb = nullptr, *dLtebT = nullptr;
+  __nv_bfloat16 *dXpb = nullptr, *dXpbT = nullptr;
+  float* dh0 = nullptr;                                    // gradient w.r.t. the embedding output
+  TcPlan tcp;
+  cudaStream_t side = nullptr;                             // dW GEMMs and column sums
+  static constexpr int kForks = 4 * kMaxBlocks + 8;
+  cudaEvent_t fork[kForks] = {};
+  cudaEvent_t join_ev = nullptr;
+  cudaEvent_t tr_ev = nullptr;                             // transposed weight copies ready
+  bool emb_in_adam = false;                                // dE left to Adam this step
 
-  // FDM kernel timing (optional)
-  cudaEvent_t ev_fdm[4] = {};
+  // FDM kernel timing (optional): forward [0,1], adjoint [2,3], split Adam [4,5]
+  cudaEvent_t ev_fdm[6] = {};
   bool timing = false;
 
   ~Model();
@@ -91,17 +110,24 @@ class Model {
  private:
   void* arena_ = nullptr;
   size_t arena_bytes_ = 0;
+  int nfork_ = 0;
+  // FP32 path
   int block_fwd(int j, const float* Xin, float* Xout, cudaStream_t st);
-  int block_bwd(int j, const float* dOut, const float* Xin, float* dXnew, cudaStream_t st);
-  // GEMM dispatch: FP32 SIMT or BF16 tcgen05 by precision. `site` names a
-  // tensor-map slot of the BF16 plan.
-  int linear_fwd(int site, const float* X, int rows, int in, size_t w_off, size_t b_off, int out,
-                 const float* resid, float* Y, cudaStream_t st);
-  int linear_dx(int site, const float* dOut, int rows, int out, size_t w_off, int in, float* dX,
-                cudaStream_t st);
-  int linear_dw(int site, const float* dOut, int rows, int out, const float* X, int in, size_t w_off,
-                cudaStream_t st);
+  int block_bwd(int j, const float* dOut, float* dXnew, cudaStream_t st);
+  int forward_f32(const StepIO& io, cudaStream_t st);
+  int backward_f32(const StepIO& io, cudaStream_t st);
+  int linear_fwd(const float* X, int rows, int in, size_t w_off, size_t b_off, int out, const float* resid, float* Yo,
+                 cudaStream_t st);
+  int linear_dx(const float* dOut, int rows, int out, size_t w_off, int in, float* dX, cudaStream_t st);
+  int linear_dw(const float* dOut, int rows, int out, const float* X, int in, size_t w_off, cudaStream_t st);
+  // BF16 path
+  int forward_bf16(const StepIO& io, cudaStream_t st);
+  int backward_bf16(const StepIO& io, cudaStream_t st);
   int build_tc_plan();
+  int run_tc(int site, cudaStream_t st);
+  int fork_side(cudaStream_t st);  // the side stream waits for the work issued so far on st
+  int fdm_fwd_call(cudaStream_t st);
+  int fdm_bwd_call(const StepIO& io, cudaStream_t st);
 };
 
 }  // namespace edpc

@@ -7,12 +7,15 @@
 // columns tx + 16j), operands staged through shared memory in [k][m] / [k][n]
 // order with coalesced global loads for either operand layout.
 #include "kernels.cuh"
+#include "launch.cuh"
 
 namespace edpc {
 
 template <bool AK, bool BK, int EPI>
 __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmF32 g) {
   constexpr int BM = 64, BN = 64, BKT = 16;
+  pdl_wait();
+  pdl_launch();
   __shared__ float As[BKT][BM + 4];
   __shared__ float Bs[BKT][BN + 4];
   const int tid = threadIdx.x;
@@ -87,11 +90,10 @@ __global__ void __launch_bounds__(256) gemm_f32_kernel(GemmF32 g) {
 template <bool AK, bool BK>
 static cudaError_t dispatch_epi(const GemmF32& g, dim3 grid, cudaStream_t st) {
   switch (g.epi) {
-    case EPI_STORE: gemm_f32_kernel<AK, BK, EPI_STORE><<<grid, 256, 0, st>>>(g); break;
-    case EPI_BIAS: gemm_f32_kernel<AK, BK, EPI_BIAS><<<grid, 256, 0, st>>>(g); break;
-    default: gemm_f32_kernel<AK, BK, EPI_BIAS_RESID><<<grid, 256, 0, st>>>(g); break;
+    case EPI_STORE: return launch_k(gemm_f32_kernel<AK, BK, EPI_STORE>, grid, dim3(256), 0, st, g);
+    case EPI_BIAS: return launch_k(gemm_f32_kernel<AK, BK, EPI_BIAS>, grid, dim3(256), 0, st, g);
+    default: return launch_k(gemm_f32_kernel<AK, BK, EPI_BIAS_RESID>, grid, dim3(256), 0, st, g);
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_gemm_f32(const GemmF32& g, cudaStream_t st) {

@@ -8,8 +8,10 @@
 //                      back to its "empty" barrier;
 //   warp 2             allocates / frees the TMEM columns;
 //   warps 0-3          drain TMEM with tcgen05.ld (warp w owns lanes 32w..32w+31,
-//                      i.e. tile rows) and apply the bias / residual epilogue.
+//                      i.e. tile rows) and run the fused epilogue.
 // The MMA order over K is fixed, so results are deterministic.
+// Barrier set-up, TMEM allocation and tensor-map prefetch run before the
+// programmatic-dependent-launch wait, overlapping the previous kernel's tail.
 // Every mbarrier wait is bounded; on expiry the kernel records kErrTcTimeout,
 // stops waiting, frees its TMEM and returns.
 #include <cudaTypedefs.h>
@@ -18,13 +20,34 @@
 
 #include "gemm_tc.cuh"
 #include "kernels.cuh"
+#include "launch.cuh"
 
 namespace edpc {
 
 namespace {
 
-constexpr int BM = 128, BK = 64, STAGES = 4;
+constexpr int BM = 128, BK = 64;
+// Pipeline depth: enough stages to hold the whole K panel in flight for the
+// small-N tiles (8 x 20-24 KB), 4 for 128-wide tiles.
+template <int BN>
+constexpr int stages_for() { return BN <= 64 ? 8 : 4; }
 constexpr uint32_t kSpinLimit = 1u << 26;
+
+struct TcEpi {
+  int M, N, K, H, k;
+  float* C;
+  int ldc;
+  __nv_bfloat16* Cb;
+  int ldcb;
+  __nv_bfloat16* CbT;
+  int ldct;
+  const float* bias;
+  const float* R;
+  int ldr;
+  const float* Aux;
+  int ldaux;
+  int* err;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -100,7 +123,8 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
       "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
@@ -110,21 +134,105 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_f(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+// Loads 32 consecutive FP32 values of one row (vectorised when in range and aligned).
+__device__ __forceinline__ void load_row32(const float* src, int n0, int N, float (&v)[32]) {
+  if (n0 + 32 <= N && ((reinterpret_cast<uintptr_t>(src + n0) & 15) == 0)) {
+#pragma unroll
+    for (int j = 0; j < 32; j += 4) {
+      float4 q = *reinterpret_cast<const float4*>(src + n0 + j);
+      v[j] = q.x;
+      v[j + 1] = q.y;
+      v[j + 2] = q.z;
+      v[j + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) v[j] = (n0 + j < N) ? src[n0 + j] : 0.f;
+  }
+}
+
+// Stores 32 consecutive values of one row as FP32 and/or BF16 (vectorised when
+// the whole chunk is in range and aligned).
+__device__ __forceinline__ void store_row32(const float (&v)[32], bool rok, int n0, int N, float* crow,
+                                            __nv_bfloat16* cbrow) {
+  if (!rok) return;
+  const bool full = n0 + 32 <= N;
+  if (crow) {
+    float* p = crow + n0;
+    if (full && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
+#pragma unroll
+      for (int j = 0; j < 32; j += 4) *reinterpret_cast<float4*>(p + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (n0 + j < N) p[j] = v[j];
+    }
+  }
+  if (cbrow) {
+    __nv_bfloat16* p = cbrow + n0;
+    if (full && ((reinterpret_cast<uintptr_t>(p) & 15) == 0)) {
+#pragma unroll
+      for (int j = 0; j < 32; j += 8) {
+        __align__(16) __nv_bfloat162 h[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(v[j + 2 * q], v[j + 2 * q + 1]);
+        *reinterpret_cast<uint4*>(p + j) = *reinterpret_cast<const uint4*>(h);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        if (n0 + j < N) p[j] = __float2bfloat16_rn(v[j]);
+    }
+  }
+}
+
+// Transposed BF16 store of a 128-row x 32-column chunk: every thread puts its
+// row into shared memory (column-major), then the CTA writes each column's 128
+// rows as 16-byte runs to CT[(n0 + c) * ldct + m0 + r]. Columns at or beyond N
+// and 8-row runs at or beyond ldct are skipped. CTA-collective.
+__device__ __forceinline__ void store_T32(const float (&v)[32], __nv_bfloat16* sT, int m0, int n0, int N,
+                                          __nv_bfloat16* CT, int ldct) {
+  const int r = threadIdx.x;  // tile row
+#pragma unroll
+  for (int c = 0; c < 32; ++c) sT[c * 128 + r] = __float2bfloat16_rn(v[c]);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 32 * 16; idx += 128) {
+    const int c = idx >> 4, seg = idx & 15;
+    const int row0 = m0 + seg * 8;
+    if (n0 + c < N && row0 + 8 <= ldct)
+      *reinterpret_cast<uint4*>(CT + (size_t)(n0 + c) * ldct + row0) =
+          *reinterpret_cast<const uint4*>(sT + c * 128 + seg * 8);
+  }
+  __syncthreads();
+}
+
+template <int BN>
+constexpr int tmem_cols() {
+  return BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
 }
 
 template <int BN>
 constexpr size_t smem_bytes() {
-  return 1024 /*alignment slack*/ + (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 256;
+  return 1024 /*alignment slack*/ + (size_t)stages_for<BN>() * (BM * BK * 2 + BN * BK * 2) + 256;
 }
 
-template <int BN, int EPI>
+template <int BN, int MODE, int KB>
 __global__ void __launch_bounds__(128, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int M, int N,
-                   int K, float* __restrict__ C, int ldc, const float* __restrict__ bias,
-                   const float* __restrict__ R, int ldr, int* err) {
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcEpi e) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  constexpr int STAGES = stages_for<BN>();
   constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  constexpr int SECTIONS = (MODE == TC_BRANCH) ? BN / 32 : 1;
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
   uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
@@ -134,8 +242,11 @@ __global__ void __launch_bounds__(128, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int nk = (K + BK - 1) / BK;
+  const int m0 = blockIdx.y * BM;
+  // N offset of the tile: in TC_BRANCH mode a tile covers hidden units
+  // [32*bx, 32*bx + 32) of every branch.
+  const int n0 = (MODE == TC_BRANCH) ? blockIdx.x * 32 : blockIdx.x * BN;
+  const int nk = (e.K + BK - 1) / BK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -150,7 +261,7 @@ __global__ void __launch_bounds__(128, 1)
   }
   if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                 "r"((uint32_t)BN));
+                 "r"((uint32_t)tmem_cols<BN>()));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   tc_fence_before();
@@ -158,15 +269,39 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
+  // B (weights, or activations of the forward pass) was written at least two
+  // kernels earlier, so its first tiles can be fetched before the
+  // programmatic-dependent-launch wait; A comes from the previous kernel.
+  auto load_b = [&](int kb, int s) {
+    if (MODE == TC_BRANCH) {
+#pragma unroll
+      for (int i = 0; i < SECTIONS; ++i)
+        tma_load_2d(sB + s * B_BYTES + i * (32 * BK * 2), &tb, kb * BK, i * e.H + n0, &full[s]);
+    } else {
+      tma_load_2d(sB + s * B_BYTES, &tb, kb * BK, n0, &full[s]);
+    }
+  };
+  const int npre = nk < STAGES ? nk : STAGES;
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < npre; ++kb) {
+      mbar_expect_tx(&full[kb], A_BYTES + B_BYTES);
+      load_b(kb, kb);
+    }
+  }
+  pdl_wait();
+  pdl_launch();
+
   if (warp == 0 && lane == 0) {
     // TMA producer
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
-      mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+      if (kb >= STAGES) {
+        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+        mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
+        load_b(kb, s);
+      }
       tma_load_2d(sA + s * A_BYTES, &ta, kb * BK, m0, &full[s]);
-      tma_load_2d(sB + s * B_BYTES, &tb, kb * BK, n0, &full[s]);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -188,33 +323,101 @@ __global__ void __launch_bounds__(128, 1)
   }
   __syncwarp();
 
-  // Epilogue: thread (warp w, lane l) owns tile row 32w + l.
-  // CTA-uniform result: the TMEM loads below are warp-collective (.sync.aligned).
+  // Epilogue: thread (warp w, lane l) owns tile row 32w + l. The TMEM loads are
+  // warp-collective, so the wait result is made CTA-uniform first.
   const bool ok = __syncthreads_and(mbar_wait(done, 0, abort_flag) ? 1 : 0) != 0;
   tc_fence_after();
   const int row = m0 + warp * 32 + lane;
+  const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+  // The pipeline's A stages are idle now: reuse them to stage transposed stores.
+  __nv_bfloat16* sT = reinterpret_cast<__nv_bfloat16*>(sA);
+  const bool rok = row < e.M;
   if (ok) {
+    if (MODE == TC_PLAIN) {
 #pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      if (row < M) {
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float v[32];
+        tmem_ld32(trow + (uint32_t)c0, v);
         const int nb = n0 + c0;
-        float* crow = C + (size_t)row * ldc;
+        if (e.bias) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += (nb + j < e.N) ? e.bias[nb + j] : 0.f;
+        }
+        if (e.R && rok) {
+          float r[32];
+          load_row32(e.R + (size_t)row * e.ldr, nb, e.N, r);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] += r[j];
+        }
+        store_row32(v, rok, nb, e.N, e.C ? e.C + (size_t)row * e.ldc : nullptr,
+                    e.Cb ? e.Cb + (size_t)row * e.ldcb : nullptr);
+        if (e.CbT) store_T32(v, sT, m0, nb, e.N, e.CbT, e.ldct);
+      }
+    } else if (MODE == TC_BRANCH) {
+      // X_i for the tile's 32 hidden units h = n0 + j, then G = GELU(prod X_i).
+      float g[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) g[j] = 1.f;
+#pragma unroll 1
+      for (int i = 0; i < SECTIONS; ++i) {
+        float v[32];
+        tmem_ld32(trow + (uint32_t)(i * 32), v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int n = nb + j;
-          if (n < N) {
-            float v = __uint_as_float(r[j]);
-            if (EPI >= EPI_BIAS) v += bias[n];
-            if (EPI == EPI_BIAS_RESID) v += R[(size_t)row * ldr + n];
-            crow[n] = v;
+          const int h = n0 + j;
+          if (h < e.H) v[j] += e.bias[i * e.H + h];
+          g[j] *= v[j];
+        }
+        // X_i -> C[row][i*H + h] (FP32, kept for the adjoint)
+        store_row32(v, rok, n0, e.H, e.C + (size_t)row * e.ldc + i * e.H, nullptr);
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) g[j] = gelu_f(g[j]);
+      store_row32(g, rok, n0, e.H, nullptr, e.Cb + (size_t)row * e.ldcb);
+      store_T32(g, sT, m0, n0, e.H, e.CbT, e.ldct);
+    } else {
+      // TC_BRANCH_BWD: dG tile of hidden units [n0, n0 + BN).
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        float dg[32];
+        tmem_ld32(trow + (uint32_t)c0, dg);
+        const int hb = n0 + c0;
+        float xs[KB][32];
+        float xf[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) xf[j] = 1.f;
+#pragma unroll
+        for (int i = 0; i < KB; ++i) {
+          if (rok) {
+            load_row32(e.Aux + (size_t)row * e.ldaux + i * e.H, hb, e.H, xs[i]);
+          } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j) xs[i][j] = 0.f;
           }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) xf[j] *= xs[i][j];
+        }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) dg[j] *= gelu_grad_f(xf[j]);
+#pragma unroll
+        for (int i = 0; i < KB; ++i) {
+          float dd[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float o = 1.f;
+#pragma unroll
+            for (int l = 0; l < KB; ++l)
+              if (l != i) o *= xs[l][j];
+            dd[j] = dg[j] * o;
+          }
+          const int colb = i * e.H;
+          store_row32(dd, rok, hb, e.H, e.C + (size_t)row * e.ldc + colb, e.Cb + (size_t)row * e.ldcb + colb);
+          store_T32(dd, sT, m0, colb + hb, colb + e.H, e.CbT, e.ldct);
         }
       }
     }
   }
-  if (!ok && threadIdx.x == 0 && err) atomicOr(err, kErrTcTimeout);
+  if (!ok && threadIdx.x == 0 && e.err) atomicOr(e.err, kErrTcTimeout);
   tc_fence_before();
   __syncthreads();
   if (*abort_flag && threadIdx.x == 0) {
@@ -226,31 +429,24 @@ __global__ void __launch_bounds__(128, 1)
   }
   if (warp == 2) {
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"((uint32_t)tmem_cols<BN>()));
   }
 }
 
-template <int BN, int EPI>
-cudaError_t launch_bn_epi(const TcGemm& g, cudaStream_t st) {
-  auto k = gemm_tc_kernel<BN, EPI>;
+template <int BN, int MODE, int KB = 1>
+cudaError_t launch_bn_mode(const TcGemm& g, cudaStream_t st) {
+  auto k = gemm_tc_kernel<BN, MODE, KB>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
     attr_err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<BN>());
   });
   if (attr_err != cudaSuccess) return attr_err;
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
-  k<<<grid, 128, smem_bytes<BN>(), st>>>(g.ta, g.tb, g.M, g.N, g.K, g.C, g.ldc, g.bias, g.R, g.ldr, g.err);
-  return cudaGetLastError();
-}
-
-template <int BN>
-cudaError_t launch_bn(const TcGemm& g, cudaStream_t st) {
-  switch (g.epi) {
-    case EPI_STORE: return launch_bn_epi<BN, EPI_STORE>(g, st);
-    case EPI_BIAS: return launch_bn_epi<BN, EPI_BIAS>(g, st);
-    default: return launch_bn_epi<BN, EPI_BIAS_RESID>(g, st);
-  }
+  TcEpi e{g.M, g.N, g.K, g.H, g.k, g.C, g.ldc, g.Cb, g.ldcb, g.CbT, g.ldct, g.bias, g.R, g.ldr, g.Aux, g.ldaux, g.err};
+  const int ntile = (MODE == TC_BRANCH) ? (g.H + 31) / 32 : (g.N + BN - 1) / BN;
+  dim3 grid(ntile, (g.M + BM - 1) / BM);
+  return launch_k(k, grid, dim3(128), smem_bytes<BN>(), st, g.ta, g.tb, e);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -286,11 +482,31 @@ int make_tmap_bf16(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t co
 }
 
 cudaError_t launch_gemm_tc(const TcGemm& g, cudaStream_t st) {
-  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  // The kernel's B tile (and the expected TMA byte count) must match the box
+  // the tensor map was encoded with; refuse any mismatch before launching.
+  if (g.mode == TC_BRANCH) {
+    if (g.box_b != 32 || g.k < 1 || g.k > 3) return cudaErrorInvalidValue;
+    switch (g.k) {
+      case 1: return launch_bn_mode<32, TC_BRANCH>(g, st);
+      case 2: return launch_bn_mode<64, TC_BRANCH>(g, st);
+      default: return launch_bn_mode<96, TC_BRANCH>(g, st);
+    }
+  }
+  if (g.box_b != g.bn) return cudaErrorInvalidValue;
+  if (g.mode == TC_BRANCH_BWD) {
+    if (g.bn != 32 || g.k < 1 || g.k > 3) return cudaErrorInvalidValue;
+    switch (g.k) {
+      case 1: return launch_bn_mode<32, TC_BRANCH_BWD, 1>(g, st);
+      case 2: return launch_bn_mode<32, TC_BRANCH_BWD, 2>(g, st);
+      default: return launch_bn_mode<32, TC_BRANCH_BWD, 3>(g, st);
+    }
+  }
   switch (g.bn) {
-    case 64: return launch_bn<64>(g, st);
-    case 128: return launch_bn<128>(g, st);
-    default: return launch_bn<256>(g, st);
+    case 32: return launch_bn_mode<32, TC_PLAIN>(g, st);
+    case 64: return launch_bn_mode<64, TC_PLAIN>(g, st);
+    case 128: return launch_bn_mode<128, TC_PLAIN>(g, st);
+    default: return cudaErrorInvalidValue;
   }
 }
 

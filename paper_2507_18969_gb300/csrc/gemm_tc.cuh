@@ -8,19 +8,39 @@
 
 namespace edpc {
 
-// C[m][n] = sum_k A[m][k] B[n][k] (+ bias[n]) (+ R[m][n]); A is M x K and B is
-// N x K, both BF16 and K-contiguous; accumulation is FP32 in TMEM.
+// Epilogue modes.
+//   TC_PLAIN     v = acc (+ bias[n]) (+ R[m][n]); writes C (FP32), Cb (BF16,
+//                row-major) and CbT (BF16, transposed [n][m]) when non-null.
+//   TC_BRANCH    MBRB Eqs. 10-12: the N tile holds the same 32 hidden units of
+//                each of the k branches (B is loaded in k sections of 32 rows).
+//                X_i = acc_i + bias[i*H + h] is stored to C (FP32, [m][i*H+h]);
+//                G = GELU(prod_i X_i) goes to Cb ([m][h]) and CbT ([h][m]).
+//   TC_BRANCH_BWD adjoint of Eqs. 11-12 on dG = acc: with X_i read from Aux
+//                ([m][i*H+h]), dX_i = dG * GELU'(prod X) * prod_{l!=i} X_l is
+//                stored to C (FP32), Cb (BF16) and CbT (BF16, [i*H+h][m]).
+enum TcMode { TC_PLAIN = 0, TC_BRANCH = 1, TC_BRANCH_BWD = 2 };
+
+// C[m][n] = sum_k A[m][k] B[n][k] (+ epilogue); A is M x K and B is N x K,
+// both BF16 and K-contiguous; accumulation is FP32 in TMEM.
 struct TcGemm {
   CUtensorMap ta;  // A: box 64 (K) x 128 (M), 128-byte swizzle
-  CUtensorMap tb;  // B: box 64 (K) x bn (N), 128-byte swizzle
+  CUtensorMap tb;  // B: box 64 (K) x bn (N) (TC_BRANCH: 64 x 32 per section)
   int M = 0, N = 0, K = 0;
-  int bn = 64;     // N tile: 64, 128 or 256
+  int bn = 64;     // N tile: 32, 64 or 128 (TC_BRANCH: 32 * k); must equal tb's box rows
+  int box_b = 0;   // rows of tb's box, recorded by the plan (checked at launch)
+  int mode = TC_PLAIN;
+  int H = 0, k = 1;        // TC_BRANCH / TC_BRANCH_BWD: hidden width and branch count
   float* C = nullptr;
   int ldc = 0;
-  int epi = 0;     // Epi of kernels.cuh
+  __nv_bfloat16* Cb = nullptr;
+  int ldcb = 0;
+  __nv_bfloat16* CbT = nullptr;
+  int ldct = 0;
   const float* bias = nullptr;
   const float* R = nullptr;
   int ldr = 0;
+  const float* Aux = nullptr;
+  int ldaux = 0;
   int* err = nullptr;  // set to kErrTcTimeout if a bounded wait expired
 };
 

@@ -5,6 +5,7 @@
 // atomics. So the encoder and the decoder, which launch the same kernels on
 // the same values, compute bit-identical probabilities and CDFs.
 #include "kernels.cuh"
+#include "launch.cuh"
 
 namespace edpc {
 
@@ -22,6 +23,8 @@ __device__ __forceinline__ unsigned long long sm64_mix(unsigned long long z) {
 
 __global__ void init_values_kernel(float* dst, size_t n, unsigned long long seed, int tid, float bound,
                                    size_t start, float fill) {
+  pdl_wait();
+  pdl_launch();
   const unsigned long long G = 0x9E3779B97F4A7C15ull;
   const unsigned long long base = seed + G * ((unsigned long long)tid << 32);
   for (size_t j = blockIdx.x * (size_t)blockDim.x + threadIdx.x; j < n; j += (size_t)gridDim.x * blockDim.x) {
@@ -41,8 +44,7 @@ cudaError_t launch_init_values(float* dst, size_t n, uint64_t seed, int tid, flo
   if (n == 0) return cudaSuccess;
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 32) grid = 152 * 32;
-  init_values_kernel<<<grid, 256, 0, st>>>(dst, n, seed, tid, bound, start, fill);
-  return cudaGetLastError();
+  return launch_k(init_values_kernel, dim3(grid), dim3(256), 0, st, dst, n, seed, tid, bound, start, fill);
 }
 
 // ============================================================================================
@@ -70,6 +72,8 @@ __device__ __forceinline__ int warp_isum(int v) {
 __global__ void embed_kernel(const uint8_t* __restrict__ data, Split sp, const StepCtl* __restrict__ ctl,
                              const float* __restrict__ E, int K, int D, float* __restrict__ X,
                              uint8_t* __restrict__ ctx) {
+  pdl_wait();
+  pdl_launch();
   const int s = blockIdx.x;
   const int F = K * D;
   if (data) {
@@ -86,8 +90,7 @@ __global__ void embed_kernel(const uint8_t* __restrict__ data, Split sp, const S
 
 cudaError_t launch_embed(const uint8_t* data, Split sp, const StepCtl* ctl, const float* E, int b, int K,
                          int D, float* X, uint8_t* ctx, cudaStream_t st) {
-  embed_kernel<<<b, 128, 0, st>>>(data, sp, ctl, E, K, D, X, ctx);
-  return cudaGetLastError();
+  return launch_k(embed_kernel, dim3(b), dim3(128), 0, st, data, sp, ctl, E, K, D, X, ctx);
 }
 
 // ============================================================================================
@@ -96,6 +99,8 @@ cudaError_t launch_embed(const uint8_t* data, Split sp, const StepCtl* ctl, cons
 __global__ void ln_fwd_kernel(const float* __restrict__ X, const float* __restrict__ g,
                               const float* __restrict__ be, float* __restrict__ xhat,
                               float* __restrict__ rstd, float* __restrict__ X0, int b, int F) {
+  pdl_wait();
+  pdl_launch();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= b) return;
@@ -120,8 +125,7 @@ __global__ void ln_fwd_kernel(const float* __restrict__ X, const float* __restri
 
 cudaError_t launch_ln_fwd(const float* X, const float* g, const float* be, float* xhat, float* rstd,
                           float* X0, int b, int F, cudaStream_t st) {
-  ln_fwd_kernel<<<div_up(b, 8), 256, 0, st>>>(X, g, be, xhat, rstd, X0, b, F);
-  return cudaGetLastError();
+  return launch_k(ln_fwd_kernel, dim3(div_up(b, 8)), dim3(256), 0, st, X, g, be, xhat, rstd, X0, b, F);
 }
 
 // ============================================================================================
@@ -133,6 +137,8 @@ __device__ __forceinline__ float gelu_grad_f(float x) {
 }
 
 __global__ void branch_gelu_kernel(const float* __restrict__ A, int b, int H, int k, float* __restrict__ G) {
+  pdl_wait();
+  pdl_launch();
   const size_t n = (size_t)b * H;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     size_t r = e / H, h = e - r * H;
@@ -146,12 +152,13 @@ __global__ void branch_gelu_kernel(const float* __restrict__ A, int b, int H, in
 cudaError_t launch_branch_gelu(const float* A, int b, int H, int k, float* G, cudaStream_t st) {
   size_t n = (size_t)b * H;
   int grid = (int)((n + 255) / 256);
-  branch_gelu_kernel<<<grid, 256, 0, st>>>(A, b, H, k, G);
-  return cudaGetLastError();
+  return launch_k(branch_gelu_kernel, dim3(grid), dim3(256), 0, st, A, b, H, k, G);
 }
 
 __global__ void branch_gelu_bwd_kernel(const float* __restrict__ dG, const float* __restrict__ A, int b, int H,
                                        int k, float* __restrict__ dA) {
+  pdl_wait();
+  pdl_launch();
   const size_t n = (size_t)b * H;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     size_t r = e / H, h = e - r * H;
@@ -173,8 +180,7 @@ cudaError_t launch_branch_gelu_bwd(const float* dG, const float* A, int b, int H
                                    cudaStream_t st) {
   size_t n = (size_t)b * H;
   int grid = (int)((n + 255) / 256);
-  branch_gelu_bwd_kernel<<<grid, 256, 0, st>>>(dG, A, b, H, k, dA);
-  return cudaGetLastError();
+  return launch_k(branch_gelu_bwd_kernel, dim3(grid), dim3(256), 0, st, dG, A, b, H, k, dA);
 }
 
 // ============================================================================================
@@ -183,6 +189,8 @@ cudaError_t launch_branch_gelu_bwd(const float* dG, const float* A, int b, int H
 // ============================================================================================
 __global__ void colsum_kernel(const float* __restrict__ X, const float* __restrict__ Y, int rows, int cols,
                               int ld, float* __restrict__ out) {
+  pdl_wait();
+  pdl_launch();
   __shared__ float part[8][33];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = blockIdx.x * 32 + lane;
@@ -206,8 +214,7 @@ __global__ void colsum_kernel(const float* __restrict__ X, const float* __restri
 
 cudaError_t launch_colsum(const float* X, const float* Y, int rows, int cols, int ld, float* out,
                           cudaStream_t st) {
-  colsum_kernel<<<div_up(cols, 32), 256, 0, st>>>(X, Y, rows, cols, ld, out);
-  return cudaGetLastError();
+  return launch_k(colsum_kernel, dim3(div_up(cols, 32)), dim3(256), 0, st, X, Y, rows, cols, ld, out);
 }
 
 // ============================================================================================
@@ -217,6 +224,8 @@ cudaError_t launch_colsum(const float* X, const float* Y, int rows, int cols, in
 __global__ void ln_bwd_kernel(const float* __restrict__ dX0, const float* __restrict__ xhat,
                               const float* __restrict__ rstd, const float* __restrict__ g,
                               const float* __restrict__ dRes, float* __restrict__ dX, int b, int F) {
+  pdl_wait();
+  pdl_launch();
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= b) return;
@@ -238,8 +247,7 @@ __global__ void ln_bwd_kernel(const float* __restrict__ dX0, const float* __rest
 
 cudaError_t launch_ln_bwd(const float* dX0, const float* xhat, const float* rstd, const float* g,
                           const float* dRes, float* dX, int b, int F, cudaStream_t st) {
-  ln_bwd_kernel<<<div_up(b, 8), 256, 0, st>>>(dX0, xhat, rstd, g, dRes, dX, b, F);
-  return cudaGetLastError();
+  return launch_k(ln_bwd_kernel, dim3(div_up(b, 8)), dim3(256), 0, st, dX0, xhat, rstd, g, dRes, dX, b, F);
 }
 
 // ============================================================================================
@@ -247,7 +255,10 @@ cudaError_t launch_ln_bwd(const float* dX0, const float* xhat, const float* rstd
 // threads own 4 consecutive columns and a row group; row groups are added in order.
 // ============================================================================================
 __global__ void __launch_bounds__(256) fdm_fwd_kernel(const float* __restrict__ Xp, const float* __restrict__ U,
-                                                      float* __restrict__ Y, int Fp) {
+                                                      float* __restrict__ Y, int Fp, __nv_bfloat16* Yb,
+                                                      __nv_bfloat16* YbT, int ldT) {
+  pdl_wait();
+  pdl_launch();
   extern __shared__ float sm[];
   float* xs = sm;              // Fp
   float* part = sm + Fp;       // groups x Fp
@@ -278,10 +289,126 @@ __global__ void __launch_bounds__(256) fdm_fwd_kernel(const float* __restrict__ 
     float t = part[j];
     for (int g = 1; g < groups; ++g) t += part[(size_t)g * Fp + j];
     Y[(size_t)s * Fp + j] = t;
+    if (Yb) Yb[(size_t)s * Fp + j] = __float2bfloat16_rn(t);
+    if (YbT) YbT[(size_t)j * ldT + s] = __float2bfloat16_rn(t);
   }
 }
 
-cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int Fp, cudaStream_t st) {
+// Streamed version (F' in {128, 256, 512, 1024}): one CTA per stream pulls U_s
+// through a 3-deep ring of 16 KB TMA bulk copies (consecutive rows are
+// contiguous), so the copy engine keeps ~48 KB per CTA in flight with no
+// per-thread load instructions. Thread t owns columns t, t + NT, ... and sums
+// its rows in increasing i (deterministic, no cross-thread reduction). Every
+// mbarrier wait is bounded; all copies are waited for before the CTA exits.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void bar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)));
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < (1u << 26); ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+template <int FP>
+struct FdmRing {
+  static constexpr int NT = FP < 256 ? FP : 256;     // threads
+  static constexpr int CPT = FP / NT;                 // columns per thread
+  static constexpr int SROWS = 4096 / FP;             // rows per 16 KB stage
+  static constexpr int NST = FP / SROWS;              // stages per stream
+  static constexpr int RING = NST < 3 ? NST : 3;
+  static constexpr size_t kSmem = (size_t)RING * 16384 + (size_t)FP * 4 + 64;
+};
+
+template <int FP>
+__global__ void __launch_bounds__(FdmRing<FP>::NT)
+    fdm_fwd_ring_kernel(const float* __restrict__ Xp, const float* __restrict__ U, float* __restrict__ Y,
+                        __nv_bfloat16* Yb, __nv_bfloat16* YbT, int ldT, int* err) {
+  using R = FdmRing<FP>;
+  extern __shared__ __align__(128) float smf[];
+  float* buf = smf;                        // RING x 16 KB
+  float* xs = smf + (size_t)R::RING * 4096;  // FP
+  uint64_t* bars = reinterpret_cast<uint64_t*>(xs + FP);
+  const int s = blockIdx.x, t = threadIdx.x;
+  if (t == 0) {
+    for (int b = 0; b < R::RING; ++b) bar_init(&bars[b]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pdl_wait();
+  pdl_launch();
+  const float* Us = U + (size_t)s * FP * FP;
+  if (t == 0)
+    for (int b = 0; b < R::RING; ++b) bulk_load(buf + (size_t)b * 4096, Us + (size_t)b * 4096, 16384u, &bars[b]);
+  for (int i = t; i < FP; i += R::NT) xs[i] = Xp[(size_t)s * FP + i];
+  __syncthreads();
+  float acc[R::CPT];
+#pragma unroll
+  for (int j = 0; j < R::CPT; ++j) acc[j] = 0.f;
+  bool ok = true;
+  for (int st = 0; st < R::NST; ++st) {
+    const int b = st % R::RING;
+    ok = bar_wait(&bars[b], (uint32_t)(st / R::RING) & 1u) && ok;
+    const float* u = buf + (size_t)b * 4096;
+    const float* xv = xs + st * R::SROWS;
+#pragma unroll
+    for (int r = 0; r < R::SROWS; ++r) {
+      const float xr = xv[r];
+#pragma unroll
+      for (int j = 0; j < R::CPT; ++j) acc[j] += xr * u[r * FP + t + j * R::NT];
+    }
+    __syncthreads();  // stage b consumed by every thread
+    if (t == 0 && st + R::RING < R::NST)
+      bulk_load(buf + (size_t)b * 4096, Us + (size_t)(st + R::RING) * 4096, 16384u, &bars[b]);
+  }
+  if (!ok && t == 0 && err) atomicOr(err, 8);
+#pragma unroll
+  for (int j = 0; j < R::CPT; ++j) {
+    const int c = t + j * R::NT;
+    Y[(size_t)s * FP + c] = acc[j];
+    if (Yb) Yb[(size_t)s * FP + c] = __float2bfloat16_rn(acc[j]);
+    if (YbT) YbT[(size_t)c * ldT + s] = __float2bfloat16_rn(acc[j]);
+  }
+}
+
+template <int FP>
+cudaError_t launch_fdm_fwd_ring(const float* Xp, const float* U, float* Y, int b, __nv_bfloat16* Yb,
+                                __nv_bfloat16* YbT, int ldT, int* err, cudaStream_t st) {
+  const size_t smem = FdmRing<FP>::kSmem;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(fdm_fwd_ring_kernel<FP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_k(fdm_fwd_ring_kernel<FP>, dim3(b), dim3(FdmRing<FP>::NT), smem, st, Xp, U, Y, Yb, YbT, ldT, err);
+}
+
+cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int Fp, cudaStream_t st,
+                           __nv_bfloat16* Yb, __nv_bfloat16* YbT, int ldT, int* err) {
+  switch (Fp) {
+    case 128: return launch_fdm_fwd_ring<128>(Xp, U, Y, b, Yb, YbT, ldT, err, st);
+    case 256: return launch_fdm_fwd_ring<256>(Xp, U, Y, b, Yb, YbT, ldT, err, st);
+    case 512: return launch_fdm_fwd_ring<512>(Xp, U, Y, b, Yb, YbT, ldT, err, st);
+    case 1024: return launch_fdm_fwd_ring<1024>(Xp, U, Y, b, Yb, YbT, ldT, err, st);
+    default: break;
+  }
   const int cols4 = Fp / 4;
   const int threads = cols4 >= 256 ? cols4 : (256 / cols4) * cols4;
   const int groups = threads / cols4;
@@ -290,8 +417,7 @@ cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int
     cudaError_t e = cudaFuncSetAttribute(fdm_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  fdm_fwd_kernel<<<b, threads, smem, st>>>(Xp, U, Y, Fp);
-  return cudaGetLastError();
+  return launch_k(fdm_fwd_kernel, dim3(b), dim3(threads), smem, st, Xp, U, Y, Fp, Yb, YbT, ldT);
 }
 
 // ============================================================================================
@@ -311,8 +437,16 @@ __device__ __forceinline__ void adam1(float& p, float& m, float& v, float g, flo
   p = p - lr * mh / (sqrtf(vh) + kAdamEps);
 }
 
+__device__ __forceinline__ void store_dxp(const FdmBwdArgs& a, int s, int i, float v) {
+  a.dXp[(size_t)s * a.Fp + i] = v;
+  if (a.dXpb) a.dXpb[(size_t)s * a.Fp + i] = __float2bfloat16_rn(v);
+  if (a.dXpbT) a.dXpbT[(size_t)i * a.ldT + s] = __float2bfloat16_rn(v);
+}
+
 template <int NCH>  // float4 chunks per lane per row: Fp = 128 * NCH
 __global__ void __launch_bounds__(256) fdm_bwd_kernel(FdmBwdArgs a) {
+  pdl_wait();
+  pdl_launch();
   const int s = blockIdx.y;
   const int Fp = a.Fp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -322,7 +456,7 @@ __global__ void __launch_bounds__(256) fdm_bwd_kernel(FdmBwdArgs a) {
   if (!act) {
     // dy is zero for an inactive stream, so dx' = 0 and its FDM state is left as is.
     for (int r = warp; r < kFdmRowsPerCta; r += 8)
-      if (lane == 0 && row0 + r < Fp) a.dXp[(size_t)s * Fp + row0 + r] = 0.f;
+      if (lane == 0 && row0 + r < Fp) store_dxp(a, s, row0 + r, 0.f);
     if (!a.update) {
       for (int r = warp; r < kFdmRowsPerCta; r += 8) {
         int i = row0 + r;
@@ -381,12 +515,14 @@ __global__ void __launch_bounds__(256) fdm_bwd_kernel(FdmBwdArgs a) {
       }
     }
     dot = warp_sum(dot);
-    if (lane == 0) a.dXp[(size_t)s * Fp + i] = dot;
+    if (lane == 0) store_dxp(a, s, i, dot);
   }
 }
 
 // Generic fallback for F' not a multiple of 128: one element per lane step.
 __global__ void __launch_bounds__(256) fdm_bwd_generic_kernel(FdmBwdArgs a) {
+  pdl_wait();
+  pdl_launch();
   const int s = blockIdx.y;
   const int Fp = a.Fp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -398,7 +534,7 @@ __global__ void __launch_bounds__(256) fdm_bwd_generic_kernel(FdmBwdArgs a) {
     if (i >= Fp) break;
     const size_t ro = ((size_t)s * Fp + i) * Fp;
     if (!act) {
-      if (lane == 0) a.dXp[(size_t)s * Fp + i] = 0.f;
+      if (lane == 0) store_dxp(a, s, i, 0.f);
       if (!a.update)
         for (int j = lane; j < Fp; j += 32) a.gU[ro + j] = 0.f;
       continue;
@@ -420,79 +556,159 @@ __global__ void __launch_bounds__(256) fdm_bwd_generic_kernel(FdmBwdArgs a) {
       }
     }
     dot = warp_sum(dot);
-    if (lane == 0) a.dXp[(size_t)s * Fp + i] = dot;
+    if (lane == 0) store_dxp(a, s, i, dot);
   }
 }
 
 cudaError_t launch_fdm_bwd(const FdmBwdArgs& a, cudaStream_t st) {
   dim3 grid(div_up(a.Fp, kFdmRowsPerCta), a.b);
+  cudaError_t e = cudaSuccess;
   switch (a.Fp) {
-    case 128: fdm_bwd_kernel<1><<<grid, 256, 0, st>>>(a); break;
-    case 256: fdm_bwd_kernel<2><<<grid, 256, 0, st>>>(a); break;
-    case 384: fdm_bwd_kernel<3><<<grid, 256, 0, st>>>(a); break;
-    case 512: fdm_bwd_kernel<4><<<grid, 256, 0, st>>>(a); break;
-    case 1024: fdm_bwd_kernel<8><<<grid, 256, 0, st>>>(a); break;
-    default: fdm_bwd_generic_kernel<<<grid, 256, 0, st>>>(a); break;
+    case 128: e = launch_k(fdm_bwd_kernel<1>, dim3(grid), dim3(256), 0, st, a); break;
+    case 256: e = launch_k(fdm_bwd_kernel<2>, dim3(grid), dim3(256), 0, st, a); break;
+    case 384: e = launch_k(fdm_bwd_kernel<3>, dim3(grid), dim3(256), 0, st, a); break;
+    case 512: e = launch_k(fdm_bwd_kernel<4>, dim3(grid), dim3(256), 0, st, a); break;
+    case 1024: e = launch_k(fdm_bwd_kernel<8>, dim3(grid), dim3(256), 0, st, a); break;
+    default: e = launch_k(fdm_bwd_generic_kernel, dim3(grid), dim3(256), 0, st, a); break;
   }
-  return cudaGetLastError();
+  return e;
 }
 
 // ============================================================================================
-// Embedding backward: scatter-add of dh0 into E's rows, owner-computes per symbol.
-// CTA c scans all b*K positions in order (8 warps over contiguous slices,
-// ballot per 32 positions); partial sums are added in warp order.
+// Embedding backward: scatter-add of dh0 into E's rows, in a fixed order.
+// Stage 1: the b*K positions are cut into chunks of kEmbChunk (one CTA each).
+//   The chunk's positions are sorted by context byte with a stable counting
+//   sort (warp match + per-warp counts, so equal bytes keep position order);
+//   then thread (c, half) sums, in that order, the dh0 rows of byte c for its
+//   half of the D columns -> part[q][c][d]. Work per thread = occurrences of c.
+// Stage 2: dE[c][d] = sum over chunks q of part[q][c][d], in a fixed order.
 // ============================================================================================
-__global__ void embed_bwd_kernel(const uint8_t* __restrict__ ctx, const float* __restrict__ dX, int b, int K,
-                                 int D, float* __restrict__ dE) {
-  __shared__ float part[8][64];
-  const int c = blockIdx.x;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int P = b * K;
-  const int per = (P + 7) / 8;
-  const int p0 = w * per, p1 = min(P, p0 + per);
-  float acc0 = 0.f, acc1 = 0.f;  // d = lane, d = lane + 32
-  for (int base = p0; base < p1; base += 32) {
-    int p = base + lane;
-    bool hit = p < p1 && ctx[p] == c;
-    unsigned m = __ballot_sync(0xffffffffu, hit);
-    while (m) {
-      int l = __ffs(m) - 1;
-      m &= m - 1;
-      int q = base + l;
-      int s = q / K, k = q - s * K;
-      const float* src = dX + (size_t)s * K * D + (size_t)k * D;
-      if (lane < D) acc0 += src[lane];
-      if (lane + 32 < D) acc1 += src[lane + 32];
-    }
-  }
-  part[w][lane] = acc0;
-  part[w][lane + 32] = acc1;
+constexpr int kEmbChunk = 256;  // = threads of stage 1 (one position each)
+
+__global__ void __launch_bounds__(512) embed_bwd_part_kernel(const uint8_t* __restrict__ ctx,
+                                                             const float* __restrict__ dX, int P, int D,
+                                                             float* __restrict__ part) {
+  pdl_wait();
+  pdl_launch();
+  extern __shared__ float sx[];                 // kEmbChunk x D rows of dh0
+  __shared__ int cnt_w[kEmbChunk / 32][256];    // per warp, per byte: occurrences
+  __shared__ int start[256];                    // first sorted slot of each byte
+  __shared__ short order[kEmbChunk];            // positions sorted by byte (stable)
+  const int q = blockIdx.x, tid = threadIdx.x;
+  const int p0 = q * kEmbChunk;
+  const int n = min(kEmbChunk, P - p0);
+  // position p = s*K + k has its D gradient values at dX[p*D .. p*D + D)
+  const float* src = dX + (size_t)p0 * D;
+  for (int i = tid; i < n * D; i += blockDim.x) sx[i] = src[i];
+  for (int i = tid; i < (kEmbChunk / 32) * 256; i += blockDim.x) (&cnt_w[0][0])[i] = 0;
   __syncthreads();
-  if (w == 0) {
-    for (int d = lane; d < D; d += 32) {
-      float t = part[0][d];
-      for (int i = 1; i < 8; ++i) t += part[i][d];
-      dE[(size_t)c * D + d] = t;
-    }
+  const int w = tid >> 5, lane = tid & 31;
+  int key = -1, rank = 0;
+  if (tid < kEmbChunk) {
+    key = tid < n ? (int)ctx[p0 + tid] : 256 + lane;  // padding keys never match a byte
+    const unsigned grp = __match_any_sync(0xffffffffu, key);
+    rank = __popc(grp & ((1u << lane) - 1u));
+    if (key < 256 && rank == 0) cnt_w[w][key] = __popc(grp);
   }
+  __syncthreads();
+  if (tid < 32) {  // exclusive scan over the 256 bytes of the chunk totals (8 per lane)
+    int v[8], run = 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      int tot = 0;
+#pragma unroll
+      for (int ww = 0; ww < kEmbChunk / 32; ++ww) tot += cnt_w[ww][tid * 8 + u];
+      v[u] = run;
+      run += tot;
+    }
+    int incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (tid >= o) incl += y;
+    }
+    const int excl = incl - run;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) start[tid * 8 + u] = excl + v[u];
+  }
+  __syncthreads();
+  if (tid < kEmbChunk && key < 256) {
+    int before = 0;  // occurrences of this byte in earlier warps
+    for (int ww = 0; ww < w; ++ww) before += cnt_w[ww][key];
+    order[start[key] + before + rank] = (short)tid;
+  }
+  __syncthreads();
+  const int c = tid >> 1, half = tid & 1;
+  int tot = 0;
+#pragma unroll
+  for (int ww = 0; ww < kEmbChunk / 32; ++ww) tot += cnt_w[ww][c];
+  const int Dh = (D + 1) / 2, d0 = half * Dh, d1 = min(D, d0 + Dh);
+  float acc[32];
+#pragma unroll
+  for (int t = 0; t < 32; ++t) acc[t] = 0.f;
+  const int j0 = start[c];
+  for (int j = 0; j < tot; ++j) {
+    const float* row = sx + (int)order[j0 + j] * D;
+#pragma unroll
+    for (int t = 0; t < 32; ++t)
+      if (d0 + t < d1) acc[t] += row[d0 + t];
+  }
+  float* out = part + ((size_t)q * 256 + c) * D;
+#pragma unroll
+  for (int t = 0; t < 32; ++t)
+    if (d0 + t < d1) out[d0 + t] = acc[t];
 }
 
-cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE,
-                             cudaStream_t st) {
+// Fixed-order sum of the chunk partials of one embedding-gradient element:
+// chunk q goes to accumulator q % 8, then the 8 are added pairwise.
+__device__ __forceinline__ float emb_grad_sum(const float* __restrict__ part, int nchunks, size_t stride, size_t e) {
+  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int q = 0;
+  for (; q + 8 <= nchunks; q += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) a[u] += part[(size_t)(q + u) * stride + e];
+  }
+  for (int u = 0; q < nchunks; ++q, ++u) a[u] += part[(size_t)q * stride + e];
+  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
+}
+
+__global__ void embed_bwd_sum_kernel(const float* __restrict__ part, int nchunks, int D, float* __restrict__ dE) {
+  pdl_wait();
+  pdl_launch();
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 256 * D) return;
+  dE[e] = emb_grad_sum(part, nchunks, (size_t)256 * D, (size_t)e);
+}
+
+int embed_bwd_chunks(int b, int K) { return (b * K + kEmbChunk - 1) / kEmbChunk; }
+
+cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, float* part,
+                             cudaStream_t st, bool sum) {
   if (D > 64) return cudaErrorInvalidValue;
-  embed_bwd_kernel<<<256, 256, 0, st>>>(ctx, dX, b, K, D, dE);
-  return cudaGetLastError();
+  const int P = b * K, nq = embed_bwd_chunks(b, K);
+  const size_t smem = (size_t)kEmbChunk * D * sizeof(float);  // <= 64 KB for D <= 64
+  if (smem > 48 * 1024) {
+    cudaError_t a = cudaFuncSetAttribute(embed_bwd_part_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (a != cudaSuccess) return a;
+  }
+  cudaError_t e = launch_k(embed_bwd_part_kernel, dim3(nq), dim3(512), smem, st, ctx, dX, P, D, part);
+  if (e != cudaSuccess || !sum) return e;
+  return launch_k(embed_bwd_sum_kernel, dim3(div_up(256 * D, 256)), dim3(256), 0, st, part, nq, D, dE);
 }
 
 // ============================================================================================
 // Adam on the shared parameters (Sec. 4.1: lr 1e-3; beta, eps as documented).
 // ============================================================================================
 __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
-                            float* __restrict__ V, size_t n, const StepCtl* __restrict__ ctl) {
+                            float* __restrict__ V, size_t n, const StepCtl* __restrict__ ctl, EmbGrad eg) {
+  pdl_wait();
+  pdl_launch();
   const StepCtl c = *ctl;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     float p = P[e], m = M[e], v = V[e];
-    adam1(p, m, v, G[e], c.lr, c.bc1, c.bc2);
+    const float gr = (eg.part && e >= eg.off && e < eg.off + eg.n) ? emb_grad_sum(eg.part, eg.nchunks, eg.n, e - eg.off)
+                                                                   : G[e];
+    adam1(p, m, v, gr, c.lr, c.bc1, c.bc2);
     P[e] = p;
     M[e] = m;
     V[e] = v;
@@ -500,17 +716,18 @@ __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, 
 }
 
 cudaError_t launch_adam(float* P, const float* G, float* M, float* V, size_t n, const StepCtl* ctl,
-                        cudaStream_t st) {
+                        cudaStream_t st, EmbGrad eg) {
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
-  adam_kernel<<<grid, 256, 0, st>>>(P, G, M, V, n, ctl);
-  return cudaGetLastError();
+  return launch_k(adam_kernel, dim3(grid), dim3(256), 0, st, P, G, M, V, n, ctl, eg);
 }
 
 // ============================================================================================
 // Step control: advance to the next time index and derive its scalars.
 // ============================================================================================
 __global__ void step_advance_kernel(StepCtl* ctl, Split sp, int K, int ring_slots, int b) {
+  pdl_wait();
+  pdl_launch();
   StepCtl c = *ctl;
   c.i += 1;
   c.t += 1;
@@ -525,8 +742,7 @@ __global__ void step_advance_kernel(StepCtl* ctl, Split sp, int K, int ring_slot
 }
 
 cudaError_t launch_step_advance(StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st) {
-  step_advance_kernel<<<1, 1, 0, st>>>(ctl, sp, K, ring_slots, b);
-  return cudaGetLastError();
+  return launch_k(step_advance_kernel, dim3(1), dim3(1), 0, st, ctl, sp, K, ring_slots, b);
 }
 
 // ============================================================================================
@@ -585,6 +801,8 @@ __device__ __forceinline__ void enc_init(EncState& s) {
 
 __global__ void prefix_encode_kernel(EncState* es, const uint8_t* __restrict__ data, Split sp, int K, int b,
                                      uint8_t* out, const unsigned long long* out_off, const uint32_t* out_cap) {
+  pdl_wait();
+  pdl_launch();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= b) return;
   EncState st;
@@ -598,8 +816,7 @@ __global__ void prefix_encode_kernel(EncState* es, const uint8_t* __restrict__ d
 
 cudaError_t launch_prefix_encode(EncState* es, const uint8_t* data, Split sp, int K, int b, uint8_t* out,
                                  const unsigned long long* out_off, const uint32_t* out_cap, cudaStream_t st) {
-  prefix_encode_kernel<<<div_up(b, 128), 128, 0, st>>>(es, data, sp, K, b, out, out_off, out_cap);
-  return cudaGetLastError();
+  return launch_k(prefix_encode_kernel, dim3(div_up(b, 128)), dim3(128), 0, st, es, data, sp, K, b, out, out_off, out_cap);
 }
 
 // One thread per stream codes `nsteps` consecutive ring slots. Reads of a slot
@@ -607,6 +824,8 @@ cudaError_t launch_prefix_encode(EncState* es, const uint8_t* data, Split sp, in
 __global__ void range_encode_kernel(EncState* es, const uint32_t* __restrict__ ring, int ring_slots, int slot0,
                                     int nsteps, int b, uint8_t* out, const unsigned long long* out_off,
                                     const uint32_t* out_cap) {
+  pdl_wait();
+  pdl_launch();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= b) return;
   EncState st = es[s];
@@ -624,13 +843,14 @@ cudaError_t launch_range_encode(EncState* es, const uint32_t* ring, int ring_slo
                                 uint8_t* out, const unsigned long long* out_off, const uint32_t* out_cap,
                                 cudaStream_t st) {
   if (nsteps <= 0) return cudaSuccess;
-  range_encode_kernel<<<div_up(b, 128), 128, 0, st>>>(es, ring, ring_slots, slot0, nsteps, b, out, out_off,
+  return launch_k(range_encode_kernel, dim3(div_up(b, 128)), dim3(128), 0, st, es, ring, ring_slots, slot0, nsteps, b, out, out_off,
                                                        out_cap);
-  return cudaGetLastError();
 }
 
 __global__ void encode_flush_kernel(EncState* es, int b, uint8_t* out, const unsigned long long* out_off,
                                     const uint32_t* out_cap, uint32_t* out_len) {
+  pdl_wait();
+  pdl_launch();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= b) return;
   EncState st = es[s];
@@ -647,8 +867,7 @@ __global__ void encode_flush_kernel(EncState* es, int b, uint8_t* out, const uns
 
 cudaError_t launch_encode_flush(EncState* es, int b, uint8_t* out, const unsigned long long* out_off,
                                 const uint32_t* out_cap, uint32_t* out_len, cudaStream_t st) {
-  encode_flush_kernel<<<div_up(b, 128), 128, 0, st>>>(es, b, out, out_off, out_cap, out_len);
-  return cudaGetLastError();
+  return launch_k(encode_flush_kernel, dim3(div_up(b, 128)), dim3(128), 0, st, es, b, out, out_off, out_cap, out_len);
 }
 
 __device__ __forceinline__ uint32_t dec_byte(const uint8_t* in, uint32_t len, uint32_t& pos) {
@@ -669,6 +888,8 @@ __device__ __forceinline__ void dec_update(DecState& d, const uint8_t* in, uint3
 
 __global__ void dec_init_kernel(DecState* ds, const uint8_t* bits, const unsigned long long* off,
                                 const uint32_t* len, int b) {
+  pdl_wait();
+  pdl_launch();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= b) return;
   DecState d;
@@ -683,12 +904,13 @@ __global__ void dec_init_kernel(DecState* ds, const uint8_t* bits, const unsigne
 
 cudaError_t launch_dec_init(DecState* ds, const uint8_t* bits, const unsigned long long* off, const uint32_t* len,
                             int b, cudaStream_t st) {
-  dec_init_kernel<<<div_up(b, 128), 128, 0, st>>>(ds, bits, off, len, b);
-  return cudaGetLastError();
+  return launch_k(dec_init_kernel, dim3(div_up(b, 128)), dim3(128), 0, st, ds, bits, off, len, b);
 }
 
 __global__ void prefix_decode_kernel(DecState* ds, const uint8_t* bits, const unsigned long long* off,
                                      const uint32_t* len, Split sp, int K, int b, uint8_t* data) {
+  pdl_wait();
+  pdl_launch();
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= b) return;
   DecState d = ds[s];
@@ -709,8 +931,7 @@ __global__ void prefix_decode_kernel(DecState* ds, const uint8_t* bits, const un
 
 cudaError_t launch_prefix_decode(DecState* ds, const uint8_t* bits, const unsigned long long* off,
                                  const uint32_t* len, Split sp, int K, int b, uint8_t* data, cudaStream_t st) {
-  prefix_decode_kernel<<<div_up(b, 128), 128, 0, st>>>(ds, bits, off, len, sp, K, b, data);
-  return cudaGetLastError();
+  return launch_k(prefix_decode_kernel, dim3(div_up(b, 128)), dim3(128), 0, st, ds, bits, off, len, sp, K, b, data);
 }
 
 // ============================================================================================
@@ -768,103 +989,138 @@ __device__ __forceinline__ void row_cdf(const float (&p)[8], int lane, RowCdf& o
   for (int q = 0; q < 8; ++q) o.cum[q] += excl;
 }
 
-__global__ void head_kernel(HeadArgs a) {
-  const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (s >= a.b) return;
-  const StepCtl c = *a.ctl;
-  const float* z = a.z + (size_t)s * 256 + lane * 8;
-  float zz[8], p[8];
-  float4 z0 = reinterpret_cast<const float4*>(z)[0], z1 = reinterpret_cast<const float4*>(z)[1];
-  zz[0] = z0.x; zz[1] = z0.y; zz[2] = z0.z; zz[3] = z0.w;
-  zz[4] = z1.x; zz[5] = z1.y; zz[6] = z1.z; zz[7] = z1.w;
-  float mx = zz[0];
+// Transposed BF16 store of an [R][cols] tile held in shared memory:
+// YT[c][r0 + r] for r < R, as 16-byte stores (R = 8 or 16).
+template <int R>
+__device__ __forceinline__ void store_tile_T(const __nv_bfloat16* tile, int ld_s, int cols, int r0,
+                                             __nv_bfloat16* YT, int ldT) {
+  for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+    __align__(16) __nv_bfloat16 v[R];
 #pragma unroll
-  for (int q = 1; q < 8; ++q) mx = fmaxf(mx, zz[q]);
-  mx = warp_max(mx);
-  float se = 0.f;
+    for (int r = 0; r < R; ++r) v[r] = tile[r * ld_s + c];
+    uint4* dst = reinterpret_cast<uint4*>(YT + (size_t)c * ldT + r0);
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    p[q] = expf(zz[q] - mx);
-    se += p[q];
+    for (int q = 0; q < R / 8; ++q) dst[q] = reinterpret_cast<const uint4*>(v)[q];
   }
-  se = warp_sum(se);
+}
+
+__global__ void __launch_bounds__(32 * kRowsT) head_kernel(HeadArgs a) {
+  pdl_wait();
+  pdl_launch();
+  __shared__ __nv_bfloat16 tile[kRowsT][256];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * kRowsT + warp;
+  const bool valid = s < a.b;  // warp-uniform
+  const StepCtl c = *a.ctl;
+  float dzv[8];
 #pragma unroll
-  for (int q = 0; q < 8; ++q) p[q] = p[q] / se;
-
-  bool active;
-  if (a.mode == 2)
-    active = a.active[s] != 0;
-  else
-    active = (long long)c.i < a.sp.len(s);
-
-  RowCdf cdf;
-  row_cdf(p, lane, cdf);
-  if (a.freq_out) {
+  for (int q = 0; q < 8; ++q) dzv[q] = 0.f;
+  if (valid) {
+    const float* z = a.z + (size_t)s * 256 + lane * 8;
+    float zz[8], p[8];
+    float4 z0 = reinterpret_cast<const float4*>(z)[0], z1 = reinterpret_cast<const float4*>(z)[1];
+    zz[0] = z0.x; zz[1] = z0.y; zz[2] = z0.z; zz[3] = z0.w;
+    zz[4] = z1.x; zz[5] = z1.y; zz[6] = z1.z; zz[7] = z1.w;
+    float mx = zz[0];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) mx = fmaxf(mx, zz[q]);
+    mx = warp_max(mx);
+    float se = 0.f;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      a.freq_out[(size_t)s * 256 + lane * 8 + q] = cdf.f[q];
-      a.cum_out[(size_t)s * 257 + lane * 8 + q] = cdf.cum[q];
+      p[q] = expf(zz[q] - mx);
+      se += p[q];
     }
-    if (lane == 31) a.cum_out[(size_t)s * 257 + 256] = (uint32_t)kT;
-  }
-
-  int x = -1;
-  if (active) {
-    if (a.mode == 0) {
-      x = a.data[a.sp.off(s) + c.i];
-      uint32_t cx = __shfl_sync(0xffffffffu, cdf.cum[x & 7], x >> 3);
-      uint32_t fx = __shfl_sync(0xffffffffu, cdf.f[x & 7], x >> 3);
-      // (all lanes must take the shuffles with the same source index: x is warp-uniform)
-      if (lane == 0) a.ring[(size_t)c.slot * a.b + s] = cx | ((fx - 1u) << 16);
-    } else if (a.mode == 1) {
-      DecState d;
-      uint32_t target = 0, r = 0;
-      if (lane == 0) {
-        d = a.dec[s];
-        r = d.range >> kTBits;
-        target = d.code / r;
-        if (target > (uint32_t)kT - 1) target = kT - 1;
-      }
-      target = __shfl_sync(0xffffffffu, target, 0);
-      unsigned ball = __ballot_sync(0xffffffffu, cdf.cum[0] <= target);
-      int L = 31 - __clz(ball);
-      int cnt = 0;
+    se = warp_sum(se);
 #pragma unroll
-      for (int q = 0; q < 8; ++q) cnt += (cdf.cum[q] <= target) ? 1 : 0;
-      cnt = __shfl_sync(0xffffffffu, cnt, L);
-      x = L * 8 + cnt - 1;
-      uint32_t cx = __shfl_sync(0xffffffffu, cdf.cum[x & 7], L);
-      uint32_t fx = __shfl_sync(0xffffffffu, cdf.f[x & 7], L);
-      if (lane == 0) {
-        dec_update(d, a.bits + a.bits_off[s], a.bits_len[s], r, cx, fx);
-        a.dec[s] = d;
-        a.data[a.sp.off(s) + c.i] = (uint8_t)x;
+    for (int q = 0; q < 8; ++q) p[q] = p[q] / se;
+
+    bool active;
+    if (a.mode == 2)
+      active = a.active[s] != 0;
+    else
+      active = (long long)c.i < a.sp.len(s);
+
+    RowCdf cdf;
+    row_cdf(p, lane, cdf);
+    if (a.freq_out) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        a.freq_out[(size_t)s * 256 + lane * 8 + q] = cdf.f[q];
+        a.cum_out[(size_t)s * 257 + lane * 8 + q] = cdf.cum[q];
       }
-    } else {
-      x = a.targets[s];
+      if (lane == 31) a.cum_out[(size_t)s * 257 + 256] = (uint32_t)kT;
     }
-  } else if (a.mode == 0 && lane == 0) {
-    a.ring[(size_t)c.slot * a.b + s] = kSkip;
-  }
 
-  float* dz = a.dz + (size_t)s * 256 + lane * 8;
-  float* po = a.p ? a.p + (size_t)s * 256 + lane * 8 : nullptr;
-  const float inv = (a.mode == 2) ? c.inv_bact : c.inv_bact;
+    int x = -1;
+    if (active) {
+      if (a.mode == 0) {
+        x = a.data[a.sp.off(s) + c.i];  // warp-uniform
+        uint32_t cx = __shfl_sync(0xffffffffu, cdf.cum[x & 7], x >> 3);
+        uint32_t fx = __shfl_sync(0xffffffffu, cdf.f[x & 7], x >> 3);
+        if (lane == 0) a.ring[(size_t)c.slot * a.b + s] = cx | ((fx - 1u) << 16);
+      } else if (a.mode == 1) {
+        DecState d;
+        uint32_t target = 0, r = 0;
+        if (lane == 0) {
+          d = a.dec[s];
+          r = d.range >> kTBits;
+          target = d.code / r;
+          if (target > (uint32_t)kT - 1) target = kT - 1;
+        }
+        target = __shfl_sync(0xffffffffu, target, 0);
+        unsigned ball = __ballot_sync(0xffffffffu, cdf.cum[0] <= target);
+        int L = 31 - __clz(ball);
+        int cnt = 0;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    int j = lane * 8 + q;
-    dz[q] = active ? (p[q] - (j == x ? 1.0f : 0.0f)) * inv : 0.f;
-    if (po) po[q] = p[q];
+        for (int q = 0; q < 8; ++q) cnt += (cdf.cum[q] <= target) ? 1 : 0;
+        cnt = __shfl_sync(0xffffffffu, cnt, L);
+        x = L * 8 + cnt - 1;
+        uint32_t cx = __shfl_sync(0xffffffffu, cdf.cum[x & 7], L);
+        uint32_t fx = __shfl_sync(0xffffffffu, cdf.f[x & 7], L);
+        if (lane == 0) {
+          dec_update(d, a.bits + a.bits_off[s], a.bits_len[s], r, cx, fx);
+          a.dec[s] = d;
+          a.data[a.sp.off(s) + c.i] = (uint8_t)x;
+        }
+      } else {
+        x = a.targets[s];
+      }
+    } else if (a.mode == 0 && lane == 0) {
+      a.ring[(size_t)c.slot * a.b + s] = kSkip;
+    }
+
+    float* dz = a.dz + (size_t)s * 256 + lane * 8;
+    float* po = a.p ? a.p + (size_t)s * 256 + lane * 8 : nullptr;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int j = lane * 8 + q;
+      dzv[q] = active ? (p[q] - (j == x ? 1.0f : 0.0f)) * c.inv_bact : 0.f;
+      dz[q] = dzv[q];
+      if (po) po[q] = p[q];
+    }
+    if (a.dzb) {
+      __align__(16) __nv_bfloat16 hb[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) hb[q] = __float2bfloat16_rn(dzv[q]);
+      *reinterpret_cast<uint4*>(a.dzb + (size_t)s * 256 + lane * 8) = *reinterpret_cast<const uint4*>(hb);
+    }
+  }
+  if (a.dzbT) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) tile[warp][lane * 8 + q] = __float2bfloat16_rn(dzv[q]);
+    __syncthreads();
+    store_tile_T<kRowsT>(&tile[0][0], 256, 256, blockIdx.x * kRowsT, a.dzbT, a.ldT);
   }
 }
 
 cudaError_t launch_head(const HeadArgs& a, cudaStream_t st) {
-  head_kernel<<<div_up(a.b, 8), 256, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_k(head_kernel, dim3(div_up(a.b, kRowsT)), dim3(32 * kRowsT), 0, st, a);
 }
 
 __global__ void cdf_quantize_kernel(const float* __restrict__ P, int rows, uint32_t* freq, uint32_t* cum) {
+  pdl_wait();
+  pdl_launch();
   const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (s >= rows) return;
@@ -883,8 +1139,291 @@ __global__ void cdf_quantize_kernel(const float* __restrict__ P, int rows, uint3
 
 cudaError_t launch_cdf_quantize(const float* p, int rows, uint32_t* freq, uint32_t* cum, cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
-  cdf_quantize_kernel<<<div_up(rows, 8), 256, 0, st>>>(p, rows, freq, cum);
-  return cudaGetLastError();
+  return launch_k(cdf_quantize_kernel, dim3(div_up(rows, 8)), dim3(256), 0, st, p, rows, freq, cum);
+}
+
+// ============================================================================================
+// BF16 path: LayerNorm forward / backward with fused BF16 operand copies.
+// kRowsLN warps per CTA, one row each; the BF16 rows are staged in shared memory
+// and written transposed ([c][row], 16-byte runs) for the dW GEMMs.
+// ============================================================================================
+constexpr int kRowsLN = 8;  // rows (warps) per CTA of the LayerNorm kernels
+
+// NPL = F / 32 values per lane held in registers (all loads issued up front);
+// NPL = 0 is the generic loop for any F.
+template <int NPL>
+__global__ void __launch_bounds__(32 * kRowsLN)
+    ln_fwd_bf16_kernel(const float* __restrict__ X, const float* __restrict__ g, const float* __restrict__ be,
+                       float* __restrict__ xhat, float* __restrict__ rstd, __nv_bfloat16* __restrict__ X0b,
+                       __nv_bfloat16* __restrict__ X0bT, int b, int F, int ldT) {
+  pdl_wait();
+  pdl_launch();
+  extern __shared__ __nv_bfloat16 tile_dyn[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kRowsLN + warp;
+  __nv_bfloat16* trow = tile_dyn + (size_t)warp * F;
+  if (row < b) {
+    const float* x = X + (size_t)row * F;
+    if (NPL > 0) {
+      float v[NPL > 0 ? NPL : 1];
+#pragma unroll
+      for (int q = 0; q < NPL; ++q) v[q] = x[lane + 32 * q];
+      float sm = 0.f;
+#pragma unroll
+      for (int q = 0; q < NPL; ++q) sm += v[q];
+      const float mean = warp_sum(sm) / (float)F;
+      float qv = 0.f;
+#pragma unroll
+      for (int q = 0; q < NPL; ++q) {
+        const float d = v[q] - mean;
+        qv += d * d;
+      }
+      const float r = 1.0f / sqrtf(warp_sum(qv) / (float)F + kLnEps);
+#pragma unroll
+      for (int q = 0; q < NPL; ++q) {
+        const int c = lane + 32 * q;
+        const float h = (v[q] - mean) * r;
+        xhat[(size_t)row * F + c] = h;
+        const __nv_bfloat16 o = __float2bfloat16_rn(h * g[c] + be[c]);
+        X0b[(size_t)row * F + c] = o;
+        trow[c] = o;
+      }
+      if (lane == 0) rstd[row] = r;
+    } else {
+      float sm = 0.f;
+      for (int c = lane; c < F; c += 32) sm += x[c];
+      const float mean = warp_sum(sm) / (float)F;
+      float qv = 0.f;
+      for (int c = lane; c < F; c += 32) {
+        const float d = x[c] - mean;
+        qv += d * d;
+      }
+      const float r = 1.0f / sqrtf(warp_sum(qv) / (float)F + kLnEps);
+      for (int c = lane; c < F; c += 32) {
+        const float h = (x[c] - mean) * r;
+        xhat[(size_t)row * F + c] = h;
+        const __nv_bfloat16 o = __float2bfloat16_rn(h * g[c] + be[c]);
+        X0b[(size_t)row * F + c] = o;
+        trow[c] = o;
+      }
+      if (lane == 0) rstd[row] = r;
+    }
+  } else {
+    for (int c = lane; c < F; c += 32) trow[c] = __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  store_tile_T<kRowsLN>(tile_dyn, F, F, blockIdx.x * kRowsLN, X0bT, ldT);
+}
+
+cudaError_t launch_ln_fwd_bf16(const float* X, const float* g, const float* be, float* xhat, float* rstd,
+                               __nv_bfloat16* X0b, __nv_bfloat16* X0bT, int b, int F, int ldT, cudaStream_t st) {
+  const size_t smem = (size_t)kRowsLN * F * sizeof(__nv_bfloat16);
+  const dim3 grid(div_up(b, kRowsLN)), block(32 * kRowsLN);
+  switch (F) {
+    case 128: return launch_k(ln_fwd_bf16_kernel<4>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT);
+    case 256: return launch_k(ln_fwd_bf16_kernel<8>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT);
+    case 512: return launch_k(ln_fwd_bf16_kernel<16>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT);
+    case 1024: return launch_k(ln_fwd_bf16_kernel<32>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT);
+    default: return launch_k(ln_fwd_bf16_kernel<0>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT);
+  }
+}
+
+template <int NPL>
+__global__ void __launch_bounds__(32 * kRowsLN)
+    ln_bwd_bf16_kernel(const float* __restrict__ dX0, const float* __restrict__ xhat, const float* __restrict__ rstd,
+                       const float* __restrict__ g, const float* __restrict__ dRes, float* __restrict__ dX,
+                       __nv_bfloat16* __restrict__ dXb, __nv_bfloat16* __restrict__ dXbT, int b, int F, int ldT) {
+  pdl_wait();
+  pdl_launch();
+  extern __shared__ __nv_bfloat16 tile_dyn[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = blockIdx.x * kRowsLN + warp;
+  __nv_bfloat16* trow = tile_dyn + (size_t)warp * F;
+  if (row < b) {
+    const size_t o = (size_t)row * F;
+    const float r = rstd[row];
+    if (NPL > 0) {
+      float d[NPL > 0 ? NPL : 1], xh[NPL > 0 ? NPL : 1], rs[NPL > 0 ? NPL : 1];
+#pragma unroll
+      for (int q = 0; q < NPL; ++q) {
+        const int c = lane + 32 * q;
+        d[q] = dX0[o + c] * g[c];
+        xh[q] = xhat[o + c];
+        rs[q] = dRes[o + c];
+      }
+      float s1 = 0.f, s2 = 0.f;
+#pragma unroll
+      for (int q = 0; q < NPL; ++q) {
+        s1 += d[q];
+        s2 += d[q] * xh[q];
+      }
+      const float m1 = warp_sum(s1) / (float)F;
+      const float m2 = warp_sum(s2) / (float)F;
+#pragma unroll
+      for (int q = 0; q < NPL; ++q) {
+        const int c = lane + 32 * q;
+        const float v = rs[q] + r * (d[q] - m1 - xh[q] * m2);
+        dX[o + c] = v;
+        if (dXb) {
+          const __nv_bfloat16 h = __float2bfloat16_rn(v);
+          dXb[o + c] = h;
+          trow[c] = h;
+        }
+      }
+    } else {
+      float s1 = 0.f, s2 = 0.f;
+      for (int c = lane; c < F; c += 32) {
+        const float dd = dX0[o + c] * g[c];
+        s1 += dd;
+        s2 += dd * xhat[o + c];
+      }
+      const float m1 = warp_sum(s1) / (float)F;
+      const float m2 = warp_sum(s2) / (float)F;
+      for (int c = lane; c < F; c += 32) {
+        const float dd = dX0[o + c] * g[c];
+        const float v = dRes[o + c] + r * (dd - m1 - xhat[o + c] * m2);
+        dX[o + c] = v;
+        if (dXb) {
+          const __nv_bfloat16 h = __float2bfloat16_rn(v);
+          dXb[o + c] = h;
+          trow[c] = h;
+        }
+      }
+    }
+  } else if (dXbT) {
+    for (int c = lane; c < F; c += 32) trow[c] = __float2bfloat16_rn(0.f);
+  }
+  if (dXbT) {
+    __syncthreads();
+    store_tile_T<kRowsLN>(tile_dyn, F, F, blockIdx.x * kRowsLN, dXbT, ldT);
+  }
+}
+
+cudaError_t launch_ln_bwd_bf16(const float* dX0, const float* xhat, const float* rstd, const float* g,
+                               const float* dRes, float* dX, __nv_bfloat16* dXb, __nv_bfloat16* dXbT, int b, int F,
+                               int ldT, cudaStream_t st) {
+  const size_t smem = dXbT ? (size_t)kRowsLN * F * sizeof(__nv_bfloat16) : 0;
+  const dim3 grid(div_up(b, kRowsLN)), block(32 * kRowsLN);
+  switch (F) {
+    case 128:
+      return launch_k(ln_bwd_bf16_kernel<4>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT);
+    case 256:
+      return launch_k(ln_bwd_bf16_kernel<8>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT);
+    case 512:
+      return launch_k(ln_bwd_bf16_kernel<16>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT);
+    case 1024:
+      return launch_k(ln_bwd_bf16_kernel<32>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT);
+    default:
+      return launch_k(ln_bwd_bf16_kernel<0>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT);
+  }
+}
+
+// ============================================================================================
+// Batched column sums (bias and LN-affine gradients), fixed order: CTA = one
+// 32-column tile of one job; warp w sums rows w, w+16, ... with four
+// interleaved accumulators; warps are then added in order.
+// ============================================================================================
+__global__ void __launch_bounds__(512) colsum_multi_kernel(ColsumJobs jobs) {
+  pdl_wait();
+  pdl_launch();
+  __shared__ float part[16][33];
+  int t = blockIdx.x, j = 0;
+  while (j < jobs.n - 1 && t >= (jobs.job[j].cols + 31) / 32) {
+    t -= (jobs.job[j].cols + 31) / 32;
+    ++j;
+  }
+  const ColsumJob jb = jobs.job[j];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = t * 32 + lane;
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  if (c < jb.cols) {
+    int r = w;
+    if (jb.Y) {
+      for (; r + 48 < jb.rows; r += 64) {
+        a0 += jb.X[(size_t)r * jb.ld + c] * jb.Y[(size_t)r * jb.ld + c];
+        a1 += jb.X[(size_t)(r + 16) * jb.ld + c] * jb.Y[(size_t)(r + 16) * jb.ld + c];
+        a2 += jb.X[(size_t)(r + 32) * jb.ld + c] * jb.Y[(size_t)(r + 32) * jb.ld + c];
+        a3 += jb.X[(size_t)(r + 48) * jb.ld + c] * jb.Y[(size_t)(r + 48) * jb.ld + c];
+      }
+      for (; r < jb.rows; r += 16) a0 += jb.X[(size_t)r * jb.ld + c] * jb.Y[(size_t)r * jb.ld + c];
+    } else {
+      for (; r + 48 < jb.rows; r += 64) {
+        a0 += jb.X[(size_t)r * jb.ld + c];
+        a1 += jb.X[(size_t)(r + 16) * jb.ld + c];
+        a2 += jb.X[(size_t)(r + 32) * jb.ld + c];
+        a3 += jb.X[(size_t)(r + 48) * jb.ld + c];
+      }
+      for (; r < jb.rows; r += 16) a0 += jb.X[(size_t)r * jb.ld + c];
+    }
+  }
+  part[w][lane] = (a0 + a1) + (a2 + a3);
+  __syncthreads();
+  if (w == 0 && c < jb.cols) {
+    float s = part[0][lane];
+#pragma unroll
+    for (int i = 1; i < 16; ++i) s += part[i][lane];
+    jb.out[c] = s;
+  }
+}
+
+cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st) {
+  int tiles = 0;
+  for (int j = 0; j < jobs.n; ++j) tiles += (jobs.job[j].cols + 31) / 32;
+  if (tiles == 0) return cudaSuccess;
+  return launch_k(colsum_multi_kernel, dim3(tiles), dim3(512), 0, st, jobs);
+}
+
+// ============================================================================================
+// Adam with the BF16 weight copy refreshed in the same pass; transposed copies
+// of every weight matrix in one launch (32 x 32 tiles through shared memory).
+// ============================================================================================
+__global__ void adam_bf16_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
+                                 float* __restrict__ V, __nv_bfloat16* __restrict__ Pb, size_t n,
+                                 const StepCtl* __restrict__ ctl, EmbGrad eg) {
+  pdl_wait();
+  pdl_launch();
+  const StepCtl c = *ctl;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
+    float p = P[e], m = M[e], v = V[e];
+    const float gr = (eg.part && e >= eg.off && e < eg.off + eg.n) ? emb_grad_sum(eg.part, eg.nchunks, eg.n, e - eg.off)
+                                                                   : G[e];
+    adam1(p, m, v, gr, c.lr, c.bc1, c.bc2);
+    P[e] = p;
+    M[e] = m;
+    V[e] = v;
+    Pb[e] = __float2bfloat16_rn(p);
+  }
+}
+
+cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
+                             const StepCtl* ctl, cudaStream_t st, EmbGrad eg) {
+  int grid = (int)((n + 255) / 256);
+  if (grid > 152 * 8) grid = 152 * 8;
+  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, G, M, V, Pb, n, ctl, eg);
+}
+
+__global__ void transpose_tiles_kernel(const __nv_bfloat16* __restrict__ Pb, __nv_bfloat16* __restrict__ PbT,
+                                       const TransposeTile* __restrict__ tiles) {
+  pdl_wait();
+  pdl_launch();
+  __shared__ __nv_bfloat16 t[32][34];
+  const TransposeTile tl = tiles[blockIdx.x];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    int r = tl.r0 + k, cc = tl.c0 + tx;
+    t[k][tx] = (r < tl.rows && cc < tl.cols) ? Pb[tl.off + (size_t)r * tl.cols + cc] : __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    int cc = tl.c0 + k, r = tl.r0 + tx;
+    if (cc < tl.cols && r < tl.rows) PbT[tl.off + (size_t)cc * tl.rows + r] = t[tx][k];
+  }
+}
+
+cudaError_t launch_transpose_tiles(const __nv_bfloat16* Pb, __nv_bfloat16* PbT, const TransposeTile* tiles,
+                                   int ntiles, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
+  return launch_k(transpose_tiles_kernel, dim3(ntiles), dim3(256), 0, st, Pb, PbT, tiles);
 }
 
 // ============================================================================================
@@ -892,6 +1431,8 @@ cudaError_t launch_cdf_quantize(const float* p, int rows, uint32_t* freq, uint32
 // ============================================================================================
 __global__ void to_bf16_kernel(const float* __restrict__ X, int rows, int cols, int ldx, __nv_bfloat16* Y, int ldy,
                                __nv_bfloat16* YT, int ldt) {
+  pdl_wait();
+  pdl_launch();
   __shared__ float tile[32][33];
   const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
@@ -912,8 +1453,7 @@ __global__ void to_bf16_kernel(const float* __restrict__ X, int rows, int cols, 
 cudaError_t launch_to_bf16(const float* X, int rows, int cols, int ldx, __nv_bfloat16* Y, int ldy,
                            __nv_bfloat16* YT, int ldt, cudaStream_t st) {
   dim3 grid(div_up(cols, 32), div_up(rows, 32));
-  to_bf16_kernel<<<grid, 256, 0, st>>>(X, rows, cols, ldx, Y, ldy, YT, ldt);
-  return cudaGetLastError();
+  return launch_k(to_bf16_kernel, dim3(grid), dim3(256), 0, st, X, rows, cols, ldx, Y, ldy, YT, ldt);
 }
 
 }  // namespace edpc

@@ -23,8 +23,11 @@ cudaError_t launch_ln_fwd(const float* X, const float* g, const float* be, float
                           float* X0, int b, int F, cudaStream_t st);
 // G = GELU(prod_i A[:, iH:(i+1)H]).
 cudaError_t launch_branch_gelu(const float* A, int b, int H, int k, float* G, cudaStream_t st);
-// Per-stream FDM product y_s = x'_s U_s.
-cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int Fp, cudaStream_t st);
+// Per-stream FDM product y_s = x'_s U_s (and optional BF16 copies of Y).
+// err (optional) gets bit 8 if a bounded wait for a bulk copy expired.
+cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int Fp, cudaStream_t st,
+                           __nv_bfloat16* Yb = nullptr, __nv_bfloat16* YbT = nullptr, int ldT = 0,
+                           int* err = nullptr);
 
 // Softmax, CDF quantization, coding and the CE gradient of one step.
 struct HeadArgs {
@@ -45,6 +48,9 @@ struct HeadArgs {
   const uint32_t* bits_len;
   uint32_t* freq_out;        // optional b x 256
   uint32_t* cum_out;         // optional b x 257
+  __nv_bfloat16* dzb;        // optional b x 256 BF16 copy of dz
+  __nv_bfloat16* dzbT;       // optional 256 x ldT transposed BF16 copy of dz
+  int ldT;
   int* err;
 };
 cudaError_t launch_head(const HeadArgs& a, cudaStream_t st);
@@ -74,14 +80,28 @@ struct FdmBwdArgs {
   const uint8_t* active;     // optional mask; else active = (ctl->i < len_s)
   int b, Fp;
   int update;
+  __nv_bfloat16* dXpb;       // optional BF16 copies of dx'
+  __nv_bfloat16* dXpbT;
+  int ldT;
 };
 cudaError_t launch_fdm_bwd(const FdmBwdArgs& a, cudaStream_t st);
 // dE[c][d] = sum over positions with ctx == c of dX[s][k*D + d], fixed order.
-cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE,
-                             cudaStream_t st);
+// `part` is scratch of embed_bwd_chunks(b, K) * 256 * D floats.
+// With sum = false only the chunk partials are written and dE is left to Adam
+// (EmbGrad below).
+int embed_bwd_chunks(int b, int K);
+cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, float* part,
+                             cudaStream_t st, bool sum = true);
+// The embedding gradient as chunk partials for Adam to reduce on the fly:
+// elements [off, off + n) of the flat gradient come from part (nchunks x n).
+struct EmbGrad {
+  const float* part;  // null: every gradient element is read from G
+  int nchunks;
+  size_t off, n;
+};
 // Adam over the flat shared parameters; bf16 != nullptr also refreshes the BF16 copy.
 cudaError_t launch_adam(float* P, const float* G, float* M, float* V, size_t n, const StepCtl* ctl,
-                        cudaStream_t st);
+                        cudaStream_t st, EmbGrad eg = EmbGrad{nullptr, 0, 0, 0});
 // i += 1 and the derived per-step scalars.
 cudaError_t launch_step_advance(StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st);
 
@@ -117,6 +137,41 @@ struct GemmF32 {
   const float* R; int ldr;
 };
 cudaError_t launch_gemm_f32(const GemmF32& g, cudaStream_t st);
+
+// ---- BF16 path: fused operand production -----------------------------------------------------
+// Rows are processed 16 per CTA so that the transposed copy YT[c][r] (ld ldT, a
+// multiple of 16; padding rows are written as zero) goes out in 32-byte runs.
+constexpr int kRowsT = 16;
+// LayerNorm forward writing xhat, rstd and the BF16 copies of X0 (row-major and transposed).
+cudaError_t launch_ln_fwd_bf16(const float* X, const float* g, const float* be, float* xhat, float* rstd,
+                               __nv_bfloat16* X0b, __nv_bfloat16* X0bT, int b, int F, int ldT, cudaStream_t st);
+// LayerNorm backward: dX = dRes + LN adjoint; also the BF16 copies of dX when non-null.
+cudaError_t launch_ln_bwd_bf16(const float* dX0, const float* xhat, const float* rstd, const float* g,
+                               const float* dRes, float* dX, __nv_bfloat16* dXb, __nv_bfloat16* dXbT, int b, int F,
+                               int ldT, cudaStream_t st);
+// Batched deterministic column sums: one launch for up to kMaxColsumJobs tensors.
+constexpr int kMaxColsumJobs = 8;
+struct ColsumJob {
+  const float* X;
+  const float* Y;  // optional: sum of X * Y
+  int rows, cols, ld;
+  float* out;
+};
+struct ColsumJobs {
+  ColsumJob job[kMaxColsumJobs];
+  int n;
+};
+cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st);
+// Adam that also writes the BF16 copy Pb of every updated parameter (same flat layout).
+cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
+                             const StepCtl* ctl, cudaStream_t st, EmbGrad eg = EmbGrad{nullptr, 0, 0, 0});
+// Transposed BF16 copies of several matrices in one launch: PbT[off + c*rows + r] = Pb[off + r*cols + c].
+struct TransposeTile {
+  unsigned long long off;
+  int rows, cols, r0, c0;
+};
+cudaError_t launch_transpose_tiles(const __nv_bfloat16* Pb, __nv_bfloat16* PbT, const TransposeTile* tiles,
+                                   int ntiles, cudaStream_t st);
 
 // ---- BF16 operands ------------------------------------------------------------------------------
 // Y[r][c] = bf16(X[r][c]) (ld ldy) and/or YT[c][r] = bf16(X[r][c]) (ld ldt).

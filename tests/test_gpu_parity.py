@@ -364,3 +364,28 @@ def test_multimedia_roundtrip_bf16():
                       precision=edpc.EDPC_BF16, seed=1)
     bits = edpc.compress(x, c)
     assert np.array_equal(edpc.decompress(bits), x)
+
+
+def test_autograd_function_matches_oracle():
+    """The adjoint kernels behind torch.autograd.Function: gradients of the mean
+    cross-entropy w.r.t. the shared parameters and the FDM, against the oracle."""
+    from paper_2507_18969_gb300.autograd import step_loss
+    dims = dict(context=16, embed_dim=16, latent=128, hidden=128, blocks=2, branches=2, lr=1e-3, seed=4)
+    c, o = cfgs(**dims)
+    b = 4
+    m = edpc.Model(c, b)
+    om = OModel(o, b)
+    rng = np.random.default_rng(21)
+    st = _state_after_steps(m, om, b, o.context, 4, rng)
+    shared = torch.tensor(st["P"], requires_grad=True)
+    fdm = torch.tensor(st["U"], requires_grad=True)
+    ctx = rng.integers(0, 256, size=(b, o.context)).astype(np.uint8)
+    tg = rng.integers(0, 256, size=b).astype(np.uint8)
+    act = np.ones(b, np.uint8)
+    loss = step_loss(shared, fdm, m, ctx, tg, act)
+    gs, gf = torch.autograd.grad(loss, [shared, fdm])
+    lo = om.loss(ctx.astype(np.int64), tg.astype(np.int64))
+    assert abs(float(loss) - lo) <= 1e-5 * max(1.0, abs(lo))
+    _, go, dUo, _ = om.grad_step(ctx.astype(np.int64), tg.astype(np.int64))
+    assert _rel(gs.numpy(), OModel.flat_grads(om.layout, go)) <= 1e-3
+    assert _rel(gf.numpy().reshape(b, 128, 128), dUo) <= 1e-3
