@@ -1,13 +1,15 @@
-"""Benchmark: EDPC compress / decompress throughput on the 64 MiB multimedia mix.
+"""Benchmark: EDPC compress / decompress throughput on the multimedia mix.
 
-Workload: 64 MiB of seeded synthetic multimedia-like bytes (8-bit images,
-16-bit PCM, order-3 Markov text in equal thirds), split into 512 streams;
-model K = 32, D = 16, F' = 256, 4 MBRBs of hidden 256; BF16 GEMMs with FP32
-accumulation (the plain FP32 path is timed beside it).
+Default workload (mix64m): 64 MiB of seeded synthetic multimedia-like bytes
+(8-bit images, 16-bit PCM, order-3 Markov text in equal thirds), split into
+512 streams; model K = 32, D = 16, F' = 256, 4 MBRBs of hidden 256; BF16 GEMMs
+with FP32 accumulation (the plain FP32 path is timed beside it).
+`--workload mix1g`: the 1 GiB mix in 4096 streams; K = 64, F' = 512, 6 MBRBs
+of hidden 512.
 
-A bench step is one coder chunk: 64 model steps of all 512 streams, i.e.
-64 x 512 = 32 KiB of input through every stage of the hot path (embedding,
-MBRBs, LTE/FDM, head, CDF, range coding on the coder stream, adjoint, Adam).
+A bench step is one coder chunk: 64 model steps of all b streams, i.e.
+64 x b input bytes through every stage of the hot path (embedding, MBRBs,
+LTE/FDM, head, CDF, range coding on the coder stream, adjoint, Adam).
 W warm-up steps run first; then exactly K steps are timed with CUDA events on
 the launching stream, bracketed by a barrier and a device synchronize.
 
@@ -19,7 +21,8 @@ Also      decompress MB/s (device-resident, same prefix input, lossless check),
           FP32 compress MB/s, bits/byte, the FDM kernels' roofline, clocks.
 
 `--impl reference` times the CPU oracle (FP64 NumPy) on the same workload:
-each step is one model step of all 512 streams.
+each step is one model step of the workload's streams (a sample of 256 of
+them for mix1g).
 
 With N GPUs (torchrun), each rank compresses its own replica (a different
 seed); the value is the total bytes of all ranks over the slowest rank's time.
@@ -42,8 +45,19 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = dict(total_bytes=64 << 20, streams=512, context=32, embed_dim=16, latent=256, hidden=256, blocks=4,
-                branches=2, lr=1e-3, seed=1, data_seed=20250719)
+WORKLOADS = {
+    # the default bench line
+    "mix64m": dict(total_bytes=64 << 20, streams=512, context=32, embed_dim=16, latent=256, hidden=256, blocks=4,
+                   branches=2, lr=1e-3, seed=1, data_seed=20250719, cpu_streams=512,
+                   desc="multimedia mix 64 MiB (images/PCM/text thirds), 512 streams",
+                   model="K=32 D=16 F=512 F'=256 4xMBRB(H=256, 2 branches)"),
+    # the large single input: 12.9 GB of FDM state and Adam moments
+    "mix1g": dict(total_bytes=1 << 30, streams=4096, context=64, embed_dim=16, latent=512, hidden=512, blocks=6,
+                  branches=2, lr=1e-3, seed=1, data_seed=20250722, cpu_streams=256,
+                  desc="multimedia mix 1 GiB (images/PCM/text thirds), 4096 streams",
+                  model="K=64 D=16 F=1024 F'=512 6xMBRB(H=512, 2 branches)"),
+}
+WORKLOAD = WORKLOADS["mix64m"]
 CHUNK = 64
 METRIC = "compress MB/s (BF16 batched; decompress and plain FP32 reported beside it)"
 PROFILES = os.path.join(ROOT, "profiles")
@@ -53,6 +67,7 @@ KERNEL_SRC = os.path.join(ROOT, "paper_2507_18969_gb300", "csrc", "kernels.cu")
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--workload", default="mix64m", choices=sorted(WORKLOADS))
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -184,11 +199,12 @@ def workload_input(rank: int) -> np.ndarray:
     return synth.multimedia_mix(WORKLOAD["total_bytes"], WORKLOAD["data_seed"] + rank)
 
 
-def prefix_input(x: np.ndarray, per_stream: int) -> np.ndarray:
-    """The first `per_stream` bytes of each of the workload's streams, concatenated."""
+def prefix_input(x: np.ndarray, per_stream: int, streams: int | None = None) -> np.ndarray:
+    """The first `per_stream` bytes of each of the workload's first `streams`
+    streams (all by default), concatenated."""
     b = WORKLOAD["streams"]
     q = x.size // b
-    return np.ascontiguousarray(x[: q * b].reshape(b, q)[:, :per_stream]).reshape(-1)
+    return np.ascontiguousarray(x[: q * b].reshape(b, q)[: streams or b, :per_stream]).reshape(-1)
 
 
 def make_cfg(prec):
@@ -239,21 +255,25 @@ def timed_session(sess, warmup_chunks, steps_chunks, stream, d: Dist, clocks=Non
 # CPU oracle (cpu_baseline and --impl reference)
 # --------------------------------------------------------------------------------------------
 def oracle_model(x: np.ndarray, n_steps: int):
-    """The oracle's configuration, a freshly initialised model and the prefix input."""
+    """The oracle's configuration, a freshly initialised model and the prefix
+    input of the workload's first cpu_streams streams (all of them for the
+    64 MiB mix; a sample for the 1 GiB one, whose 4096 FP64 FDMs with their
+    moments would need 26 GB of host memory)."""
     from oracle.model import Config, Model
     w = WORKLOAD
     cfg = Config(context=w["context"], embed_dim=w["embed_dim"], latent=w["latent"], hidden=w["hidden"],
                  blocks=w["blocks"], branches=w["branches"], lr=w["lr"], seed=w["seed"])
-    xp = prefix_input(x, w["context"] + n_steps)
-    return cfg, Model(cfg, w["streams"]), xp
+    xp = prefix_input(x, w["context"] + n_steps, w["cpu_streams"])
+    return cfg, Model(cfg, w["cpu_streams"]), xp
 
 
 def oracle_steps(cfg, model, xp, n_steps: int) -> float:
-    """Seconds the FP64 oracle takes for n_steps model steps of all 512 streams
-    (its own Algorithm 1 loop, coding included), with the model built beforehand."""
+    """Seconds the FP64 oracle takes for n_steps model steps of cpu_streams
+    streams (its own Algorithm 1 loop, coding included), with the model built
+    beforehand."""
     from oracle.compress import oracle_compress
     t0 = time.perf_counter()
-    oracle_compress(xp, cfg, WORKLOAD["streams"], max_steps=n_steps, model=model)
+    oracle_compress(xp, cfg, WORKLOAD["cpu_streams"], max_steps=n_steps, model=model)
     return time.perf_counter() - t0
 
 
@@ -277,16 +297,16 @@ def run_reference(args):
         if k >= args.warmup:
             times.append(t)
     tot = sum(times)
-    value = WORKLOAD["streams"] * steps / tot / 1e6
-    sample = ("per bench step, one model step of all 512 streams of the 64 MiB workload (512 input bytes), "
-              "FP64 NumPy oracle with its uniform-prefix coding")
+    w = WORKLOAD
+    value = w["cpu_streams"] * steps / tot / 1e6
+    sample = (f"per bench step, one model step of {w['cpu_streams']} of the {w['streams']} streams of the workload "
+              f"({w['cpu_streams']} input bytes), FP64 NumPy oracle with its uniform-prefix coding")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MB/s", "n_gpus": args.gpus,
         "steps": steps, "warmup": args.warmup, "ms_per_step": tot / steps * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "multimedia mix 64 MiB (images/PCM/text thirds), 512 streams",
-                   "model": "K=32 D=16 F=512 F'=256 4xMBRB(H=256, 2 branches)", "global_batch": 512,
-                   "step": "one model step of all 512 streams"},
+        "config": {"workload": w["desc"], "model": w["model"], "global_batch": w["streams"],
+                   "step": f"one model step of {w['cpu_streams']} streams"},
         "cpu_baseline": {"value": value, "unit": "MB/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "MB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -351,7 +371,7 @@ def run_ours(args, d: Dist):
         n_chunks = (per - WORKLOAD["context"]) / CHUNK
         e2e = {"value": e2e_value, "unit": "MB/s", "h2d_bytes_per_step": int(xp.size / n_chunks),
                "d2h_bytes_per_step": int(len(bits) / n_chunks),
-               "input": f"first {per} bytes of each of the 512 streams ({xp.size} bytes), host pinned"}
+               "input": f"first {per} bytes of each of the {b} streams ({xp.size} bytes), host pinned"}
         _, n, be = edpc.peek(bits)
         bpb = 8 * (len(bits) - (88 + 4 * be + 4)) / n
 
@@ -376,15 +396,9 @@ def run_ours(args, d: Dist):
     def gbs(nbytes, ms):
         return nbytes / (ms / 1e3) / 1e9 if ms else None
 
-    if st.fdm_adam_ms:
-        kname, prof, alg, ms = ("fdm_adam_kernel (FDM Adam update, side stream)", "fdm_adam_c1",
-                                24 * fdm_elems, st.fdm_adam_ms)
-        others = {"fdm_dx": {"alg_bytes_per_launch": 4 * fdm_elems, "mean_ms": st.fdm_bwd_ms,
-                             "achieved": gbs(4 * fdm_elems, st.fdm_bwd_ms)}}
-    else:
-        kname, prof, alg, ms = ("fdm_bwd_kernel (FDM adjoint + Adam)", "fdm_bwd_adam_c1", 24 * fdm_elems,
-                                st.fdm_bwd_ms)
-        others = {}
+    kname, prof, alg, ms = ("fdm_bwd_kernel (FDM adjoint + Adam)", "fdm_bwd_adam_" + args.workload,
+                            24 * fdm_elems, st.fdm_bwd_ms)
+    others = {}
     achieved = gbs(alg, ms)
     others["fdm_fwd"] = {"alg_bytes_per_launch": 4 * fdm_elems, "mean_ms": st.fdm_fwd_ms,
                          "achieved": gbs(4 * fdm_elems, st.fdm_fwd_ms)}
@@ -399,9 +413,10 @@ def run_ours(args, d: Dist):
         n = args.cpu_steps or 8
         ocfg, omodel, oxp = oracle_model(x, n)
         tc = oracle_steps(ocfg, omodel, oxp, n)
-        cpu = {"value": b * n / tc / 1e6, "unit": "MB/s", "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"{n} model steps of all 512 streams (the first {WORKLOAD['context'] + n} bytes of each "
-                         f"stream), FP64 NumPy oracle, {tc:.1f} s"}
+        ns = WORKLOAD["cpu_streams"]
+        cpu = {"value": ns * n / tc / 1e6, "unit": "MB/s", "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{n} model steps of {ns} of the {b} streams (the first {WORKLOAD['context'] + n} bytes of "
+                         f"each), FP64 NumPy oracle, {tc:.1f} s"}
 
     if d.rank == 0:
         ms_step = out["t"] / (out["done"] / CHUNK) * 1e3 if out["done"] else None
@@ -409,10 +424,10 @@ def run_ours(args, d: Dist):
             "metric": METRIC, "value": out["value"], "unit": "MB/s", "n_gpus": d.world, "steps": K, "warmup": W,
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "multimedia mix 64 MiB (images/PCM/text thirds), 512 streams",
-                       "model": "K=32 D=16 F=512 F'=256 4xMBRB(H=256, 2 branches)", "global_batch": b,
+            "config": {"workload": WORKLOAD["desc"], "model": WORKLOAD["model"], "global_batch": b,
                        "step": f"{CHUNK} model steps x {b} streams = {CHUNK * b} input bytes",
-                       "l2": "inputs larger than L2: FDM state 403 MB per step pass, no flush",
+                       "l2": f"inputs larger than L2: FDM state {12 * fdm_elems / 1e6:.0f} MB per model step, "
+                             "no flush",
                        "parallelism": "replicas" if d.world > 1 else "single"},
             "decompress_mbs": decomp_value, "fp32_compress_mbs": fp32_value,
             "bf16_vs_fp32": (out["value"] / fp32_value) if fp32_value else None,
@@ -425,7 +440,9 @@ def run_ours(args, d: Dist):
 
 
 def main():
+    global WORKLOAD
     args = parse()
+    WORKLOAD = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args)
         return

@@ -187,17 +187,19 @@ class Model:
         except Exception:
             pass
 
-    def get_state(self):
-        P = np.empty(self.np, np.float32)
-        U = np.empty(self.fdm, np.float32)
-        M = np.empty(self.np, np.float32)
-        V = np.empty(self.np, np.float32)
-        Um = np.empty(self.fdm, np.float32)
-        Uv = np.empty(self.fdm, np.float32)
+    def get_state(self, which=("P", "U", "M", "V", "Um", "Uv")):
+        """Host copies of the state arrays named in ``which`` (the others are
+        None): P shared parameters, U per-stream FDMs, M/V and Um/Uv their Adam
+        moments; ``t`` is the Adam step count."""
+        out = {}
+        for k in ("P", "U", "M", "V", "Um", "Uv"):
+            n = self.np if k in ("P", "M", "V") else self.fdm
+            out[k] = np.empty(n, np.float32) if k in which else None
         t = C.c_uint32()
-        check(load().edpc_model_get_state(self._h, _ptr(P), _ptr(U), _ptr(M), _ptr(V), _ptr(Um), _ptr(Uv),
-                                          C.byref(t)), "edpc_model_get_state")
-        return dict(P=P, U=U, M=M, V=V, Um=Um, Uv=Uv, t=t.value)
+        ptrs = [C.c_void_p(0) if out[k] is None else _ptr(out[k]) for k in ("P", "U", "M", "V", "Um", "Uv")]
+        check(load().edpc_model_get_state(self._h, *ptrs, C.byref(t)), "edpc_model_get_state")
+        out["t"] = t.value
+        return out
 
     def set_state(self, P=None, U=None, M=None, V=None, Um=None, Uv=None, t=0):
         arrs = [None if x is None else np.ascontiguousarray(x, dtype=np.float32) for x in (P, U, M, V, Um, Uv)]

@@ -85,14 +85,19 @@ def _sample_chains(table: np.ndarray, ctx_index, n_steps: int, state: np.ndarray
     chains = state.shape[0]
     out = np.empty((chains, n_steps), dtype=np.uint8)
     st = state.astype(np.int64)
-    u = rng.random((n_steps, chains))
-    bucket = (u * 256).astype(np.int64)
+    # The uniforms are drawn in blocks of steps: the generator yields the same
+    # sequence as one (n_steps, chains) draw, with bounded memory.
+    blk = max(1, min(n_steps, (1 << 24) // max(1, chains)))
     for t in range(n_steps):
+        if t % blk == 0:
+            u = rng.random((min(blk, n_steps - t), chains))
+            bucket = (u * 256).astype(np.int64)
+        ut = u[t % blk]
         r = ctx_index(st) if order > 0 else np.zeros(chains, dtype=np.int64)
         base = r * 256
-        j = np.minimum(guide[r, bucket[t]], 255)
+        j = np.minimum(guide[r, bucket[t % blk]], 255)
         while True:
-            adv = cum_flat[base + j] <= u[t]
+            adv = cum_flat[base + j] <= ut
             if not adv.any():
                 break
             j = np.minimum(j + adv, 255)
@@ -217,7 +222,8 @@ def text_bytes(n_bytes: int, seed: int, alpha: float = 0.05, chains: int = 2048,
         return np.zeros(0, dtype=np.uint8)
     table = markov_table(3, alpha, seed, rows=table_rows)
     rng = np.random.default_rng([seed, 0x3C])
-    chains = max(1, min(chains, n_bytes // 64 or 1))
+    # long texts get more chains (about 64 KiB each) so the lockstep loop stays short
+    chains = max(1, min(chains, n_bytes // 64 or 1), n_bytes >> 16)
     per = -(-n_bytes // chains)
     init = rng.integers(0, 256, size=(chains, 3), dtype=np.uint8)
 
