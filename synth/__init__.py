@@ -61,16 +61,8 @@ def markov_table(order: int, alpha: float, seed: int, rows: int | None = None) -
     return g / s
 
 
-def _sample_chains(table: np.ndarray, ctx_index, n_steps: int, state: np.ndarray,
-                   rng: np.random.Generator, order: int) -> np.ndarray:
-    """Runs ``len(state)`` chains in lockstep for ``n_steps`` steps.
-
-    ``state`` is (chains, order) uint8, the last ``order`` bytes of each chain.
-    ``ctx_index`` maps that state to a row of ``table``.
-    Sampling is by inverse CDF: the symbol is the first j with CDF_j > u.
-    A 256-entry guide table per row gives the starting j for u's bucket.
-    Returns a (chains, n_steps) uint8 array.
-    """
+def _guide(table: np.ndarray):
+    """(flat CDF, guide table) of the inverse-CDF sampler for ``table``'s rows."""
     rows = table.shape[0]
     cum = np.cumsum(table, axis=1)
     cum[:, -1] = 1.0
@@ -81,7 +73,21 @@ def _sample_chains(table: np.ndarray, ctx_index, n_steps: int, state: np.ndarray
     q = (grid[None, :] + 2.0 * np.arange(rows)[:, None]).ravel()
     guide = (np.searchsorted(flat, q, side="right").reshape(rows, 256)
              - 256 * np.arange(rows)[:, None]).astype(np.int64)
-    cum_flat = cum.ravel()
+    return cum.ravel(), guide
+
+
+def _sample_chains(table: np.ndarray, ctx_index, n_steps: int, state: np.ndarray,
+                   rng: np.random.Generator, order: int, prep=None) -> np.ndarray:
+    """Runs ``len(state)`` chains in lockstep for ``n_steps`` steps.
+
+    ``state`` is (chains, order) uint8, the last ``order`` bytes of each chain.
+    ``ctx_index`` maps that state to a row of ``table``.
+    Sampling is by inverse CDF: the symbol is the first j with CDF_j > u.
+    A 256-entry guide table per row gives the starting j for u's bucket.
+    ``prep`` is ``_guide(table)`` when the caller has it already.
+    Returns a (chains, n_steps) uint8 array.
+    """
+    cum_flat, guide = _guide(table) if prep is None else prep
     chains = state.shape[0]
     out = np.empty((chains, n_steps), dtype=np.uint8)
     st = state.astype(np.int64)
@@ -96,11 +102,26 @@ def _sample_chains(table: np.ndarray, ctx_index, n_steps: int, state: np.ndarray
         r = ctx_index(st) if order > 0 else np.zeros(chains, dtype=np.int64)
         base = r * 256
         j = np.minimum(guide[r, bucket[t % blk]], 255)
-        while True:
+        # The symbol is the first j >= guide start with CDF_j > u. A few linear
+        # steps settle most chains; the rest take a binary search for the
+        # count of CDF entries <= u (the same answer: the CDF is nondecreasing).
+        for _ in range(3):
             adv = cum_flat[base + j] <= ut
             if not adv.any():
                 break
             j = np.minimum(j + adv, 255)
+        else:
+            left = np.nonzero(cum_flat[base + j] <= ut)[0]
+            if left.size:
+                lo = np.zeros(left.size, np.int64)
+                hi = np.full(left.size, 256, np.int64)
+                bl, ul = base[left], ut[left]
+                for _ in range(9):
+                    mid = (lo + hi) // 2
+                    le = cum_flat[bl + np.minimum(mid, 255)] <= ul
+                    lo = np.where((lo < hi) & le, mid + 1, lo)
+                    hi = np.where((lo < hi) & ~le, mid, hi)
+                j[left] = np.minimum(np.maximum(j[left], lo), 255)
         out[:, t] = j
         if order > 0:
             st[:, :-1] = st[:, 1:]
@@ -210,17 +231,21 @@ def pcm_bytes(n_bytes: int, seed: int, rate: int = 44100, segment: int = 65536) 
 
 
 def text_bytes(n_bytes: int, seed: int, alpha: float = 0.05, chains: int = 2048,
-               table_rows: int = 1 << 12) -> np.ndarray:
+               table_rows: int = 1 << 12, table: np.ndarray | None = None, prep=None) -> np.ndarray:
     """``n_bytes`` of order-3 Markov bytes with Dirichlet(alpha) rows.
 
     The 3-byte context is hashed into ``table_rows`` rows. Each row is a
     Dirichlet(alpha) draw, so the source is still an order-3 chain.
     ``chains`` independent chains run in lockstep and are laid out
-    one after another.
+    one after another. ``table`` (with ``prep = _guide(table)``) replaces
+    the seed's own table, so several texts can share one source.
     """
     if n_bytes == 0:
         return np.zeros(0, dtype=np.uint8)
-    table = markov_table(3, alpha, seed, rows=table_rows)
+    if table is None:
+        table = markov_table(3, alpha, seed, rows=table_rows)
+        prep = None
+    table_rows = table.shape[0]
     rng = np.random.default_rng([seed, 0x3C])
     # long texts get more chains (about 64 KiB each) so the lockstep loop stays short
     chains = max(1, min(chains, n_bytes // 64 or 1), n_bytes >> 16)
@@ -232,7 +257,7 @@ def text_bytes(n_bytes: int, seed: int, alpha: float = 0.05, chains: int = 2048,
         h = (h * 0x9E3779B1) & 0xFFFFFFFF
         return (h >> 16) % table_rows
 
-    body = _sample_chains(table, index, per, init, rng, 3)
+    body = _sample_chains(table, index, per, init, rng, 3, prep)
     return body.reshape(-1)[:n_bytes].copy()
 
 
@@ -257,12 +282,15 @@ def uneven_files(n_files: int, seed: int, lo: int = 4096, hi: int = 16 * MIB,
     """``n_files`` files with sizes log-uniform in [lo, hi].
 
     Each file mixes image, PCM and text bytes. The weights are Dirichlet(1, 1, 1)
-    per file; the parts are laid out contiguously.
+    per file; the parts are laid out contiguously. All files' text comes from
+    one order-3 source (one Dirichlet(0.05) table for the set, hashed contexts
+    as in ``text_bytes``), sampled as chains of 4 KiB run in lockstep; each
+    file takes its own consecutive chains.
     ``max_total`` caps the total size by truncating the list.
     """
     rng = np.random.default_rng([seed, 0x4D])
     sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_files)).astype(np.int64)
-    files = []
+    parts = []
     total = 0
     for k, sz in enumerate(sizes):
         if max_total is not None and total + sz > max_total:
@@ -274,7 +302,27 @@ def uneven_files(n_files: int, seed: int, lo: int = 4096, hi: int = 16 * MIB,
         rem_img = n_img_b - img.size
         pcm_n = (int(sz * w[1]) + rem_img) // 2 * 2
         pcm = pcm_bytes(pcm_n, seed * 7919 + k)
-        txt = text_bytes(int(sz) - img.size - pcm.size, seed * 7919 + k, chains=64)
-        files.append(np.concatenate([img, pcm, txt]).astype(np.uint8))
+        parts.append((img, pcm, int(sz) - img.size - pcm.size))
         total += int(sz)
+    # all text in one lockstep run: file k owns ceil(n_txt / 4096) chains
+    chunk = 4096
+    nch = [-(-t // chunk) for _, _, t in parts]
+    table = markov_table(3, 0.05, seed, rows=1 << 12)
+    trng = np.random.default_rng([seed, 0x3D])
+    body = np.zeros((0, chunk), np.uint8)
+    if sum(nch):
+        init = trng.integers(0, 256, size=(sum(nch), 3), dtype=np.uint8)
+
+        def index(st):
+            h = (st[:, 0] * 65599 + st[:, 1]) * 65599 + st[:, 2]
+            h = (h * 0x9E3779B1) & 0xFFFFFFFF
+            return (h >> 16) % table.shape[0]
+
+        body = _sample_chains(table, index, chunk, init, trng, 3)
+    files = []
+    c0 = 0
+    for (img, pcm, t), m in zip(parts, nch):
+        txt = body[c0:c0 + m].reshape(-1)[:t]
+        c0 += m
+        files.append(np.concatenate([img, pcm, txt]).astype(np.uint8))
     return files
