@@ -81,7 +81,8 @@ def _sample_chains(table: np.ndarray, ctx_index, n_steps: int, state: np.ndarray
     """Runs ``len(state)`` chains in lockstep for ``n_steps`` steps.
 
     ``state`` is (chains, order) uint8, the last ``order`` bytes of each chain.
-    ``ctx_index`` maps that state to a row of ``table``.
+    ``ctx_index`` maps that state, given as a list of ``order`` int64 columns
+    (oldest first), to a row of ``table``.
     Sampling is by inverse CDF: the symbol is the first j with CDF_j > u.
     A 256-entry guide table per row gives the starting j for u's bucket.
     ``prep`` is ``_guide(table)`` when the caller has it already.
@@ -89,8 +90,9 @@ def _sample_chains(table: np.ndarray, ctx_index, n_steps: int, state: np.ndarray
     """
     cum_flat, guide = _guide(table) if prep is None else prep
     chains = state.shape[0]
-    out = np.empty((chains, n_steps), dtype=np.uint8)
-    st = state.astype(np.int64)
+    out = np.empty((n_steps, chains), dtype=np.uint8)
+    cols = [state[:, k].astype(np.int64) for k in range(order)]
+    guide_flat = guide.ravel()
     # The uniforms are drawn in blocks of steps: the generator yields the same
     # sequence as one (n_steps, chains) draw, with bounded memory.
     blk = max(1, min(n_steps, (1 << 24) // max(1, chains)))
@@ -99,9 +101,9 @@ def _sample_chains(table: np.ndarray, ctx_index, n_steps: int, state: np.ndarray
             u = rng.random((min(blk, n_steps - t), chains))
             bucket = (u * 256).astype(np.int64)
         ut = u[t % blk]
-        r = ctx_index(st) if order > 0 else np.zeros(chains, dtype=np.int64)
+        r = ctx_index(cols) if order > 0 else np.zeros(chains, dtype=np.int64)
         base = r * 256
-        j = np.minimum(guide[r, bucket[t % blk]], 255)
+        j = np.minimum(guide_flat[base + bucket[t % blk]], 255)
         # The symbol is the first j >= guide start with CDF_j > u. A few linear
         # steps settle most chains; the rest take a binary search for the
         # count of CDF entries <= u (the same answer: the CDF is nondecreasing).
@@ -122,11 +124,10 @@ def _sample_chains(table: np.ndarray, ctx_index, n_steps: int, state: np.ndarray
                     lo = np.where((lo < hi) & le, mid + 1, lo)
                     hi = np.where((lo < hi) & ~le, mid, hi)
                 j[left] = np.minimum(np.maximum(j[left], lo), 255)
-        out[:, t] = j
+        out[t] = j
         if order > 0:
-            st[:, :-1] = st[:, 1:]
-            st[:, -1] = j
-    return out
+            cols = cols[1:] + [j]
+    return np.ascontiguousarray(out.T)
 
 
 def markov_bytes(n: int, order: int, alpha: float, seed: int,
@@ -143,10 +144,10 @@ def markov_bytes(n: int, order: int, alpha: float, seed: int,
         return rng.integers(0, 256, size=n, dtype=np.uint8)
     init = rng.integers(0, 256, size=(1, order), dtype=np.uint8)
 
-    def index(st):
-        r = np.zeros(st.shape[0], dtype=np.int64)
-        for k in range(order):
-            r = r * 256 + st[:, k]
+    def index(cols):
+        r = np.zeros(cols[0].shape[0], dtype=np.int64)
+        for c in cols:
+            r = r * 256 + c
         return r
 
     body = _sample_chains(table, index, n - order, init, rng, order)[0]
@@ -252,8 +253,8 @@ def text_bytes(n_bytes: int, seed: int, alpha: float = 0.05, chains: int = 2048,
     per = -(-n_bytes // chains)
     init = rng.integers(0, 256, size=(chains, 3), dtype=np.uint8)
 
-    def index(st):
-        h = (st[:, 0] * 65599 + st[:, 1]) * 65599 + st[:, 2]
+    def index(cols):
+        h = (cols[0] * 65599 + cols[1]) * 65599 + cols[2]
         h = (h * 0x9E3779B1) & 0xFFFFFFFF
         return (h >> 16) % table_rows
 
@@ -313,8 +314,8 @@ def uneven_files(n_files: int, seed: int, lo: int = 4096, hi: int = 16 * MIB,
     if sum(nch):
         init = trng.integers(0, 256, size=(sum(nch), 3), dtype=np.uint8)
 
-        def index(st):
-            h = (st[:, 0] * 65599 + st[:, 1]) * 65599 + st[:, 2]
+        def index(cols):
+            h = (cols[0] * 65599 + cols[1]) * 65599 + cols[2]
             h = (h * 0x9E3779B1) & 0xFFFFFFFF
             return (h >> 16) % table.shape[0]
 
