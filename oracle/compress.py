@@ -17,6 +17,9 @@ Readings:
   * Step i (0-based) is active for stream s when K <= i < len_s. The uniform
     prefix covers i < K (each byte costs exactly 8 bits, f = 256).
   * The loss of a step is the mean over its active streams.
+  * A file set (archive) is cut file by file into streams of at most L
+    bytes (``archive_split``); all its streams start together and share the
+    model, exactly as the streams of one input do.
 
 Parity: the round trip is an invariant, checked here on every call that
 decodes. The code length is checked against the ideal plus truncation bound,
@@ -41,13 +44,60 @@ def split_streams(n: int, b: int, K: int):
     return b_eff, offsets, lengths
 
 
+def archive_split(sizes, L: int):
+    """(b, offsets, lengths) of a file set cut into streams of at most L bytes.
+
+    Reading for many files in one batch (Sec. 3.3's parallel streams over a
+    file set): file f of n_f bytes becomes m_f = ceil(n_f / L) contiguous
+    streams; with q, rem = divmod(n_f, m_f) the first rem of them have q + 1
+    bytes and the others q. Streams are numbered file by file, offsets are
+    into the files' concatenation, and an empty file has no stream. If no
+    file has a byte, there is one empty stream (as for an empty input).
+    """
+    assert L >= 1
+    offsets, lengths = [], []
+    base = 0
+    for n in sizes:
+        n = int(n)
+        m = -(-n // L)
+        if m:
+            q, rem = divmod(n, m)
+            for j in range(m):
+                offsets.append(base + j * q + min(j, rem))
+                lengths.append(q + (1 if j < rem else 0))
+        base += n
+    if not lengths:
+        offsets, lengths = [0], [0]
+    return len(lengths), np.array(offsets, dtype=np.int64), np.array(lengths, dtype=np.int64)
+
+
+def archive_stream_len(sizes, budget: int) -> int:
+    """The smallest L >= 1 with sum_f ceil(n_f / L) <= budget (budget >= the
+    number of non-empty files, else the largest file size)."""
+    sizes = [int(n) for n in sizes if int(n) > 0]
+    if not sizes:
+        return 1
+
+    def count(L):
+        return sum(-(-n // L) for n in sizes)
+
+    lo, hi = 1, max(sizes)
+    while lo < hi:
+        mid = (lo + hi) // 2
+        if count(mid) <= budget:
+            hi = mid
+        else:
+            lo = mid + 1
+    return lo
+
+
 def _contexts(buf, offsets, rows, i, K):
     idx = offsets[rows][:, None] + (i - K) + np.arange(K)[None, :]
     return buf[idx]
 
 
 def oracle_compress(data, cfg: Config, streams: int, max_steps: int | None = None,
-                    model: Model | None = None):
+                    model: Model | None = None, split=None):
     """Encodes ``data`` (uint8) with Algorithm 1 over ``streams`` streams.
 
     Returns a dict: ``streams`` (list of bytes), ``b``, ``lengths``,
@@ -55,11 +105,13 @@ def oracle_compress(data, cfg: Config, streams: int, max_steps: int | None = Non
     (the final state), ``steps`` (model steps run). With ``max_steps``, only
     that many model steps run and the coders are flushed there (a prefix
     run, used for timing and for comparing bits/byte on a prefix).
+    ``split`` = (b, offsets, lengths) replaces the contiguous split (for
+    example ``archive_split`` of a file set; ``streams`` is then ignored).
     """
     data = np.asarray(data, dtype=np.uint8)
     n = data.size
     K = cfg.context
-    b, offsets, lengths = split_streams(n, streams, K)
+    b, offsets, lengths = split_streams(n, streams, K) if split is None else split
     if model is None:
         model = Model(cfg, b)
     encs = [RangeEncoder() for _ in range(b)]
@@ -95,10 +147,10 @@ def oracle_compress(data, cfg: Config, streams: int, max_steps: int | None = Non
                 model=model, steps=steps)
 
 
-def oracle_decompress(streams, n: int, cfg: Config, b_req: int) -> np.ndarray:
+def oracle_decompress(streams, n: int, cfg: Config, b_req: int, split=None) -> np.ndarray:
     """Decodes the per-stream bitstreams of ``oracle_compress`` back to ``n`` bytes."""
     K = cfg.context
-    b, offsets, lengths = split_streams(n, b_req, K)
+    b, offsets, lengths = split_streams(n, b_req, K) if split is None else split
     assert len(streams) == b
     model = Model(cfg, b)
     decs = [RangeDecoder(s) for s in streams]

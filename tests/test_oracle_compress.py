@@ -7,7 +7,8 @@ import pytest
 
 import synth
 from oracle.coder import T, RangeDecoder, RangeEncoder, quantize_cdf
-from oracle.compress import oracle_compress, oracle_decompress, split_streams
+from oracle.compress import (archive_split, archive_stream_len, oracle_compress, oracle_decompress,
+                             split_streams)
 from oracle.model import Config, Model, softmax
 
 TINY = dict(embed_dim=4, latent=8, hidden=8, blocks=2, branches=2, lr=1e-3)
@@ -27,6 +28,55 @@ def test_split_partitions_input(n, b, K):
     assert np.array_equal(off, np.concatenate([[0], np.cumsum(ln)[:-1]]))
     if n >= K:
         assert be <= n // K
+
+
+@pytest.mark.parametrize("sizes,L", [([], 4), ([0, 0], 3), ([5], 1), ([5], 5), ([5], 2), ([10, 0, 3, 17], 4),
+                                     ([4096, 70000, 1, 65536], 65536), ([9, 8, 7], 100)])
+def test_archive_split_partitions_each_file(sizes, L):
+    b, off, ln = archive_split(sizes, L)
+    assert b == len(ln) == len(off)
+    if sum(sizes) == 0:
+        assert b == 1 and ln[0] == 0
+        return
+    assert b == sum(-(-n // L) for n in sizes)
+    # the streams tile the concatenation in order, none crossing a file boundary
+    assert off[0] == 0 and np.array_equal(off[1:], off[:-1] + ln[:-1])
+    ends = np.cumsum(sizes)
+    starts = ends - np.array(sizes)
+    s = 0
+    for n, a, e in zip(sizes, starts, ends):
+        m = -(-n // L)
+        piece = ln[s:s + m]
+        assert piece.sum() == n and (m == 0 or piece.max() - piece.min() <= 1)
+        assert np.all(piece <= L) and np.all(np.diff(piece) <= 0)
+        assert np.all((off[s:s + m] >= a) & (off[s:s + m] + piece <= e))
+        s += m
+
+
+@pytest.mark.parametrize("sizes", [[1], [7, 3], [100, 1, 50, 0, 33], [4096, 9000, 70000]])
+def test_archive_stream_len_is_the_smallest_that_fits(sizes):
+    count = lambda L: sum(-(-n // L) for n in sizes if n)
+    for budget in (1, 2, 3, 5, 17, 64, 10 ** 6):
+        L = archive_stream_len(sizes, budget)
+        nz = sum(1 for n in sizes if n)
+        if budget >= nz:
+            assert count(L) <= budget
+            assert L == 1 or count(L - 1) > budget
+        else:
+            assert L == max(sizes)
+
+
+def test_archive_roundtrip_with_uneven_streams():
+    """Streams of very different lengths (some shorter than K, one empty file)."""
+    rng = np.random.default_rng(5)
+    sizes = [1, 0, 40, 7, 95]
+    data = rng.integers(0, 256, size=sum(sizes)).astype(np.uint8)
+    cfg = tiny(3)
+    sp = archive_split(sizes, 32)
+    r = oracle_compress(data, cfg, 0, split=sp)
+    assert r["b"] == 1 + 2 + 1 + 3
+    y = oracle_decompress(r["streams"], data.size, cfg, 0, split=sp)
+    assert np.array_equal(y, data)
 
 
 @pytest.mark.parametrize("n,b,K", [(0, 2, 2), (1, 2, 2), (5, 3, 2), (300, 4, 3), (257, 5, 2)])
