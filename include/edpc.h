@@ -58,6 +58,8 @@ extern "C" {
 /* cfg.flags */
 #define EDPC_FLAG_NO_PIPELINE 1u  /* run the coder stage inline (DPCA off) */
 #define EDPC_FLAG_NO_GRAPH 2u     /* launch every kernel eagerly (no CUDA graph) */
+#define EDPC_FLAG_TUNE_TILES 4u   /* BF16: time each GEMM's N tile at open and record the
+                                     choice in the header (file sets always do) */
 
 /*
  * Model and coder configuration. Everything here that changes the bitstream
@@ -83,7 +85,7 @@ extern "C" {
  *
  * Limits: 1 <= context <= 256; embed_dim a multiple of 8 in [8, 64];
  * latent and hidden multiples of 8; F <= 2048, F' <= 1024, H <= 2048;
- * streams <= 65536; blocks <= 16.
+ * streams <= 65535; blocks <= 16.
  */
 typedef struct {
   uint32_t version;     /* must be EDPC_ABI_VERSION */
@@ -153,10 +155,10 @@ typedef struct edpc_session edpc_session;
 
 /*
  * Opens an encoder over `len` input bytes.
- *   data            input bytes. If data_on_device is 0 they are host bytes
- *                   and each run() copies the bytes its steps need to the
- *                   device; otherwise `data` is a device pointer that must
- *                   stay valid until the session is closed.
+ *   data            input bytes. If data_on_device is 0 they are host bytes,
+ *                   copied to the device at open; otherwise `data` is a
+ *                   device pointer that must stay valid until the session
+ *                   is closed.
  *   cuda_stream     cudaStream_t on which the model stage runs (NULL: the
  *                   library's own). The coder stage runs on a second stream
  *                   of the library's and joins back before run() returns.
@@ -215,6 +217,74 @@ int edpc_session_stats(const edpc_session* s, edpc_stats* st);
 int edpc_session_profile(edpc_session* s, int on);
 
 void edpc_session_close(edpc_session* s);
+
+/* ------------------------------------------------------------------------ */
+/* File sets: many files of uneven size in one batch.                       */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper codes one input split into parallel streams (Sec. 3.3); it has
+ * no archive format. Here a file set runs as one batch under one model: with
+ * stream length L, file f of n_f bytes becomes m_f = ceil(n_f / L) contiguous
+ * streams of q or q + 1 bytes (q = n_f / m_f, the longer ones first),
+ * numbered file by file; an empty file has none. All streams start together
+ * and each stops when its bytes run out (it is then masked: no coding, no
+ * gradient, no FDM update). Each stream has its own FDM, Adam moments and
+ * range coder; the shared parameters learn from every active stream.
+ *
+ * cfg->streams chooses L:
+ *   > 0  a stream budget: the smallest L whose split has at most that many
+ *        streams (one stream per file when even that exceeds the budget).
+ *   0    autotuned on the current GPU: candidates L = 8 KiB * 2^j, model step
+ *        times measured at two stream counts (CUDA graph of the step) and
+ *        fitted as t0 + c * b, models that do not fit in 70 % of free device
+ *        memory dropped; the longest L within 5 % of the fastest estimate is
+ *        taken (fewer streams learn from more bytes each).
+ * The GEMM N tiles are also timed at open (BF16) and recorded in the header.
+ * Limits as for edpc_cfg; at most 65535 streams in all.
+ */
+typedef struct {
+  uint64_t stream_len;        /* L */
+  uint32_t streams;           /* b = sum_f ceil(n_f / L) (1 if no bytes) */
+  uint32_t reserved;
+  double est_seconds;         /* autotuner's estimate of the encode time (0 for a budget) */
+  double step_ms_t0;          /* fitted model-step time at zero streams (ms) */
+  double step_ms_per_stream;  /* fitted model-step time per stream (ms) */
+} edpc_split_plan;
+
+/* The split edpc_compress_many would use (lens: host, nfiles sizes). With
+ * cfg->streams = 0 this runs the autotuner's probes on the current GPU.
+ * Errors: EINVAL (bad cfg, NULL, more than 65535 streams), ENOMEM, ECUDA. */
+int edpc_archive_plan(const size_t* lens, size_t nfiles, const edpc_cfg* cfg, edpc_split_plan* plan);
+
+/* One-shot compression of a file set into one container.
+ *   bufs, lens  host arrays of nfiles pointers and sizes (a pointer may be
+ *               NULL when its size is 0).
+ * out/out_len as for edpc_compress. Errors as edpc_compress and
+ * edpc_archive_plan. */
+int edpc_compress_many(const uint8_t* const* bufs, const size_t* lens, size_t nfiles, const edpc_cfg* cfg,
+                       uint8_t** out, size_t* out_len);
+
+/* Encoder session over a file set (see edpc_encoder_open). bufs[f] are host
+ * pointers, or device pointers when data_on_device != 0; either way the
+ * files are copied, in order, into one library-owned device buffer at open.
+ * edpc_decoder_open decodes the container; its output is the files' bytes
+ * back to back, in order. */
+int edpc_encoder_open_many(const edpc_cfg* cfg, const uint8_t* const* bufs, const size_t* lens, size_t nfiles,
+                           int data_on_device, void* cuda_stream, edpc_session** out);
+
+/* File count and sizes of a container. For a single-input container
+ * *nfiles = 1 and sizes[0] = its length. sizes (host, *nfiles entries) may
+ * be NULL to query the count first. Errors: ECORRUPT, EVERSION, EARCH. */
+int edpc_archive_info(const uint8_t* bits, size_t bits_len, uint64_t* nfiles, uint64_t* sizes);
+
+/* One-shot decompression of a container into its files.
+ *   *outs   receives one library-allocated block: *nfiles pointers, one per
+ *           file, followed by the files' bytes; release it with
+ *           edpc_free(*outs).
+ *   *lens   receives a library-allocated array of *nfiles sizes; release
+ *           with edpc_free(*lens).
+ * Errors as edpc_decompress. */
+int edpc_decompress_many(const uint8_t* bits, size_t bits_len, uint8_t*** outs, size_t** lens, size_t* nfiles);
 
 /* ------------------------------------------------------------------------ */
 /* Single kernels on device buffers, for tests and benchmarks.              */
@@ -319,6 +389,23 @@ int edpc_model_backward(edpc_model* m, const uint8_t* ctx, const uint8_t* target
  * of the encoder: inactive rows leave their FDM and its moments unchanged. */
 int edpc_model_train_step(edpc_model* m, const uint8_t* ctx, const uint8_t* targets,
                           const uint8_t* active);
+
+/*
+ * GEMM N tiles of a BF16 model (no effect in FP32). Each tcgen05 GEMM site
+ * has a code: 0 = chosen from the problem size, 1/2/4 = N tile of 32/64/128.
+ * The codes fix how each output tile is accumulated, so a decoder must use
+ * the encoder's (containers record them when tuned). There is no such
+ * choice in the paper; it is a GPU implementation parameter.
+ *   edpc_model_set_tiles   sets codes[0..n) (the rest 0). Errors: EARCH for
+ *                          a code outside {0, 1, 2, 4}.
+ *   edpc_model_tune_tiles  times N = 32, 64 and 128 at every site on the
+ *                          model's buffers (before a step: it overwrites
+ *                          activations and gradients), keeps the fastest, and
+ *                          copies up to cap codes to `codes` (host, may be
+ *                          NULL); *n receives the number of sites.
+ */
+int edpc_model_set_tiles(edpc_model* m, const uint8_t* codes, uint32_t n);
+int edpc_model_tune_tiles(edpc_model* m, uint8_t* codes, uint32_t cap, uint32_t* n);
 
 #ifdef __cplusplus
 }

@@ -12,12 +12,13 @@ import ctypes as C
 
 import numpy as np
 
-from ._lib import (EDPC_BF16, EDPC_FLAG_NO_GRAPH, EDPC_FLAG_NO_PIPELINE, EDPC_FP32, Cfg, EdpcError,
-                   Stats, check, load)
+from ._lib import (EDPC_BF16, EDPC_FLAG_NO_GRAPH, EDPC_FLAG_NO_PIPELINE, EDPC_FLAG_TUNE_TILES, EDPC_FP32, Cfg,
+                   EdpcError, SplitPlan, Stats, check, load)
 
 __all__ = [
     "Cfg", "EdpcError", "EDPC_FP32", "EDPC_BF16", "EDPC_FLAG_NO_PIPELINE", "EDPC_FLAG_NO_GRAPH",
-    "make_cfg", "compress", "decompress", "peek", "param_count", "Encoder", "Decoder", "Model",
+    "EDPC_FLAG_TUNE_TILES", "make_cfg", "compress", "decompress", "peek", "param_count", "Encoder", "Decoder",
+    "Model", "archive_plan", "compress_many", "decompress_many", "archive_info", "SplitPlan",
     "cdf_quantize", "range_encode", "range_encode_noalloc", "NOALLOC_MAX_STREAMS", "load",
 ]
 
@@ -79,6 +80,68 @@ def peek(bits):
     return c, n.value, b.value
 
 
+def _files(files):
+    """(keep-alive arrays, pointer array, size array) of a list of byte buffers."""
+    keep = [_buf(f) for f in files]
+    n = len(keep)
+    ptrs = (C.c_void_p * max(1, n))(*[a.ctypes.data if a.size else None for a in keep])
+    lens = (C.c_size_t * max(1, n))(*[a.size for a in keep])
+    return keep, ptrs, lens
+
+
+def archive_plan(sizes, cfg: Cfg) -> SplitPlan:
+    """The stream split edpc_compress_many would use for files of ``sizes``
+    (cfg.streams = budget, or 0 to autotune on the GPU)."""
+    n = len(sizes)
+    lens = (C.c_size_t * max(1, n))(*[int(x) for x in sizes])
+    plan = SplitPlan()
+    check(load().edpc_archive_plan(lens, n, C.byref(cfg), C.byref(plan)), "edpc_archive_plan")
+    return plan
+
+
+def compress_many(files, cfg: Cfg) -> bytes:
+    """One container for a list of files (bytes or uint8 arrays)."""
+    lib = load()
+    keep, ptrs, lens = _files(files)
+    out = C.c_void_p()
+    n = C.c_size_t()
+    check(lib.edpc_compress_many(ptrs, lens, len(keep), C.byref(cfg), C.byref(out), C.byref(n)), "edpc_compress_many")
+    try:
+        return C.string_at(out, n.value)
+    finally:
+        lib.edpc_free(out)
+
+
+def archive_info(bits) -> list[int]:
+    """File sizes stored in a container."""
+    lib = load()
+    a = _buf(bits)
+    nf = C.c_uint64()
+    check(lib.edpc_archive_info(_ptr(a), a.size, C.byref(nf), C.c_void_p(0)), "edpc_archive_info")
+    sizes = np.zeros(max(1, nf.value), np.uint64)
+    check(lib.edpc_archive_info(_ptr(a), a.size, C.byref(nf), _ptr(sizes)), "edpc_archive_info")
+    return [int(x) for x in sizes[:nf.value]]
+
+
+def decompress_many(bits) -> list[np.ndarray]:
+    """The files of a container, as uint8 arrays."""
+    lib = load()
+    a = _buf(bits)
+    outs = C.c_void_p()
+    lens = C.c_void_p()
+    nf = C.c_size_t()
+    check(lib.edpc_decompress_many(_ptr(a), a.size, C.byref(outs), C.byref(lens), C.byref(nf)),
+          "edpc_decompress_many")
+    try:
+        ptrs = C.cast(outs, C.POINTER(C.c_void_p))
+        ls = C.cast(lens, C.POINTER(C.c_size_t))
+        return [np.frombuffer(C.string_at(ptrs[i], ls[i]), np.uint8).copy() if ls[i] else np.zeros(0, np.uint8)
+                for i in range(nf.value)]
+    finally:
+        lib.edpc_free(outs)
+        lib.edpc_free(lens)
+
+
 class _Session:
     def __init__(self, handle, keep):
         self._h = handle
@@ -121,12 +184,27 @@ class _Session:
 
 
 class Encoder(_Session):
-    """Encoder session. ``data``: host bytes / uint8 array, or ``device_ptr`` + ``length``."""
+    """Encoder session. ``data``: host bytes / uint8 array, or ``device_ptr`` + ``length``;
+    or ``files`` (host buffers) / ``device_files`` (list of (device pointer, size)) for a file set."""
 
     def __init__(self, cfg: Cfg, data=None, device_ptr: int | None = None, length: int | None = None,
-                 stream: int | None = None):
+                 stream: int | None = None, files=None, device_files=None):
         lib = load()
         h = C.c_void_p()
+        if files is not None or device_files is not None:
+            if device_files is not None:
+                keep = None
+                n = len(device_files)
+                ptrs = (C.c_void_p * max(1, n))(*[int(p) for p, _ in device_files])
+                lens = (C.c_size_t * max(1, n))(*[int(x) for _, x in device_files])
+                on_dev = 1
+            else:
+                keep, ptrs, lens = _files(files)
+                n, on_dev = len(keep), 0
+            check(lib.edpc_encoder_open_many(C.byref(cfg), ptrs, lens, n, on_dev, C.c_void_p(stream or 0),
+                                             C.byref(h)), "edpc_encoder_open_many")
+            super().__init__(h, (keep, ptrs, lens))
+            return
         if device_ptr is not None:
             keep = None
             check(lib.edpc_encoder_open(C.byref(cfg), C.c_void_p(device_ptr), int(length), 1,
@@ -222,6 +300,18 @@ class Model:
         check(load().edpc_model_backward(self._h, _ptr(ctx), _ptr(tg), _ptr(ac), _ptr(g), _ptr(gu)),
               "edpc_model_backward")
         return g, gu
+
+    def set_tiles(self, codes) -> None:
+        """GEMM N-tile codes per site (0 heuristic, 1/2/4 = N 32/64/128); BF16 only."""
+        a = np.ascontiguousarray(codes, dtype=np.uint8)
+        check(load().edpc_model_set_tiles(self._h, _ptr(a), a.size), "edpc_model_set_tiles")
+
+    def tune_tiles(self) -> np.ndarray:
+        """Times every GEMM site's N tiles and keeps the fastest; returns the codes."""
+        n = C.c_uint32()
+        codes = np.zeros(512, np.uint8)
+        check(load().edpc_model_tune_tiles(self._h, _ptr(codes), codes.size, C.byref(n)), "edpc_model_tune_tiles")
+        return codes[:n.value].copy()
 
     def train_step(self, ctx, targets, active):
         ctx = np.ascontiguousarray(ctx, dtype=np.uint8)

@@ -17,6 +17,7 @@ EDPC_FP32 = 0
 EDPC_BF16 = 1
 EDPC_FLAG_NO_PIPELINE = 1
 EDPC_FLAG_NO_GRAPH = 2
+EDPC_FLAG_TUNE_TILES = 4
 
 STATUS = {0: "EDPC_OK", 1: "EDPC_EINVAL", 2: "EDPC_ENOMEM", 3: "EDPC_ECORRUPT", 4: "EDPC_EVERSION",
           5: "EDPC_ECUDA", 6: "EDPC_ETIMEOUT", 7: "EDPC_EARCH"}
@@ -54,6 +55,17 @@ class Stats(C.Structure):
     ]
 
 
+class SplitPlan(C.Structure):
+    _fields_ = [
+        ("stream_len", C.c_uint64),
+        ("streams", C.c_uint32),
+        ("reserved", C.c_uint32),
+        ("est_seconds", C.c_double),
+        ("step_ms_t0", C.c_double),
+        ("step_ms_per_stream", C.c_double),
+    ]
+
+
 P = C.c_void_p
 U8P = C.POINTER(C.c_uint8)
 FP = C.POINTER(C.c_float)
@@ -77,6 +89,11 @@ PROTOS = {
     "edpc_session_stats": (C.c_int, [P, C.POINTER(Stats)]),
     "edpc_session_profile": (C.c_int, [P, C.c_int]),
     "edpc_session_close": (None, [P]),
+    "edpc_archive_plan": (C.c_int, [P, C.c_size_t, C.POINTER(Cfg), C.POINTER(SplitPlan)]),
+    "edpc_compress_many": (C.c_int, [P, P, C.c_size_t, C.POINTER(Cfg), C.POINTER(P), C.POINTER(C.c_size_t)]),
+    "edpc_encoder_open_many": (C.c_int, [C.POINTER(Cfg), P, P, C.c_size_t, C.c_int, P, C.POINTER(P)]),
+    "edpc_archive_info": (C.c_int, [P, C.c_size_t, C.POINTER(C.c_uint64), P]),
+    "edpc_decompress_many": (C.c_int, [P, C.c_size_t, C.POINTER(P), C.POINTER(P), C.POINTER(C.c_size_t)]),
     "edpc_cdf_quantize": (C.c_int, [P, C.c_uint32, P, P, P]),
     "edpc_range_encode": (C.c_int, [P, C.c_uint32, C.c_uint32, P, C.c_uint32, P, P]),
     "edpc_range_encode_noalloc": (C.c_int, [P, C.c_uint32, C.c_uint32, P, C.c_uint32, P, P]),
@@ -87,6 +104,8 @@ PROTOS = {
     "edpc_model_forward": (C.c_int, [P, P, P, P]),
     "edpc_model_backward": (C.c_int, [P, P, P, P, P, P]),
     "edpc_model_train_step": (C.c_int, [P, P, P, P]),
+    "edpc_model_set_tiles": (C.c_int, [P, P, C.c_uint32]),
+    "edpc_model_tune_tiles": (C.c_int, [P, P, C.c_uint32, C.POINTER(C.c_uint32)]),
 }
 
 _LIB = None

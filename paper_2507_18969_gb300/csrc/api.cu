@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include "archive.cuh"
 #include "engine.cuh"
 
 using namespace edpc;
@@ -59,10 +60,12 @@ extern "C" void edpc_default_cfg(edpc_cfg* c) {
   c->seed = 1;
 }
 
-static int check_cfg(const edpc_cfg* c) {
+// streams = 0 (autotuned stream count) is accepted for file sets only.
+static int check_cfg(const edpc_cfg* c, bool auto_streams = false) {
   if (!c) return fail(EDPC_EINVAL, "cfg is NULL");
   if (c->version != EDPC_ABI_VERSION) return fail(EDPC_EINVAL, "cfg.version != EDPC_ABI_VERSION");
-  if (c->streams < 1 || c->streams > 65536) return fail(EDPC_EINVAL, "streams must be in [1, 65536]");
+  if ((c->streams < 1 && !auto_streams) || c->streams > kMaxStreams)
+    return fail(EDPC_EINVAL, auto_streams ? "streams must be in [0, 65535]" : "streams must be in [1, 65535]");
   if (c->context < 1 || c->context > 256) return fail(EDPC_EINVAL, "context must be in [1, 256]");
   if (c->embed_dim < 8 || c->embed_dim > 64 || c->embed_dim % 8)
     return fail(EDPC_EINVAL, "embed_dim must be a multiple of 8 in [8, 64]");
@@ -156,15 +159,27 @@ __global__ void gather_streams_kernel(const uint8_t* __restrict__ src, const uns
 constexpr uint32_t kMagic = 0x43504445u;  // "EDPC" little-endian
 constexpr size_t kFixedHeader = 88;
 
+// Variant 0: one input, balanced split, size-heuristic GEMM tiles.
+// Variant 1: extended header after the fixed part:
+//   u64 nfiles, u64 L (stream length of the file-set split; 0 = one input
+//   with the balanced split), u32 ntile, u32 0, u64 size[nfiles],
+//   u8 tile[ntile] (padded to 4 bytes): the GEMM tile code of every site.
 struct Header {
   edpc_cfg cfg;
   uint64_t n = 0;
   uint32_t b = 0;
   uint64_t checksum = 0;
   uint32_t variant = 0;
+  uint64_t L = 0;
+  std::vector<uint64_t> sizes;
+  std::vector<uint8_t> tiles;
   std::vector<uint32_t> len;
   size_t header_len = 0;
 };
+
+size_t ext_bytes(const Header& h) {
+  return h.variant == 1 ? 24 + 8 * h.sizes.size() + ((h.tiles.size() + 3) & ~(size_t)3) : 0;
+}
 
 template <class T>
 void put(std::vector<uint8_t>& v, size_t off, T x) {
@@ -178,7 +193,8 @@ T get(const uint8_t* p, size_t off) {
 }
 
 std::vector<uint8_t> write_header(const Header& h) {
-  std::vector<uint8_t> v(kFixedHeader + 4 * (size_t)h.b + 4, 0);
+  const size_t ext = ext_bytes(h);
+  std::vector<uint8_t> v(kFixedHeader + ext + 4 * (size_t)h.b + 4, 0);
   put<uint32_t>(v, 0, kMagic);
   put<uint32_t>(v, 4, EDPC_FORMAT_VERSION);
   put<uint32_t>(v, 8, (uint32_t)v.size());
@@ -198,7 +214,19 @@ std::vector<uint8_t> write_header(const Header& h) {
   put<uint64_t>(v, 72, h.checksum);
   put<uint32_t>(v, 80, h.variant);
   put<uint32_t>(v, 84, 0);
-  for (uint32_t s = 0; s < h.b; ++s) put<uint32_t>(v, kFixedHeader + 4 * s, h.len[s]);
+  if (h.variant == 1) {
+    size_t o = kFixedHeader;
+    put<uint64_t>(v, o, (uint64_t)h.sizes.size());
+    put<uint64_t>(v, o + 8, h.L);
+    put<uint32_t>(v, o + 16, (uint32_t)h.tiles.size());
+    o += 24;
+    for (uint64_t sz : h.sizes) {
+      put<uint64_t>(v, o, sz);
+      o += 8;
+    }
+    if (!h.tiles.empty()) memcpy(v.data() + o, h.tiles.data(), h.tiles.size());
+  }
+  for (uint32_t s = 0; s < h.b; ++s) put<uint32_t>(v, kFixedHeader + ext + 4 * (size_t)s, h.len[s]);
   put<uint32_t>(v, v.size() - 4, crc32_ieee(v.data(), v.size() - 4));
   return v;
 }
@@ -210,9 +238,25 @@ int read_header(const uint8_t* p, size_t n, Header* h) {
   if (get<uint32_t>(p, 4) != EDPC_FORMAT_VERSION) return fail(EDPC_EVERSION, "unsupported format version");
   size_t hl = get<uint32_t>(p, 8);
   uint32_t b = get<uint32_t>(p, 68);
-  if (b < 1 || b > 65536 || hl != kFixedHeader + 4 * (size_t)b + 4 || hl > n)
+  if (b < 1 || b > (uint32_t)kMaxStreams || hl < kFixedHeader + 4 * (size_t)b + 4 || hl > n)
     return fail(EDPC_ECORRUPT, "bad header length or stream count");
   if (crc32_ieee(p, hl - 4) != get<uint32_t>(p, hl - 4)) return fail(EDPC_ECORRUPT, "header CRC mismatch");
+  h->variant = get<uint32_t>(p, 80);
+  size_t ext = 0;
+  if (h->variant == 1) {
+    if (hl < kFixedHeader + 24 + 4 * (size_t)b + 4) return fail(EDPC_ECORRUPT, "bad extended header length");
+    const uint64_t nf = get<uint64_t>(p, kFixedHeader);
+    h->L = get<uint64_t>(p, kFixedHeader + 8);
+    const uint32_t nt = get<uint32_t>(p, kFixedHeader + 16);
+    if (nf > hl / 8 || nt > (uint32_t)TcPlan::kMaxSites) return fail(EDPC_ECORRUPT, "bad extended header counts");
+    h->sizes.resize(nf);
+    for (uint64_t f = 0; f < nf; ++f) h->sizes[f] = get<uint64_t>(p, kFixedHeader + 24 + 8 * f);
+    h->tiles.assign(p + kFixedHeader + 24 + 8 * nf, p + kFixedHeader + 24 + 8 * nf + nt);
+    ext = ext_bytes(*h);
+  } else if (h->variant != 0) {
+    return fail(EDPC_EARCH, "unknown header variant " + std::to_string(h->variant));
+  }
+  if (hl != kFixedHeader + ext + 4 * (size_t)b + 4) return fail(EDPC_ECORRUPT, "bad header length");
   edpc_default_cfg(&h->cfg);
   h->cfg.precision = get<uint32_t>(p, 12);
   h->cfg.context = get<uint32_t>(p, 16);
@@ -227,18 +271,24 @@ int read_header(const uint8_t* p, size_t n, Header* h) {
   h->cfg.streams = get<uint32_t>(p, 64);
   h->b = b;
   h->checksum = get<uint64_t>(p, 72);
-  h->variant = get<uint32_t>(p, 80);
-  if (h->variant != 0) return fail(EDPC_EARCH, "unknown GEMM variant in header");
-  int r = check_cfg(&h->cfg);
+  int r = check_cfg(&h->cfg, h->variant == 1 && h->L > 0);
   if (r != EDPC_OK) return fail(EDPC_ECORRUPT, "header holds an invalid configuration: " + g_last_error);
   h->len.resize(b);
   uint64_t total = 0;
   for (uint32_t s = 0; s < b; ++s) {
-    h->len[s] = get<uint32_t>(p, kFixedHeader + 4 * (size_t)s);
+    h->len[s] = get<uint32_t>(p, kFixedHeader + ext + 4 * (size_t)s);
     total += h->len[s];
   }
   h->header_len = hl;
   if (hl + total != n) return fail(EDPC_ECORRUPT, "stream lengths do not match the bitstream size");
+  if (h->variant == 1 && h->L > 0) {
+    uint64_t tot = 0;
+    for (uint64_t sz : h->sizes) tot += sz;
+    if (tot != h->n) return fail(EDPC_ECORRUPT, "file sizes do not add up to the input length");
+    if (archive_stream_count(h->sizes.data(), h->sizes.size(), h->L) != b)
+      return fail(EDPC_ECORRUPT, "stream count does not match the file-set split");
+    return EDPC_OK;
+  }
   uint32_t be = (uint32_t)std::min<uint64_t>(h->cfg.streams, std::max<uint64_t>(1, h->n / h->cfg.context));
   if (be != b) return fail(EDPC_ECORRUPT, "stream count does not match the split rule");
   return EDPC_OK;
@@ -266,6 +316,13 @@ struct edpc_session {
   edpc_cfg cfg{};
   Model model;
   Split sp{};
+  StreamLayout lay;                    // host copy of every stream's byte range
+  unsigned long long* seg = nullptr;   // device: b + 1 stream offsets (explicit split)
+  ActivePoint* cp = nullptr;           // device: active-count change points
+  uint32_t variant = 0;                // header variant written by the encoder
+  uint64_t arch_L = 0;                 // file-set stream length (variant 1)
+  std::vector<uint64_t> file_sizes;    // file-set sizes (variant 1)
+  std::vector<uint8_t> tiles;          // GEMM tile codes recorded in the header
   int b = 0;
   uint64_t n = 0;
   cudaStream_t st = nullptr;
@@ -320,7 +377,7 @@ struct edpc_session {
   Model::StepIO io;
 
   ~edpc_session();
-  int setup_common(const edpc_cfg& c, uint64_t n_, void* stream);
+  int setup_common(const edpc_cfg& c, uint64_t n_, void* stream, const StreamLayout* explicit_lay = nullptr);
   int capture_graph();
   int launch_step();
   int code_pending();
@@ -354,15 +411,30 @@ edpc_session::~edpc_session() {
   cudaFree(bits_off);
   cudaFree(bits_len);
   cudaFree(ds);
+  cudaFree(seg);
+  cudaFree(cp);
   if (st_coder) cudaStreamDestroy(st_coder);
   if (own_stream && st) cudaStreamDestroy(st);
 }
 
-int edpc_session::setup_common(const edpc_cfg& c, uint64_t n_, void* stream) {
+int edpc_session::setup_common(const edpc_cfg& c, uint64_t n_, void* stream, const StreamLayout* explicit_lay) {
   cfg = c;
   n = n_;
-  b = effective_streams(c, n);
-  sp = make_split(n, b);
+  if (explicit_lay) {
+    lay = *explicit_lay;
+    b = lay.streams();
+    if (b < 1 || b > (int)kMaxStreams) return fail(EDPC_EINVAL, "stream count out of range");
+    sp = Split{(long long)n, 0, 0};
+  } else {
+    b = effective_streams(c, n);
+    sp = make_split(n, b);
+    lay.off.resize(b);
+    lay.len.resize(b);
+    for (int i = 0; i < b; ++i) {
+      lay.off[i] = sp.off(i);
+      lay.len[i] = sp.len(i);
+    }
+  }
   pipeline = !(c.flags & EDPC_FLAG_NO_PIPELINE);
   use_graph = !(c.flags & EDPC_FLAG_NO_GRAPH);
   if (stream) {
@@ -378,8 +450,30 @@ int edpc_session::setup_common(const edpc_cfg& c, uint64_t n_, void* stream) {
   }
   EDPC_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
   EDPC_CUDA(cudaMalloc(&scratch, 64));
+  if (explicit_lay) {
+    // stream table and the steps at which the active count drops (Q12 masking)
+    std::vector<unsigned long long> so(b + 1);
+    for (int i = 0; i < b; ++i) so[i] = (unsigned long long)lay.off[i];
+    so[b] = so[b - 1] + (unsigned long long)lay.len[b - 1];
+    std::vector<long long> ls(lay.len);
+    std::sort(ls.begin(), ls.end());
+    std::vector<ActivePoint> pts;
+    for (size_t k = 0; k < ls.size(); ++k) {
+      if (ls[k] <= (long long)c.context || (k + 1 < ls.size() && ls[k + 1] == ls[k])) continue;
+      pts.push_back({(int)ls[k], (int)(ls.size() - k - 1)});  // from step len on, the longer ones stay
+    }
+    EDPC_CUDA(cudaMalloc(&seg, 8 * (size_t)(b + 1)));
+    EDPC_CUDA(cudaMalloc(&cp, sizeof(ActivePoint) * std::max<size_t>(1, pts.size())));
+    EDPC_CUDA(cudaMemcpyAsync(seg, so.data(), 8 * (size_t)(b + 1), cudaMemcpyHostToDevice, st));
+    if (!pts.empty())
+      EDPC_CUDA(cudaMemcpyAsync(cp, pts.data(), sizeof(ActivePoint) * pts.size(), cudaMemcpyHostToDevice, st));
+    EDPC_CUDA(cudaStreamSynchronize(st));
+    sp.seg = seg;
+    sp.cp = cp;
+    sp.ncp = (int)pts.size();
+  }
   EDPC_TRY(model.init(c, b));
-  long long L = sp.q + (sp.rem ? 1 : 0);
+  long long L = lay.max_len();
   steps_total = L > (long long)c.context ? (uint64_t)(L - c.context) : 0;
   chunk = 64;
   ring_slots = 2 * chunk;
@@ -508,12 +602,18 @@ static int session_prepare_events(edpc_session* s) {
   return EDPC_OK;
 }
 
-extern "C" int edpc_encoder_open(const edpc_cfg* cfg, const uint8_t* data, size_t len, int data_on_device,
-                                 void* cuda_stream, edpc_session** out) {
-  if (!out) return fail(EDPC_EINVAL, "out is NULL");
-  *out = nullptr;
-  EDPC_TRY(check_cfg(cfg));
-  if (!data && len) return fail(EDPC_EINVAL, "data is NULL");
+// Opens an encoder over the concatenation of `nparts` buffers (host, or
+// device when data_on_device). A single device buffer is used in place.
+// lay: explicit stream layout (file sets), else the balanced split.
+// tune: time the GEMM tiles and record the chosen codes (header variant 1).
+static int encoder_open_impl(const edpc_cfg* cfg, const uint8_t* const* parts, const uint64_t* part_len,
+                             size_t nparts, int data_on_device, void* cuda_stream, const StreamLayout* lay,
+                             uint32_t variant, uint64_t arch_L, bool tune, edpc_session** out) {
+  uint64_t len = 0;
+  for (size_t f = 0; f < nparts; ++f) {
+    if (!parts[f] && part_len[f]) return fail(EDPC_EINVAL, "data is NULL");
+    len += part_len[f];
+  }
   EDPC_TRY(current_device_ok());
   edpc_session* s = new (std::nothrow) edpc_session();
   if (!s) return fail(EDPC_ENOMEM, "host allocation failed");
@@ -522,18 +622,27 @@ extern "C" int edpc_encoder_open(const edpc_cfg* cfg, const uint8_t* data, size_
     return r;
   };
   s->encoder = true;
-  int r = s->setup_common(*cfg, len, cuda_stream);
+  int r = s->setup_common(*cfg, len, cuda_stream, lay);
   if (r != EDPC_OK) return bail(r);
   if ((r = session_prepare_events(s)) != EDPC_OK) return bail(r);
   cudaStream_t st = s->st;
+  s->variant = variant;
+  s->arch_L = arch_L;
+  if (variant == 1 && lay) s->file_sizes.assign(part_len, part_len + nparts);
   // input bytes on the device
-  if (data_on_device) {
-    s->data = const_cast<uint8_t*>(data);
+  if (data_on_device && nparts == 1) {
+    s->data = const_cast<uint8_t*>(parts[0]);
   } else {
-    if (cudaMalloc(&s->data, std::max<size_t>(len, 1)) != cudaSuccess) return bail(fail(EDPC_ENOMEM, "input buffer"));
+    if (cudaMalloc(&s->data, std::max<uint64_t>(len, 1)) != cudaSuccess) return bail(fail(EDPC_ENOMEM, "input buffer"));
     s->own_data = true;
-    if (len && cudaMemcpyAsync(s->data, data, len, cudaMemcpyHostToDevice, st) != cudaSuccess)
-      return bail(fail(EDPC_ECUDA, "input copy failed"));
+    uint64_t o = 0;
+    for (size_t f = 0; f < nparts; ++f) {
+      if (part_len[f] && cudaMemcpyAsync(s->data + o, parts[f], part_len[f],
+                                         data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                         st) != cudaSuccess)
+        return bail(fail(EDPC_ECUDA, "input copy failed"));
+      o += part_len[f];
+    }
   }
   // per-stream output buffers: a stream of L bytes codes to at most 2L + L/256 + 64 bytes
   const int b = s->b;
@@ -541,7 +650,8 @@ extern "C" int edpc_encoder_open(const edpc_cfg* cfg, const uint8_t* data, size_
   std::vector<uint32_t> cap(b);
   unsigned long long tot = 0;
   for (int i = 0; i < b; ++i) {
-    long long L = s->sp.len(i);
+    long long L = s->lay.len[i];
+    if (L > (1ll << 31) - (1ll << 24)) return bail(fail(EDPC_EINVAL, "a stream is longer than 2 GiB - 16 MiB"));
     cap[i] = (uint32_t)(2 * L + (L >> 8) + 64);
     s->h_out_off[i] = tot;
     tot += (cap[i] + 15) & ~15u;
@@ -555,13 +665,16 @@ extern "C" int edpc_encoder_open(const edpc_cfg* cfg, const uint8_t* data, size_
   if (cudaMemcpyAsync(s->out_off, s->h_out_off.data(), 8 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(s->out_cap, cap.data(), 4 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return bail(fail(EDPC_ECUDA, "encoder setup copies"));
+  if (tune && cfg->precision == EDPC_BF16) {
+    if ((r = s->model.tune_tiles(st)) != EDPC_OK) return bail(r);
+    s->tiles.assign(s->model.tile_code, s->model.tile_code + TcPlan::kMaxSites);
+  }
   // Algorithm 1, first line: the first K bytes of each stream with equal probability
   if (launch_prefix_encode(s->es, s->data, s->sp, (int)cfg->context, b, s->out, s->out_off, s->out_cap, st) !=
       cudaSuccess)
     return bail(fail(EDPC_ECUDA, "prefix encode launch"));
   long long i0 = cfg->context;
-  int bact = (i0 < s->sp.q) ? b : (i0 == s->sp.q ? s->sp.rem : 0);
-  if ((r = s->model.set_ctl_for_step((int)i0, 1, bact, s->ring_slots, st)) != EDPC_OK) return bail(r);
+  if ((r = s->model.set_ctl_for_step((int)i0, 1, s->lay.active_at(i0), s->ring_slots, st)) != EDPC_OK) return bail(r);
   s->io.mode = 0;
   s->io.data = s->data;
   s->io.sp = s->sp;
@@ -571,6 +684,16 @@ extern "C" int edpc_encoder_open(const edpc_cfg* cfg, const uint8_t* data, size_
   if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(EDPC_ECUDA, "encoder open sync"));
   *out = s;
   return EDPC_OK;
+}
+
+extern "C" int edpc_encoder_open(const edpc_cfg* cfg, const uint8_t* data, size_t len, int data_on_device,
+                                 void* cuda_stream, edpc_session** out) {
+  if (!out) return fail(EDPC_EINVAL, "out is NULL");
+  *out = nullptr;
+  EDPC_TRY(check_cfg(cfg));
+  const uint64_t l = len;
+  const bool tune = (cfg->flags & EDPC_FLAG_TUNE_TILES) != 0;
+  return encoder_open_impl(cfg, &data, &l, 1, data_on_device, cuda_stream, nullptr, tune ? 1u : 0u, 0, tune, out);
 }
 
 extern "C" int edpc_session_run(edpc_session* s, uint64_t max_steps, int sync, uint64_t* steps_done) {
@@ -628,6 +751,10 @@ extern "C" int edpc_encoder_finish(edpc_session* s, uint8_t** out, size_t* out_l
   h.n = s->n;
   h.b = (uint32_t)b;
   h.len = len;
+  h.variant = s->variant;
+  h.L = s->arch_L;
+  h.sizes = s->file_sizes;
+  h.tiles = s->tiles;
   EDPC_TRY(device_checksum(s->data, s->n, s->scratch, st, &h.checksum));
   std::vector<uint8_t> hdr = write_header(h);
   uint8_t* buf = static_cast<uint8_t*>(malloc(hdr.size() + total + 1));
@@ -682,12 +809,17 @@ extern "C" int edpc_decoder_open(const uint8_t* bits, size_t bits_len, void* out
     return r;
   };
   s->encoder = false;
-  int r = s->setup_common(h.cfg, h.n, cuda_stream);
+  StreamLayout lay;
+  const bool file_set = h.variant == 1 && h.L > 0;
+  if (file_set) archive_split(h.sizes.data(), h.sizes.size(), h.L, &lay);
+  int r = s->setup_common(h.cfg, h.n, cuda_stream, file_set ? &lay : nullptr);
   if (r != EDPC_OK) return bail(r);
   if ((r = session_prepare_events(s)) != EDPC_OK) return bail(r);
   cudaStream_t st = s->st;
   const int b = s->b;
   s->checksum_expected = h.checksum;
+  // the encoder's GEMM tiles (they fix the accumulation layout of the replay)
+  if (!h.tiles.empty() && (r = s->model.set_tiles(h.tiles.data(), (int)h.tiles.size())) != EDPC_OK) return bail(r);
   if (out_device) {
     s->data = static_cast<uint8_t*>(out_device);
   } else {
@@ -715,8 +847,7 @@ extern "C" int edpc_decoder_open(const uint8_t* bits, size_t bits_len, void* out
           cudaSuccess)
     return bail(fail(EDPC_ECUDA, "decoder prefix launch"));
   long long i0 = h.cfg.context;
-  int bact = (i0 < s->sp.q) ? b : (i0 == s->sp.q ? s->sp.rem : 0);
-  if ((r = s->model.set_ctl_for_step((int)i0, 1, bact, s->ring_slots, st)) != EDPC_OK) return bail(r);
+  if ((r = s->model.set_ctl_for_step((int)i0, 1, s->lay.active_at(i0), s->ring_slots, st)) != EDPC_OK) return bail(r);
   s->io.mode = 1;
   s->io.data = s->data;
   s->io.sp = s->sp;
@@ -808,6 +939,124 @@ extern "C" int edpc_decompress(const uint8_t* bits, size_t bits_len, uint8_t** o
 }
 
 // ==========================================================================================
+// file sets (archives)
+// ==========================================================================================
+static int plan_file_set(const size_t* lens, size_t nfiles, const edpc_cfg* cfg, edpc_split_plan* plan,
+                         std::vector<uint64_t>* sizes) {
+  if (!lens && nfiles) return fail(EDPC_EINVAL, "lens is NULL");
+  EDPC_TRY(check_cfg(cfg, true));
+  sizes->assign(lens, lens + nfiles);
+  memset(plan, 0, sizeof(*plan));
+  uint64_t L = 0;
+  if (cfg->streams > 0) {
+    L = archive_stream_len(sizes->data(), nfiles, cfg->streams);
+  } else {
+    EDPC_TRY(current_device_ok());
+    TunedPlan tp;
+    EDPC_TRY(archive_autotune(*cfg, sizes->data(), nfiles, &tp));
+    L = tp.L;
+    plan->est_seconds = tp.est_seconds;
+    plan->step_ms_t0 = tp.step_ms_t0;
+    plan->step_ms_per_stream = tp.step_ms_per_stream;
+  }
+  const uint64_t b = archive_stream_count(sizes->data(), nfiles, L);
+  if (b > kMaxStreams) return fail(EDPC_EINVAL, "the file set needs more than 65535 streams");
+  plan->stream_len = L;
+  plan->streams = (uint32_t)b;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_archive_plan(const size_t* lens, size_t nfiles, const edpc_cfg* cfg, edpc_split_plan* plan) {
+  if (!plan) return fail(EDPC_EINVAL, "plan is NULL");
+  std::vector<uint64_t> sizes;
+  return plan_file_set(lens, nfiles, cfg, plan, &sizes);
+}
+
+extern "C" int edpc_encoder_open_many(const edpc_cfg* cfg, const uint8_t* const* bufs, const size_t* lens,
+                                      size_t nfiles, int data_on_device, void* cuda_stream, edpc_session** out) {
+  if (!out) return fail(EDPC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!bufs && nfiles) return fail(EDPC_EINVAL, "bufs is NULL");
+  edpc_split_plan plan;
+  std::vector<uint64_t> sizes;
+  EDPC_TRY(plan_file_set(lens, nfiles, cfg, &plan, &sizes));
+  StreamLayout lay;
+  archive_split(sizes.data(), nfiles, plan.stream_len, &lay);
+  edpc_cfg c = *cfg;
+  std::vector<const uint8_t*> parts(bufs, bufs + nfiles);
+  return encoder_open_impl(&c, parts.data(), sizes.data(), nfiles, data_on_device, cuda_stream, &lay, 1u,
+                           plan.stream_len, true, out);
+}
+
+extern "C" int edpc_compress_many(const uint8_t* const* bufs, const size_t* lens, size_t nfiles, const edpc_cfg* cfg,
+                                  uint8_t** out, size_t* out_len) {
+  if (!out || !out_len) return fail(EDPC_EINVAL, "NULL output pointer");
+  edpc_session* s = nullptr;
+  EDPC_TRY(edpc_encoder_open_many(cfg, bufs, lens, nfiles, 0, nullptr, &s));
+  int r = edpc_encoder_finish(s, out, out_len);
+  edpc_session_close(s);
+  return r;
+}
+
+extern "C" int edpc_archive_info(const uint8_t* bits, size_t bits_len, uint64_t* nfiles, uint64_t* sizes) {
+  if (!nfiles) return fail(EDPC_EINVAL, "nfiles is NULL");
+  Header h;
+  EDPC_TRY(read_header(bits, bits_len, &h));
+  if (h.variant == 1 && h.L > 0) {
+    *nfiles = h.sizes.size();
+    if (sizes) memcpy(sizes, h.sizes.data(), 8 * h.sizes.size());
+  } else {
+    *nfiles = 1;
+    if (sizes) sizes[0] = h.n;
+  }
+  return EDPC_OK;
+}
+
+extern "C" int edpc_decompress_many(const uint8_t* bits, size_t bits_len, uint8_t*** outs, size_t** lens,
+                                    size_t* nfiles) {
+  if (!outs || !lens || !nfiles) return fail(EDPC_EINVAL, "NULL output pointer");
+  *outs = nullptr;
+  *lens = nullptr;
+  *nfiles = 0;
+  uint64_t nf = 0;
+  EDPC_TRY(edpc_archive_info(bits, bits_len, &nf, nullptr));
+  std::vector<uint64_t> sizes(nf);
+  EDPC_TRY(edpc_archive_info(bits, bits_len, &nf, sizes.data()));
+  uint64_t total = 0;
+  for (uint64_t v : sizes) total += v;
+  // one block: nf pointers, then the files' bytes back to back
+  const size_t head = sizeof(uint8_t*) * (size_t)std::max<uint64_t>(nf, 1);
+  uint8_t* block = static_cast<uint8_t*>(malloc(head + std::max<uint64_t>(total, 1)));
+  size_t* ls = static_cast<size_t*>(malloc(sizeof(size_t) * (size_t)std::max<uint64_t>(nf, 1)));
+  if (!block || !ls) {
+    free(block);
+    free(ls);
+    return fail(EDPC_ENOMEM, "output buffers");
+  }
+  uint8_t* data = block + head;
+  edpc_session* s = nullptr;
+  int r = edpc_decoder_open(bits, bits_len, nullptr, nullptr, &s);
+  if (r == EDPC_OK) r = edpc_decoder_finish(s, data);
+  edpc_session_close(s);
+  if (r != EDPC_OK) {
+    free(block);
+    free(ls);
+    return r;
+  }
+  uint8_t** ptrs = reinterpret_cast<uint8_t**>(block);
+  uint64_t o = 0;
+  for (uint64_t f = 0; f < nf; ++f) {
+    ptrs[f] = data + o;
+    ls[f] = (size_t)sizes[f];
+    o += sizes[f];
+  }
+  *outs = ptrs;
+  *lens = ls;
+  *nfiles = (size_t)nf;
+  return EDPC_OK;
+}
+
+// ==========================================================================================
 // single-kernel entry points
 // ==========================================================================================
 extern "C" int edpc_cdf_quantize(const float* p, uint32_t rows, uint32_t* freq, uint32_t* cum, void* stream) {
@@ -881,7 +1130,7 @@ extern "C" int edpc_model_create(const edpc_cfg* cfg, uint32_t streams, edpc_mod
   if (!out) return fail(EDPC_EINVAL, "out is NULL");
   *out = nullptr;
   EDPC_TRY(check_cfg(cfg));
-  if (streams < 1 || streams > 65536) return fail(EDPC_EINVAL, "streams must be in [1, 65536]");
+  if (streams < 1 || streams > kMaxStreams) return fail(EDPC_EINVAL, "streams must be in [1, 65535]");
   EDPC_TRY(current_device_ok());
   edpc_model* m = new (std::nothrow) edpc_model();
   if (!m) return fail(EDPC_ENOMEM, "host allocation failed");
@@ -938,13 +1187,13 @@ static int model_prepare(edpc_model* mm, const uint8_t* ctx, const uint8_t* targ
                          uint32_t t, Model::StepIO* io) {
   Model& m = mm->m;
   const int b = m.d.b;
-  std::vector<uint8_t> zeros(b, 0);
+  std::vector<uint8_t> zeros(b, 0), ones(b, 1);
   EDPC_CUDA(cudaMemcpy(m.ctx, ctx, (size_t)b * m.d.K, cudaMemcpyHostToDevice));
   EDPC_CUDA(cudaMemcpy(mm->tgt, targets ? targets : zeros.data(), b, cudaMemcpyHostToDevice));
-  EDPC_CUDA(cudaMemcpy(mm->act, active ? active : zeros.data(), b, cudaMemcpyHostToDevice));
+  // a forward pass without a mask predicts for every stream
+  EDPC_CUDA(cudaMemcpy(mm->act, active ? active : ones.data(), b, cudaMemcpyHostToDevice));
   int bact = 0;
-  if (active)
-    for (int i = 0; i < b; ++i) bact += active[i] != 0;
+  for (int i = 0; i < b; ++i) bact += active ? active[i] != 0 : 1;
   EDPC_TRY(m.set_ctl_for_step(0, (int)t, bact, 1, 0));
   io->mode = 2;
   io->targets = mm->tgt;
@@ -997,5 +1246,21 @@ extern "C" int edpc_model_train_step(edpc_model* mm, const uint8_t* ctx, const u
   EDPC_TRY(m.step(io, 0));
   EDPC_CUDA(cudaDeviceSynchronize());
   mm->t += 1;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_model_set_tiles(edpc_model* mm, const uint8_t* codes, uint32_t n) {
+  if (!mm) return fail(EDPC_EINVAL, "model is NULL");
+  EDPC_TRY(mm->m.set_tiles(codes, (int)n));
+  return EDPC_OK;
+}
+
+extern "C" int edpc_model_tune_tiles(edpc_model* mm, uint8_t* codes, uint32_t cap, uint32_t* n) {
+  if (!mm) return fail(EDPC_EINVAL, "model is NULL");
+  EDPC_TRY(mm->m.tune_tiles(0));
+  EDPC_CUDA(cudaDeviceSynchronize());
+  const uint32_t k = (uint32_t)TcPlan::kMaxSites;
+  if (codes) memcpy(codes, mm->m.tile_code, std::min(cap, k));
+  if (n) *n = k;
   return EDPC_OK;
 }

@@ -16,6 +16,7 @@ constexpr int kTBits = 16;
 constexpr uint32_t kTop = 1u << 24;  // range coder renormalisation threshold
 constexpr uint32_t kSkip = 0xFFFFFFFFu;
 constexpr int kMaxBlocks = 16;
+constexpr uint32_t kMaxStreams = 65535;  // streams index grid dimension y of the FDM adjoint
 constexpr float kLnEps = 1e-5f;
 constexpr float kB1 = 0.9f, kB2 = 0.999f, kAdamEps = 1e-8f;
 constexpr int kFdmTid = 1023;        // tensor id of the FDM in the initial-value rule
@@ -56,16 +57,37 @@ struct StepCtl {
   float bc2;      // 1 - beta2^t
   float lr;
   int err;        // sticky error bits
-  int pad[7];
+  int cpi;        // next entry of the active-count table (uneven splits)
+  int pad[6];
 };
 
-// Balanced split of n bytes into b streams: q or q+1 bytes each.
+// Change point of the active-stream count: from time index i on, bact
+// streams are active (uneven splits; see ActiveTable).
+struct ActivePoint {
+  int i;
+  int bact;
+};
+
+// Split of the input into b streams.
+//   Balanced (seg == nullptr): n bytes into b streams of q or q+1 bytes.
+//   Explicit (seg != nullptr): stream s is bytes [seg[s], seg[s+1]) of the
+//   input (device array of b+1 offsets); cp[0..ncp) lists, in increasing i,
+//   the time indices at which the count of active streams changes.
+// off/len dereference seg, so the explicit form is for device code; host
+// code keeps its own copy of the offsets.
 struct Split {
   long long n;
   long long q;
   int rem;
-  __host__ __device__ long long off(int s) const { return (long long)s * q + (s < rem ? s : rem); }
-  __host__ __device__ long long len(int s) const { return q + (s < rem ? 1 : 0); }
+  const unsigned long long* seg = nullptr;
+  const ActivePoint* cp = nullptr;
+  int ncp = 0;
+  __host__ __device__ long long off(int s) const {
+    return seg ? (long long)seg[s] : (long long)s * q + (s < rem ? s : rem);
+  }
+  __host__ __device__ long long len(int s) const {
+    return seg ? (long long)(seg[s + 1] - seg[s]) : q + (s < rem ? 1 : 0);
+  }
 };
 
 // Range coder states (one per stream), kept in device memory between launches.

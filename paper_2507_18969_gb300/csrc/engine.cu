@@ -332,9 +332,13 @@ int Model::block_fwd(int j, const float* Xin, float* Xout, cudaStream_t st) {
   return EDPC_OK;
 }
 
-int Model::fdm_fwd_call(cudaStream_t st) {
+int Model::fdm_fwd_call(const StepIO& io, cudaStream_t st) {
   if (timing && ev_fdm[0]) EDPC_CUDA(record_timing(ev_fdm[0], st));
-  EDPC_CUDA(launch_fdm_fwd(Xp, U, Y, d.b, d.Fp, st, Yb, YbT, d.ldT, &ctl->err));  // Eq. 15
+  FdmAct act;
+  act.ctl = ctl;
+  act.sp = io.sp;
+  act.active = io.mode == 2 ? io.active : nullptr;
+  EDPC_CUDA(launch_fdm_fwd(Xp, U, Y, d.b, d.Fp, st, Yb, YbT, d.ldT, &ctl->err, act));  // Eq. 15
   if (timing && ev_fdm[1]) EDPC_CUDA(record_timing(ev_fdm[1], st));
   return EDPC_OK;
 }
@@ -343,7 +347,7 @@ int Model::forward_f32(const StepIO& io, cudaStream_t st) {
   EDPC_CUDA(launch_embed(io.mode == 2 ? nullptr : io.data, io.sp, ctl, P + po.E, d.b, d.K, d.D, S[0], ctx, st));
   for (int j = 0; j < d.nloc; ++j) EDPC_TRY(block_fwd(j, S[j], S[j + 1], st));
   EDPC_TRY(linear_fwd(S[d.nloc], d.b, d.F, po.W1, po.b1, d.Fp, nullptr, Xp, st));  // Eq. 14
-  EDPC_TRY(fdm_fwd_call(st));
+  EDPC_TRY(fdm_fwd_call(io, st));
   EDPC_TRY(linear_fwd(Y, d.b, d.Fp, po.W2, po.b2, d.F, nullptr, S[d.nloc + 1], st));  // Eq. 16
   for (int j = d.nloc; j < d.n; ++j) EDPC_TRY(block_fwd(j, S[j + 1], S[j + 2], st));
   EDPC_TRY(linear_fwd(S[d.n + 1], d.b, d.F, po.Wh, po.bh, 256, nullptr, z, st));
@@ -431,8 +435,11 @@ int Model::backward_f32(const StepIO& io, cudaStream_t st) {
 int Model::build_tc_plan() {
   const int kH = d.k * d.H;
   const int T = d.ldT;
-  // N tile: 32 while 64-wide tiles would leave the GPU mostly idle (small b), else 64.
-  auto bn_for = [&](int N) { return ((d.b + 127) / 128) * ((N + 63) / 64) < 2 * 152 ? 32 : 64; };
+  // N tile: the site's tile code when one is set (tuned or read from a
+  // bitstream); else 32 while 64-wide tiles would leave the GPU mostly idle
+  // (small b), else 64.
+  auto bn_heur = [&](int N) { return ((d.b + 127) / 128) * ((N + 63) / 64) < 2 * 152 ? 32 : 64; };
+  auto bn_site = [&](int id, int N) { return tile_code[id] ? 32 * (int)tile_code[id] : bn_heur(N); };
   auto site = [&](int id, int M, int N, int K, const void* a, int a_rows, int a_cols, int a_ld, const void* b,
                   int b_rows, int b_cols, int b_ld, int bn, int box_b) -> int {
     TcGemm& g = tcp.site[id];
@@ -469,7 +476,7 @@ int Model::build_tc_plan() {
     // Eq. 13: out GEMM + residual (the output's BF16 copies when a GEMM reads it next)
     {
       int id = blk_site(OUT_FWD, j);
-      int bn = bn_for(F);
+      int bn = bn_site(id, F);
       EDPC_TRY(site(id, b, F, H, q.Gb, b, H, H, Pb + o.Wo, F, H, H, bn, bn));
       TcGemm& g = tcp.site[id];
       int out = (j < d.nloc) ? j + 1 : j + 2;
@@ -510,7 +517,7 @@ int Model::build_tc_plan() {
     }
     {  // dWo = dOut^T G
       int id = blk_site(OUT_DW, j);
-      int bn = bn_for(H);
+      int bn = bn_site(id, H);
       EDPC_TRY(site(id, F, H, b, q.dOutbT, F, b, T, q.GbT, H, b, T, bn, bn));
       TcGemm& g = tcp.site[id];
       g.C = G + o.Wo;
@@ -518,7 +525,7 @@ int Model::build_tc_plan() {
     }
     {  // dX0 = dA W
       int id = blk_site(BR_DX, j);
-      int bn = bn_for(F);
+      int bn = bn_site(id, F);
       EDPC_TRY(site(id, b, F, kH, q.dAb, b, kH, kH, PbT + o.W, F, kH, kH, bn, bn));
       TcGemm& g = tcp.site[id];
       g.C = q.dX0;
@@ -526,7 +533,7 @@ int Model::build_tc_plan() {
     }
     {  // dW = dA^T X0
       int id = blk_site(BR_DW, j);
-      int bn = bn_for(F);
+      int bn = bn_site(id, F);
       EDPC_TRY(site(id, kH, F, b, q.dAbT, kH, b, T, q.X0bT, F, b, T, bn, bn));
       TcGemm& g = tcp.site[id];
       g.C = G + o.W;
@@ -534,7 +541,7 @@ int Model::build_tc_plan() {
     }
   }
   {  // Eq. 14
-    int bn = bn_for(Fp);
+    int bn = bn_site(kSiteLteDownFwd, Fp);
     EDPC_TRY(site(kSiteLteDownFwd, b, Fp, F, Slte_b, b, F, F, Pb + po.W1, Fp, F, F, bn, bn));
     TcGemm& g = tcp.site[kSiteLteDownFwd];
     g.C = Xp;
@@ -542,7 +549,7 @@ int Model::build_tc_plan() {
     g.bias = P + po.b1;
   }
   {  // Eq. 16
-    int bn = bn_for(F);
+    int bn = bn_site(kSiteLteUpFwd, F);
     EDPC_TRY(site(kSiteLteUpFwd, b, F, Fp, Yb, b, Fp, Fp, Pb + po.W2, F, Fp, Fp, bn, bn));
     TcGemm& g = tcp.site[kSiteLteUpFwd];
     g.C = S[d.nloc + 1];
@@ -550,14 +557,15 @@ int Model::build_tc_plan() {
     g.bias = P + po.b2;
   }
   {  // head
-    EDPC_TRY(site(kSiteHeadFwd, b, 256, F, Shead_b, b, F, F, Pb + po.Wh, 256, F, F, 64, 64));
+    const int bh = tile_code[kSiteHeadFwd] ? 32 * (int)tile_code[kSiteHeadFwd] : 64;
+    EDPC_TRY(site(kSiteHeadFwd, b, 256, F, Shead_b, b, F, F, Pb + po.Wh, 256, F, F, bh, bh));
     TcGemm& g = tcp.site[kSiteHeadFwd];
     g.C = z;
     g.ldc = 256;
     g.bias = P + po.bh;
   }
   {  // head adjoint: dX = dz Wh -> gradient of the last block's output
-    int bn = bn_for(F);
+    int bn = bn_site(kSiteHeadDx, F);
     EDPC_TRY(site(kSiteHeadDx, b, F, 256, dzb, b, 256, 256, PbT + po.Wh, F, 256, 256, bn, bn));
     TcGemm& g = tcp.site[kSiteHeadDx];
     BlockBf16& q = bb[d.n - 1];
@@ -569,28 +577,28 @@ int Model::build_tc_plan() {
     g.ldct = T;
   }
   {  // dWh = dz^T X
-    int bn = bn_for(F);
+    int bn = bn_site(kSiteHeadDw, F);
     EDPC_TRY(site(kSiteHeadDw, 256, F, b, dzbT, 256, b, T, Shead_bT, F, b, T, bn, bn));
     TcGemm& g = tcp.site[kSiteHeadDw];
     g.C = G + po.Wh;
     g.ldc = F;
   }
   {  // LTE up adjoint: dY = dX W2
-    int bn = bn_for(Fp);
+    int bn = bn_site(kSiteLteUpDx, Fp);
     EDPC_TRY(site(kSiteLteUpDx, b, Fp, F, dLteb, b, F, F, PbT + po.W2, Fp, F, F, bn, bn));
     TcGemm& g = tcp.site[kSiteLteUpDx];
     g.C = dY;
     g.ldc = Fp;
   }
   {  // dW2 = dX^T Y
-    int bn = bn_for(Fp);
+    int bn = bn_site(kSiteLteUpDw, Fp);
     EDPC_TRY(site(kSiteLteUpDw, F, Fp, b, dLtebT, F, b, T, YbT, Fp, b, T, bn, bn));
     TcGemm& g = tcp.site[kSiteLteUpDw];
     g.C = G + po.W2;
     g.ldc = Fp;
   }
   {  // LTE down adjoint: dX = dX' W1 -> gradient of the last Local block's output
-    int bn = bn_for(F);
+    int bn = bn_site(kSiteLteDownDx, F);
     EDPC_TRY(site(kSiteLteDownDx, b, F, Fp, dXpb, b, Fp, Fp, PbT + po.W1, F, Fp, Fp, bn, bn));
     TcGemm& g = tcp.site[kSiteLteDownDx];
     g.ldc = F;
@@ -606,7 +614,7 @@ int Model::build_tc_plan() {
     }
   }
   {  // dW1 = dX'^T X
-    int bn = bn_for(F);
+    int bn = bn_site(kSiteLteDownDw, F);
     EDPC_TRY(site(kSiteLteDownDw, Fp, F, b, dXpbT, Fp, b, T, Slte_bT, F, b, T, bn, bn));
     TcGemm& g = tcp.site[kSiteLteDownDw];
     g.C = G + po.W1;
@@ -614,6 +622,67 @@ int Model::build_tc_plan() {
   }
   tcp.ready = true;
   return EDPC_OK;
+}
+
+void Model::tunable_sites(std::vector<int>* ids) const {
+  ids->clear();
+  for (int kind : {OUT_FWD, OUT_DW, BR_DX, BR_DW})
+    for (int j = 0; j < d.n; ++j) ids->push_back(blk_site(kind, j));
+  for (int id = kSiteLteDownFwd; id <= kSiteLteDownDx; ++id) ids->push_back(id);
+}
+
+int Model::set_tiles(const uint8_t* code, int n) {
+  if (precision != EDPC_BF16) return EDPC_OK;
+  for (int i = 0; i < TcPlan::kMaxSites; ++i) tile_code[i] = (code && i < n) ? code[i] : 0;
+  for (int i = 0; i < TcPlan::kMaxSites; ++i)
+    if (tile_code[i] != 0 && tile_code[i] != 1 && tile_code[i] != 2 && tile_code[i] != 4)
+      return fail(EDPC_EARCH, "unknown GEMM tile code " + std::to_string(tile_code[i]));
+  return build_tc_plan();
+}
+
+// Autotuner for the GEMM N tiles: every TC_PLAIN site of the step is timed
+// with N tiles of 32, 64 and 128 (CUDA events, after a warm-up launch) on the
+// model's own buffers, and keeps the fastest. Runs before the first step: the
+// GEMMs only overwrite per-step outputs (activations, BF16 copies, gradients).
+int Model::tune_tiles(cudaStream_t st) {
+  if (precision != EDPC_BF16) return EDPC_OK;
+  std::vector<int> ids;
+  tunable_sites(&ids);
+  cudaEvent_t e0, e1;
+  EDPC_CUDA(cudaEventCreate(&e0));
+  EDPC_CUDA(cudaEventCreate(&e1));
+  int r = EDPC_OK;
+  const int reps = 4;
+  for (int id : ids) {
+    float best = 1e30f;
+    uint8_t best_code = 1;
+    for (uint8_t code : {(uint8_t)1, (uint8_t)2, (uint8_t)4}) {
+      tile_code[id] = code;
+      if ((r = build_tc_plan()) != EDPC_OK) break;
+      NoPdl scope;
+      cudaError_t e = launch_gemm_tc(tcp.site[id], st);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      for (int q = 0; q < reps && e == cudaSuccess; ++q) e = launch_gemm_tc(tcp.site[id], st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        r = fail(EDPC_ECUDA, std::string("GEMM tile tuning: ") + cudaGetErrorString(e));
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        best_code = code;
+      }
+    }
+    if (r != EDPC_OK) break;
+    tile_code[id] = best_code;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r != EDPC_OK) return r;
+  return build_tc_plan();
 }
 
 int Model::run_tc(int site, cudaStream_t st) {
@@ -649,7 +718,7 @@ int Model::forward_bf16(const StepIO& io, cudaStream_t st) {
   for (int jj = 0; jj < d.n; ++jj) {
     if (jj == d.nloc) {
       EDPC_TRY(run_tc(kSiteLteDownFwd, st));  // Eq. 14
-      EDPC_TRY(fdm_fwd_call(st));             // Eq. 15
+      EDPC_TRY(fdm_fwd_call(io, st));             // Eq. 15
       EDPC_TRY(run_tc(kSiteLteUpFwd, st));    // Eq. 16
     }
     const BlockOff& o = po.blk[jj];

@@ -106,6 +106,15 @@ class Model {
   int step(const StepIO& io, cudaStream_t st);
   int launches_per_step() const;
   int refresh_bf16_weights(cudaStream_t st);
+  size_t device_bytes() const { return arena_bytes_; }
+
+  // GEMM N tile per tcgen05 site: 32 * code (0 = size heuristic). The codes
+  // change the accumulation layout, so a bitstream records the ones its
+  // encoder used and the decoder sets the same.
+  uint8_t tile_code[TcPlan::kMaxSites] = {};
+  int set_tiles(const uint8_t* code, int n);  // codes 0, 1, 2 or 4; rebuilds the plan
+  int tune_tiles(cudaStream_t st);            // times 32/64/128 at every TC_PLAIN site
+  void tunable_sites(std::vector<int>* ids) const;
 
  private:
   void* arena_ = nullptr;
@@ -126,7 +135,7 @@ class Model {
   int build_tc_plan();
   int run_tc(int site, cudaStream_t st);
   int fork_side(cudaStream_t st);  // the side stream waits for the work issued so far on st
-  int fdm_fwd_call(cudaStream_t st);
+  int fdm_fwd_call(const StepIO& io, cudaStream_t st);
   int fdm_bwd_call(const StepIO& io, cudaStream_t st);
 };
 

@@ -76,7 +76,9 @@ __global__ void embed_kernel(const uint8_t* __restrict__ data, Split sp, const S
   pdl_launch();
   const int s = blockIdx.x;
   const int F = K * D;
-  if (data) {
+  // A stream past its end (inactive) keeps its last context: its bytes
+  // [i - K, i) would run beyond the stream, and its outputs are masked.
+  if (data && ctl->i <= sp.len(s)) {
     const long long base = sp.off(s) + ctl->i - K;
     for (int k = threadIdx.x; k < K; k += blockDim.x) ctx[(size_t)s * K + k] = data[base + k];
     __syncthreads();
@@ -254,15 +256,35 @@ cudaError_t launch_ln_bwd(const float* dX0, const float* xhat, const float* rstd
 // FDM forward (Eq. 15): y_s[j] = sum_i x'_s[i] U_s[i][j]. One CTA per stream;
 // threads own 4 consecutive columns and a row group; row groups are added in order.
 // ============================================================================================
+// A stream that is past its end (or masked in the model API) has no
+// prediction to make: its y is written as zeros and its U_s is not read.
+__device__ __forceinline__ bool fdm_row_active(const FdmAct& a, int s) {
+  if (!a.ctl) return true;
+  return a.active ? a.active[s] != 0 : (long long)a.ctl->i < a.sp.len(s);
+}
+
+__device__ __forceinline__ void fdm_zero_row(float* Y, __nv_bfloat16* Yb, __nv_bfloat16* YbT, int ldT, int s,
+                                             int Fp) {
+  for (int j = threadIdx.x; j < Fp; j += blockDim.x) {
+    Y[(size_t)s * Fp + j] = 0.f;
+    if (Yb) Yb[(size_t)s * Fp + j] = __float2bfloat16_rn(0.f);
+    if (YbT) YbT[(size_t)j * ldT + s] = __float2bfloat16_rn(0.f);
+  }
+}
+
 __global__ void __launch_bounds__(256) fdm_fwd_kernel(const float* __restrict__ Xp, const float* __restrict__ U,
                                                       float* __restrict__ Y, int Fp, __nv_bfloat16* Yb,
-                                                      __nv_bfloat16* YbT, int ldT) {
+                                                      __nv_bfloat16* YbT, int ldT, FdmAct act) {
   pdl_wait();
   pdl_launch();
   extern __shared__ float sm[];
   float* xs = sm;              // Fp
   float* part = sm + Fp;       // groups x Fp
   const int s = blockIdx.x;
+  if (!fdm_row_active(act, s)) {
+    fdm_zero_row(Y, Yb, YbT, ldT, s, Fp);
+    return;
+  }
   const int cols4 = Fp >> 2;
   const int groups = blockDim.x / cols4;
   const int cg = threadIdx.x % cols4, rg = threadIdx.x / cols4;
@@ -340,7 +362,7 @@ struct FdmRing {
 template <int FP>
 __global__ void __launch_bounds__(FdmRing<FP>::NT)
     fdm_fwd_ring_kernel(const float* __restrict__ Xp, const float* __restrict__ U, float* __restrict__ Y,
-                        __nv_bfloat16* Yb, __nv_bfloat16* YbT, int ldT, int* err) {
+                        __nv_bfloat16* Yb, __nv_bfloat16* YbT, int ldT, int* err, FdmAct act) {
   using R = FdmRing<FP>;
   extern __shared__ __align__(128) float smf[];
   float* buf = smf;                        // RING x 16 KB
@@ -354,6 +376,10 @@ __global__ void __launch_bounds__(FdmRing<FP>::NT)
   __syncthreads();
   pdl_wait();
   pdl_launch();
+  if (!fdm_row_active(act, s)) {  // CTA-uniform, before any copy is issued
+    fdm_zero_row(Y, Yb, YbT, ldT, s, FP);
+    return;
+  }
   const float* Us = U + (size_t)s * FP * FP;
   if (t == 0)
     for (int b = 0; b < R::RING; ++b) bulk_load(buf + (size_t)b * 4096, Us + (size_t)b * 4096, 16384u, &bars[b]);
@@ -390,23 +416,24 @@ __global__ void __launch_bounds__(FdmRing<FP>::NT)
 
 template <int FP>
 cudaError_t launch_fdm_fwd_ring(const float* Xp, const float* U, float* Y, int b, __nv_bfloat16* Yb,
-                                __nv_bfloat16* YbT, int ldT, int* err, cudaStream_t st) {
+                                __nv_bfloat16* YbT, int ldT, int* err, const FdmAct& act, cudaStream_t st) {
   const size_t smem = FdmRing<FP>::kSmem;
   if (smem > 48 * 1024) {
     cudaError_t e =
         cudaFuncSetAttribute(fdm_fwd_ring_kernel<FP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return launch_k(fdm_fwd_ring_kernel<FP>, dim3(b), dim3(FdmRing<FP>::NT), smem, st, Xp, U, Y, Yb, YbT, ldT, err);
+  return launch_k(fdm_fwd_ring_kernel<FP>, dim3(b), dim3(FdmRing<FP>::NT), smem, st, Xp, U, Y, Yb, YbT, ldT, err,
+                  act);
 }
 
 cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int Fp, cudaStream_t st,
-                           __nv_bfloat16* Yb, __nv_bfloat16* YbT, int ldT, int* err) {
+                           __nv_bfloat16* Yb, __nv_bfloat16* YbT, int ldT, int* err, FdmAct act) {
   switch (Fp) {
-    case 128: return launch_fdm_fwd_ring<128>(Xp, U, Y, b, Yb, YbT, ldT, err, st);
-    case 256: return launch_fdm_fwd_ring<256>(Xp, U, Y, b, Yb, YbT, ldT, err, st);
-    case 512: return launch_fdm_fwd_ring<512>(Xp, U, Y, b, Yb, YbT, ldT, err, st);
-    case 1024: return launch_fdm_fwd_ring<1024>(Xp, U, Y, b, Yb, YbT, ldT, err, st);
+    case 128: return launch_fdm_fwd_ring<128>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
+    case 256: return launch_fdm_fwd_ring<256>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
+    case 512: return launch_fdm_fwd_ring<512>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
+    case 1024: return launch_fdm_fwd_ring<1024>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
     default: break;
   }
   const int cols4 = Fp / 4;
@@ -417,7 +444,7 @@ cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int
     cudaError_t e = cudaFuncSetAttribute(fdm_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  return launch_k(fdm_fwd_kernel, dim3(b), dim3(threads), smem, st, Xp, U, Y, Fp, Yb, YbT, ldT);
+  return launch_k(fdm_fwd_kernel, dim3(b), dim3(threads), smem, st, Xp, U, Y, Fp, Yb, YbT, ldT, act);
 }
 
 // ============================================================================================
@@ -732,7 +759,14 @@ __global__ void step_advance_kernel(StepCtl* ctl, Split sp, int K, int ring_slot
   c.i += 1;
   c.t += 1;
   long long i = c.i;
-  int bact = (i < sp.q) ? b : (i == sp.q ? sp.rem : 0);
+  int bact;
+  if (sp.cp) {
+    // uneven split: the count changes only at the table's time indices
+    bact = c.bact;
+    while (c.cpi < sp.ncp && sp.cp[c.cpi].i <= i) bact = sp.cp[c.cpi++].bact;
+  } else {
+    bact = (i < sp.q) ? b : (i == sp.q ? sp.rem : 0);
+  }
   c.bact = bact;
   c.inv_bact = bact > 0 ? 1.0f / (float)bact : 0.f;
   c.bc1 = 1.0f - powf(kB1, (float)c.t);

@@ -23,11 +23,19 @@ cudaError_t launch_ln_fwd(const float* X, const float* g, const float* be, float
                           float* X0, int b, int F, cudaStream_t st);
 // G = GELU(prod_i A[:, iH:(i+1)H]).
 cudaError_t launch_branch_gelu(const float* A, int b, int H, int k, float* G, cudaStream_t st);
-// Per-stream FDM product y_s = x'_s U_s (and optional BF16 copies of Y).
+// Which streams of a step are active: `active` (model API) if set, else
+// the stream still has bytes at time index ctl->i. ctl == nullptr: all.
+struct FdmAct {
+  const StepCtl* ctl = nullptr;
+  Split sp{0, 0, 0};
+  const uint8_t* active = nullptr;
+};
+// Per-stream FDM product y_s = x'_s U_s (and optional BF16 copies of Y);
+// inactive streams get y_s = 0 without reading U_s.
 // err (optional) gets bit 8 if a bounded wait for a bulk copy expired.
 cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int Fp, cudaStream_t st,
                            __nv_bfloat16* Yb = nullptr, __nv_bfloat16* YbT = nullptr, int ldT = 0,
-                           int* err = nullptr);
+                           int* err = nullptr, FdmAct act = FdmAct{});
 
 // Softmax, CDF quantization, coding and the CE gradient of one step.
 struct HeadArgs {

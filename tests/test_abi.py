@@ -77,3 +77,29 @@ def test_peek_rejects_garbage(lib):
     with pytest.raises(pkg.EdpcError) as e:
         pkg.peek(b"not a container at all" * 10)
     assert e.value.code == 3
+
+
+def test_file_set_plan_matches_the_oracle_split(lib):
+    """The library's stream budget rule (host code) against the oracle's, on
+    random file sets: the same stream length and stream count."""
+    import paper_2507_18969_gb300 as pkg
+    from oracle.compress import archive_split, archive_stream_len
+    rng = np.random.default_rng(9)
+    for trial in range(40):
+        nf = int(rng.integers(1, 30))
+        sizes = np.exp(rng.uniform(0, np.log(1 << 22), size=nf)).astype(np.int64)
+        sizes[rng.random(nf) < 0.1] = 0
+        budget = int(rng.integers(1, 2000))
+        plan = pkg.archive_plan(list(sizes), pkg.make_cfg(streams=budget))
+        L = archive_stream_len(list(sizes), budget)
+        b, _, _ = archive_split(list(sizes), L)
+        assert (plan.stream_len, plan.streams) == (L, b), (trial, budget)
+        assert plan.est_seconds == 0
+
+
+def test_file_set_plan_rejects_too_many_streams(lib):
+    import paper_2507_18969_gb300 as pkg
+    with pytest.raises(pkg.EdpcError):
+        pkg.archive_plan([1] * 70000, pkg.make_cfg(streams=65535))
+    with pytest.raises(pkg.EdpcError):
+        pkg.archive_plan([10, 20], pkg.make_cfg(streams=70000))
