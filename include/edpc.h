@@ -54,6 +54,9 @@ extern "C" {
  * state and the FDM stay FP32 in every mode. */
 #define EDPC_FP32 0u     /* plain FP32 (SIMT) GEMMs */
 #define EDPC_BF16 1u     /* BF16 operands, FP32 accumulation (tcgen05) */
+#define EDPC_FP8E4M3 2u  /* FP8 e4m3 operands with per-tensor power-of-two scales
+                            (2^k, k largest with amax * 2^k <= 448, every step),
+                            FP32 accumulation (tcgen05 kind::f8f6f4) */
 
 /* cfg.flags */
 #define EDPC_FLAG_NO_PIPELINE 1u  /* run the coder stage inline (DPCA off) */
@@ -80,7 +83,7 @@ extern "C" {
  *   branches   k, the MBRB paths multiplied together (Eq. 11); 2 by default
  *              (Sec. 3.1.2), 1..3 accepted.
  *   lr         Adam learning rate (Sec. 4.1: 1e-3).
- *   precision  EDPC_FP32 or EDPC_BF16.
+ *   precision  EDPC_FP32, EDPC_BF16 or EDPC_FP8E4M3.
  *   seed       seed of the initial parameters (SplitMix64 counter streams).
  *
  * Limits: 1 <= context <= 256; embed_dim a multiple of 8 in [8, 64];

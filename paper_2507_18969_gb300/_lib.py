@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libedpc.so")
 EDPC_ABI_VERSION = 1
 EDPC_FP32 = 0
 EDPC_BF16 = 1
+EDPC_FP8E4M3 = 2
 EDPC_FLAG_NO_PIPELINE = 1
 EDPC_FLAG_NO_GRAPH = 2
 EDPC_FLAG_TUNE_TILES = 4

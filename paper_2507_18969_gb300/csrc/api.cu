@@ -77,7 +77,8 @@ static int check_cfg(const edpc_cfg* c, bool auto_streams = false) {
   if (c->blocks < 1 || c->blocks > (uint32_t)kMaxBlocks) return fail(EDPC_EINVAL, "blocks must be in [1, 16]");
   if (c->branches < 1 || c->branches > 3) return fail(EDPC_EINVAL, "branches must be in [1, 3]");
   if (!(c->lr > 0.f) || !std::isfinite(c->lr)) return fail(EDPC_EINVAL, "lr must be finite and > 0");
-  if (c->precision != EDPC_FP32 && c->precision != EDPC_BF16) return fail(EDPC_EINVAL, "unknown precision");
+  if (c->precision != EDPC_FP32 && c->precision != EDPC_BF16 && c->precision != EDPC_FP8E4M3)
+    return fail(EDPC_EINVAL, "unknown precision");
   return EDPC_OK;
 }
 
@@ -665,7 +666,7 @@ static int encoder_open_impl(const edpc_cfg* cfg, const uint8_t* const* parts, c
   if (cudaMemcpyAsync(s->out_off, s->h_out_off.data(), 8 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(s->out_cap, cap.data(), 4 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return bail(fail(EDPC_ECUDA, "encoder setup copies"));
-  if (tune && cfg->precision == EDPC_BF16) {
+  if (tune && cfg->precision != EDPC_FP32) {
     if ((r = s->model.tune_tiles(st)) != EDPC_OK) return bail(r);
     s->tiles.assign(s->model.tile_code, s->model.tile_code + TcPlan::kMaxSites);
   }
@@ -1176,7 +1177,7 @@ extern "C" int edpc_model_set_state(edpc_model* mm, const float* shared, const f
   if (m_fdm) EDPC_CUDA(cudaMemcpy(m.Um, m_fdm, nf, cudaMemcpyHostToDevice));
   if (v_fdm) EDPC_CUDA(cudaMemcpy(m.Uv, v_fdm, nf, cudaMemcpyHostToDevice));
   mm->t = t;
-  if (shared && m.precision == EDPC_BF16) {
+  if (shared && m.precision != EDPC_FP32) {
     EDPC_TRY(m.refresh_bf16_weights(0));
     EDPC_CUDA(cudaDeviceSynchronize());
   }

@@ -130,6 +130,7 @@ Model::~Model() {
   if (tr_ev) cudaEventDestroy(tr_ev);
   if (side) cudaStreamDestroy(side);
   if (gU) cudaFree(gU);
+  if (f8_arena) cudaFree(f8_arena);
   if (arena_) cudaFree(arena_);
 }
 
@@ -143,7 +144,7 @@ int Model::init(const edpc_cfg& cfg, int streams) {
   const size_t bF = (size_t)d.b * d.F, bFp = (size_t)d.b * d.Fp, bH = (size_t)d.b * d.H;
   const int kH = d.k * d.H;
   const size_t bkH = (size_t)d.b * kH, fdm = (size_t)d.b * d.Fp * d.Fp;
-  const bool bf16 = precision == EDPC_BF16;
+  const bool bf16 = precision != EDPC_FP32;  // BF16 operand copies (also the FP8 mode's sources)
   const size_t T = d.ldT;
 
   // weight matrices that need transposed BF16 copies (32 x 32 tiles)
@@ -432,7 +433,85 @@ int Model::backward_f32(const StepIO& io, cudaStream_t st) {
 // ==========================================================================================
 // BF16 path
 // ==========================================================================================
+// FP8 e4m3 shadow of a BF16 operand matrix (one per distinct source).
+int Model::fp8_shadow(const void* src, int rows, int cols, int ld) {
+  const auto* p = static_cast<const __nv_bfloat16*>(src);
+  for (size_t i = 0; i < f8.size(); ++i)
+    if (f8[i].src == p && f8[i].rows == rows && f8[i].cols == cols && f8[i].ld == ld) return (int)i;
+  Fp8Shadow sh;
+  sh.src = p;
+  sh.rows = rows;
+  sh.cols = cols;
+  sh.ld = ld;
+  sh.ld8 = (int)round_up(cols, 16);
+  // quantized columns: whole 8-element vectors; a transposed operand's extra
+  // columns up to ld are its zero padding (b rounded up to 16)
+  sh.qcols = (int)std::min<long long>(ld, round_up(cols, 8));
+  sh.weight = (p >= Pb && p < Pb + nparam) || (p >= PbT && p < PbT + nparam);
+  sh.transposed = p >= PbT && p < PbT + nparam;
+  f8.push_back(sh);
+  return (int)f8.size() - 1;
+}
+
 int Model::build_tc_plan() {
+  if (precision == EDPC_FP8E4M3 && !f8_arena) {
+    // first pass: collect the operand shadows; then allocate them
+    f8.clear();
+    f8_collect = true;
+    int r = build_tc_sites();
+    f8_collect = false;
+    if (r != EDPC_OK) return r;
+    size_t tot = 256 + 8 * f8.size();  // amax words and inverse scales first
+    for (auto& sh : f8) tot += round_up((long long)sh.rows * sh.ld8, 256);
+    EDPC_CUDA(cudaMalloc(&f8_arena, tot));
+    EDPC_CUDA(cudaMemset(f8_arena, 0, tot));
+    f8_amax = reinterpret_cast<unsigned*>(f8_arena);
+    f8_inv = reinterpret_cast<float*>(f8_arena + 4 * f8.size());
+    size_t off = round_up(8 * (long long)f8.size(), 256);
+    for (auto& sh : f8) {
+      sh.dst = f8_arena + off;
+      off += round_up((long long)sh.rows * sh.ld8, 256);
+    }
+    f8_done.assign(f8.size(), 0);
+  }
+  return build_tc_sites();
+}
+
+// FP8: quantizes the step's weight shadows (transposed ones or not) in one
+// amax + convert launch pair per group of kMaxFp8Jobs.
+int Model::quantize_weights(bool transposed, cudaStream_t st) {
+  Fp8Jobs J{};
+  J.amax = f8_amax;
+  J.inv = f8_inv;
+  for (size_t i = 0; i <= f8.size(); ++i) {
+    if (i < f8.size() && f8[i].weight && f8[i].transposed == transposed) {
+      const Fp8Shadow& sh = f8[i];
+      J.job[J.n++] = {sh.src, sh.rows, sh.qcols, sh.ld, sh.dst, sh.ld8, (int)i};
+    }
+    if (J.n == kMaxFp8Jobs || (i == f8.size() && J.n)) {
+      EDPC_CUDA(launch_fp8_quantize(J, st));
+      J.n = 0;
+    }
+  }
+  return EDPC_OK;
+}
+
+// FP8: quantizes the activation shadows a GEMM site reads, once per step.
+int Model::quantize_site(int site, cudaStream_t st) {
+  Fp8Jobs J{};
+  J.amax = f8_amax;
+  J.inv = f8_inv;
+  for (int id : {site_fa[site], site_fb[site]}) {
+    if (f8[id].weight || f8_done[id]) continue;
+    const Fp8Shadow& sh = f8[id];
+    J.job[J.n++] = {sh.src, sh.rows, sh.qcols, sh.ld, sh.dst, sh.ld8, id};
+    f8_done[id] = 1;
+  }
+  if (J.n) EDPC_CUDA(launch_fp8_quantize(J, st));
+  return EDPC_OK;
+}
+
+int Model::build_tc_sites() {
   const int kH = d.k * d.H;
   const int T = d.ldT;
   // N tile: the site's tile code when one is set (tuned or read from a
@@ -449,6 +528,20 @@ int Model::build_tc_plan() {
     g.bn = bn;
     g.box_b = box_b;
     g.err = &ctl->err;
+    if (precision == EDPC_FP8E4M3) {
+      // e4m3 shadows of both BF16 operands, quantized before the launch
+      const int ia = fp8_shadow(a, a_rows, a_cols, a_ld), ib = fp8_shadow(b, b_rows, b_cols, b_ld);
+      site_fa[id] = ia;
+      site_fb[id] = ib;
+      if (f8_collect) return EDPC_OK;
+      EDPC_TRY(make_tmap_u8(&g.ta, f8[ia].dst, a_rows, a_cols, f8[ia].ld8, 128));
+      EDPC_TRY(make_tmap_u8(&g.tb, f8[ib].dst, b_rows, b_cols, f8[ib].ld8, box_b));
+      g.fp8 = true;
+      g.inv_a = f8_inv + ia;
+      g.inv_b = f8_inv + ib;
+      g.b_early = f8[ib].weight;  // activation shadows are written by the launch just before
+      return EDPC_OK;
+    }
     EDPC_TRY(make_tmap_bf16(&g.ta, a, a_rows, a_cols, a_ld, 128));
     EDPC_TRY(make_tmap_bf16(&g.tb, b, b_rows, b_cols, b_ld, box_b));
     return EDPC_OK;
@@ -632,7 +725,7 @@ void Model::tunable_sites(std::vector<int>* ids) const {
 }
 
 int Model::set_tiles(const uint8_t* code, int n) {
-  if (precision != EDPC_BF16) return EDPC_OK;
+  if (precision == EDPC_FP32) return EDPC_OK;
   for (int i = 0; i < TcPlan::kMaxSites; ++i) tile_code[i] = (code && i < n) ? code[i] : 0;
   for (int i = 0; i < TcPlan::kMaxSites; ++i)
     if (tile_code[i] != 0 && tile_code[i] != 1 && tile_code[i] != 2 && tile_code[i] != 4)
@@ -645,7 +738,7 @@ int Model::set_tiles(const uint8_t* code, int n) {
 // model's own buffers, and keeps the fastest. Runs before the first step: the
 // GEMMs only overwrite per-step outputs (activations, BF16 copies, gradients).
 int Model::tune_tiles(cudaStream_t st) {
-  if (precision != EDPC_BF16) return EDPC_OK;
+  if (precision == EDPC_FP32) return EDPC_OK;
   std::vector<int> ids;
   tunable_sites(&ids);
   cudaEvent_t e0, e1;
@@ -688,8 +781,10 @@ int Model::tune_tiles(cudaStream_t st) {
 int Model::run_tc(int site, cudaStream_t st) {
   if (st == side) {
     NoPdl scope;
+    if (precision == EDPC_FP8E4M3) EDPC_TRY(quantize_site(site, st));
     EDPC_CUDA(launch_gemm_tc(tcp.site[site], st));
   } else {
+    if (precision == EDPC_FP8E4M3) EDPC_TRY(quantize_site(site, st));
     EDPC_CUDA(launch_gemm_tc(tcp.site[site], st));
   }
   return EDPC_OK;
@@ -705,14 +800,21 @@ int Model::fork_side(cudaStream_t st) {
 
 int Model::forward_bf16(const StepIO& io, cudaStream_t st) {
   nfork_ = 0;
+  const bool f8m = precision == EDPC_FP8E4M3;
+  if (f8m) {
+    std::fill(f8_done.begin(), f8_done.end(), 0);
+    EDPC_CUDA(launch_zero_u32(f8_amax, (int)f8.size(), st));  // this step's amax slots
+  }
   // Transposed BF16 weight copies for this step's dX GEMMs, from the weights the
   // previous Adam wrote, on the side stream while the forward pass runs.
   EDPC_TRY(fork_side(st));
   {
     NoPdl scope;
     EDPC_CUDA(launch_transpose_tiles(Pb, PbT, tiles, ntiles, side));
+    if (f8m) EDPC_TRY(quantize_weights(true, side));
   }
   EDPC_CUDA(cudaEventRecord(tr_ev, side));
+  if (f8m) EDPC_TRY(quantize_weights(false, st));
   EDPC_CUDA(launch_embed(io.mode == 2 ? nullptr : io.data, io.sp, ctl, P + po.E, d.b, d.K, d.D, S[0], ctx, st));
   if (d.nloc == 0) EDPC_CUDA(launch_to_bf16(S[0], d.b, d.F, d.F, Slte_b, d.F, Slte_bT, d.ldT, st));
   for (int jj = 0; jj < d.n; ++jj) {
@@ -832,7 +934,7 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
 // step
 // ==========================================================================================
 int Model::forward(const StepIO& io, cudaStream_t st) {
-  return precision == EDPC_BF16 ? forward_bf16(io, st) : forward_f32(io, st);
+  return precision != EDPC_FP32 ? forward_bf16(io, st) : forward_f32(io, st);
 }
 
 int Model::head(const StepIO& io, cudaStream_t st) {
@@ -861,13 +963,13 @@ int Model::head(const StepIO& io, cudaStream_t st) {
 }
 
 int Model::backward(const StepIO& io, cudaStream_t st) {
-  return precision == EDPC_BF16 ? backward_bf16(io, st) : backward_f32(io, st);
+  return precision != EDPC_FP32 ? backward_bf16(io, st) : backward_f32(io, st);
 }
 
 int Model::adam(cudaStream_t st) {
   EmbGrad eg{nullptr, 0, 0, 0};
   if (emb_in_adam) eg = EmbGrad{emb_part, embed_bwd_chunks(d.b, d.K), po.E, (size_t)256 * d.D};
-  if (precision == EDPC_BF16) {
+  if (precision != EDPC_FP32) {
     NoPdl scope;  // follows the join of the side stream
     EDPC_CUDA(launch_adam_bf16(P, G, M, V, Pb, nparam, ctl, st, eg));
   } else {
@@ -887,7 +989,7 @@ int Model::step(const StepIO& io, cudaStream_t st) {
 }
 
 int Model::launches_per_step() const {
-  if (precision == EDPC_BF16) {
+  if (precision != EDPC_FP32) {
     // forward: embed + 3 per block + LTE (2 GEMMs + FDM) + head GEMM + head
     int n = 1 + 3 * d.n + 3 + 1 + 1;
     // backward: head dW/colsum/dX, per block 3 main + 3 side, LTE 3 + 2 side ... + embed

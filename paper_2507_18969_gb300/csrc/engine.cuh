@@ -113,6 +113,24 @@ class Model {
   // encoder used and the decoder sets the same.
   uint8_t tile_code[TcPlan::kMaxSites] = {};
   int set_tiles(const uint8_t* code, int n);  // codes 0, 1, 2 or 4; rebuilds the plan
+
+  // FP8 e4m3 mode: one e4m3 shadow per distinct BF16 GEMM operand, with a
+  // per-tensor power-of-two scale computed every step (amax slot + inverse).
+  struct Fp8Shadow {
+    const __nv_bfloat16* src = nullptr;
+    int rows = 0, cols = 0, ld = 0;
+    uint8_t* dst = nullptr;
+    int ld8 = 0;
+    int qcols = 0;            // columns quantized (cols rounded up to 8, within ld)
+    bool weight = false;      // a weight copy (Pb / PbT): quantized once at the step's start
+    bool transposed = false;  // a PbT weight copy
+  };
+  std::vector<Fp8Shadow> f8;
+  uint8_t* f8_arena = nullptr;
+  unsigned* f8_amax = nullptr;
+  float* f8_inv = nullptr;
+  std::vector<char> f8_done;
+  int site_fa[TcPlan::kMaxSites] = {}, site_fb[TcPlan::kMaxSites] = {};
   int tune_tiles(cudaStream_t st);            // times 32/64/128 at every TC_PLAIN site
   void tunable_sites(std::vector<int>* ids) const;
 
@@ -133,6 +151,11 @@ class Model {
   int forward_bf16(const StepIO& io, cudaStream_t st);
   int backward_bf16(const StepIO& io, cudaStream_t st);
   int build_tc_plan();
+  int build_tc_sites();
+  int fp8_shadow(const void* src, int rows, int cols, int ld);
+  int quantize_weights(bool transposed, cudaStream_t st);
+  int quantize_site(int site, cudaStream_t st);
+  bool f8_collect = false;
   int run_tc(int site, cudaStream_t st);
   int fork_side(cudaStream_t st);  // the side stream waits for the work issued so far on st
   int fdm_fwd_call(const StepIO& io, cudaStream_t st);

@@ -1,11 +1,13 @@
-// BF16 GEMM on the 5th-generation tensor cores (sm_103a).
+// BF16 / FP8 GEMM on the 5th-generation tensor cores (sm_103a).
 //
 // One CTA computes a 128 x BN tile of C = A B^T:
-//   warp 0 (one lane)  issues TMA loads of 128x64 A and BNx64 B tiles
-//                      (128-byte swizzle) into a STAGES-deep ring;
-//   warp 1 (one lane)  issues tcgen05.mma (M=128, N=BN, K=16, BF16 x BF16 ->
-//                      FP32) into a TMEM accumulator and commits each stage
-//                      back to its "empty" barrier;
+//   warp 0 (one lane)  issues TMA loads of 128-byte-wide A (128 rows) and B
+//                      (BN rows) tiles (64 BF16 or 128 FP8 elements of K,
+//                      128-byte swizzle) into a STAGES-deep ring;
+//   warp 1 (one lane)  issues tcgen05.mma (M=128, N=BN; kind::f16 with K=16
+//                      for BF16, kind::f8f6f4 with K=32 for FP8 e4m3; FP32
+//                      accumulation) into a TMEM accumulator and commits each
+//                      stage back to its "empty" barrier;
 //   warp 2             allocates / frees the TMEM columns;
 //   warps 0-3          drain TMEM with tcgen05.ld (warp w owns lanes 32w..32w+31,
 //                      i.e. tile rows) and run the fused epilogue.
@@ -26,7 +28,10 @@ namespace edpc {
 
 namespace {
 
-constexpr int BM = 128, BK = 64;
+constexpr int BM = 128;
+constexpr int BKB = 128;  // bytes of K per stage row (one 128-byte swizzle span)
+template <bool F8>
+constexpr int bk_elems() { return F8 ? 128 : 64; }
 // Pipeline depth: enough stages to hold the whole K panel in flight for the
 // small-N tiles (8 x 20-24 KB), 4 for 128-wide tiles.
 template <int BN>
@@ -47,6 +52,9 @@ struct TcEpi {
   const float* Aux;
   int ldaux;
   int* err;
+  const float* inv_a;  // FP8: 1 / scale of A and of B (powers of two)
+  const float* inv_b;
+  int b_early;         // B may be fetched before the dependent-launch wait
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -110,11 +118,22 @@ __device__ __forceinline__ uint64_t sdesc(const void* p) {
 __host__ __device__ constexpr uint32_t idesc_bf16(int bn) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
+// kind::f8f6f4 with A = B = E4M3 (type code 0), D = F32, K-major, M = 128, N = bn.
+__host__ __device__ constexpr uint32_t idesc_e4m3(int bn) {
+  return (1u << 4) | ((uint32_t)(bn >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_e4m3(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
       "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
 }
 
@@ -222,16 +241,17 @@ constexpr int tmem_cols() {
 
 template <int BN>
 constexpr size_t smem_bytes() {
-  return 1024 /*alignment slack*/ + (size_t)stages_for<BN>() * (BM * BK * 2 + BN * BK * 2) + 256;
+  return 1024 /*alignment slack*/ + (size_t)stages_for<BN>() * (BM * BKB + BN * BKB) + 256;
 }
 
-template <int BN, int MODE, int KB>
+template <int BN, int MODE, int KB, bool F8>
 __global__ void __launch_bounds__(128, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcEpi e) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr int STAGES = stages_for<BN>();
-  constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+  constexpr uint32_t A_BYTES = BM * BKB, B_BYTES = BN * BKB;
+  constexpr int BK = bk_elems<F8>();
   constexpr int SECTIONS = (MODE == TC_BRANCH) ? BN / 32 : 1;
   uint8_t* sA = smem;
   uint8_t* sB = smem + STAGES * A_BYTES;
@@ -269,19 +289,19 @@ __global__ void __launch_bounds__(128, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  // B (weights, or activations of the forward pass) was written at least two
-  // kernels earlier, so its first tiles can be fetched before the
+  // When B (weights, or activations of the forward pass) was written at least
+  // two kernels earlier (b_early), its first tiles are fetched before the
   // programmatic-dependent-launch wait; A comes from the previous kernel.
   auto load_b = [&](int kb, int s) {
     if (MODE == TC_BRANCH) {
 #pragma unroll
       for (int i = 0; i < SECTIONS; ++i)
-        tma_load_2d(sB + s * B_BYTES + i * (32 * BK * 2), &tb, kb * BK, i * e.H + n0, &full[s]);
+        tma_load_2d(sB + s * B_BYTES + i * (32 * BKB), &tb, kb * BK, i * e.H + n0, &full[s]);
     } else {
       tma_load_2d(sB + s * B_BYTES, &tb, kb * BK, n0, &full[s]);
     }
   };
-  const int npre = nk < STAGES ? nk : STAGES;
+  const int npre = e.b_early ? (nk < STAGES ? nk : STAGES) : 0;
   if (warp == 0 && lane == 0) {
     for (int kb = 0; kb < npre; ++kb) {
       mbar_expect_tx(&full[kb], A_BYTES + B_BYTES);
@@ -296,8 +316,8 @@ __global__ void __launch_bounds__(128, 1)
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (kb >= STAGES) {
-        if (!mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+      if (kb >= STAGES && !mbar_wait(&empty[s], ph ^ 1u, abort_flag)) break;
+      if (kb >= npre) {
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
         load_b(kb, s);
       }
@@ -305,17 +325,20 @@ __global__ void __launch_bounds__(128, 1)
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    constexpr uint32_t idesc = idesc_bf16(BN);
+    constexpr uint32_t idesc = F8 ? idesc_e4m3(BN) : idesc_bf16(BN);
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
       if (!mbar_wait(&full[s], ph, abort_flag)) break;
       tc_fence_after();
 #pragma unroll
-      for (int k = 0; k < BK / 16; ++k) {
+      for (int k = 0; k < BKB / 32; ++k) {  // one MMA per 32 bytes of K
         const uint64_t ad = sdesc(sA + s * A_BYTES + k * 32);
         const uint64_t bd = sdesc(sB + s * B_BYTES + k * 32);
-        mma_bf16(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+        if (F8)
+          mma_e4m3(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
+        else
+          mma_bf16(tmem, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
       }
       mma_commit(&empty[s]);
     }
@@ -332,12 +355,18 @@ __global__ void __launch_bounds__(128, 1)
   // The pipeline's A stages are idle now: reuse them to stage transposed stores.
   __nv_bfloat16* sT = reinterpret_cast<__nv_bfloat16*>(sA);
   const bool rok = row < e.M;
+  // FP8: undo the operands' power-of-two scales (exact)
+  const float sc = F8 ? e.inv_a[0] * e.inv_b[0] : 1.f;
   if (ok) {
     if (MODE == TC_PLAIN) {
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float v[32];
         tmem_ld32(trow + (uint32_t)c0, v);
+        if (F8) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) v[j] *= sc;
+        }
         const int nb = n0 + c0;
         if (e.bias) {
 #pragma unroll
@@ -364,6 +393,7 @@ __global__ void __launch_bounds__(128, 1)
         tmem_ld32(trow + (uint32_t)(i * 32), v);
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
+          if (F8) v[j] *= sc;
           const int h = n0 + j;
           if (h < e.H) v[j] += e.bias[i * e.H + h];
           g[j] *= v[j];
@@ -381,6 +411,10 @@ __global__ void __launch_bounds__(128, 1)
       for (int c0 = 0; c0 < BN; c0 += 32) {
         float dg[32];
         tmem_ld32(trow + (uint32_t)c0, dg);
+        if (F8) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) dg[j] *= sc;
+        }
         const int hb = n0 + c0;
         float xs[KB][32];
         float xf[32];
@@ -434,16 +468,17 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
-template <int BN, int MODE, int KB = 1>
+template <int BN, int MODE, int KB = 1, bool F8 = false>
 cudaError_t launch_bn_mode(const TcGemm& g, cudaStream_t st) {
-  auto k = gemm_tc_kernel<BN, MODE, KB>;
+  auto k = gemm_tc_kernel<BN, MODE, KB, F8>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
     attr_err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<BN>());
   });
   if (attr_err != cudaSuccess) return attr_err;
-  TcEpi e{g.M, g.N, g.K, g.H, g.k, g.C, g.ldc, g.Cb, g.ldcb, g.CbT, g.ldct, g.bias, g.R, g.ldr, g.Aux, g.ldaux, g.err};
+  TcEpi e{g.M, g.N, g.K, g.H, g.k, g.C, g.ldc, g.Cb, g.ldcb, g.CbT, g.ldct, g.bias, g.R, g.ldr, g.Aux, g.ldaux, g.err,
+          g.inv_a, g.inv_b, g.b_early ? 1 : 0};
   const int ntile = (MODE == TC_BRANCH) ? (g.H + 31) / 32 : (g.N + BN - 1) / BN;
   dim3 grid(ntile, (g.M + BM - 1) / BM);
   return launch_k(k, grid, dim3(128), smem_bytes<BN>(), st, g.ta, g.tb, e);
@@ -481,33 +516,65 @@ int make_tmap_bf16(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t co
   return EDPC_OK;
 }
 
+int make_tmap_u8(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows) {
+  auto enc = get_encode();
+  if (!enc) return fail(EDPC_ECUDA, "cuTensorMapEncodeTiled is not available");
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld & 15))
+    return fail(EDPC_EINVAL, "FP8 tensor map base or row stride is not 16-byte aligned");
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {ld};
+  cuuint32_t box[2] = {128, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(EDPC_ECUDA, "cuTensorMapEncodeTiled (u8) failed: " + std::to_string((int)r));
+  return EDPC_OK;
+}
+
+namespace {
+template <bool F8>
+cudaError_t launch_gemm_tc_t(const TcGemm& g, cudaStream_t st);
+}
+
 cudaError_t launch_gemm_tc(const TcGemm& g, cudaStream_t st) {
   if (g.M <= 0 || g.N <= 0 || g.K <= 0) return cudaSuccess;
+  if (g.fp8) {
+    if (!g.inv_a || !g.inv_b) return cudaErrorInvalidValue;
+    return launch_gemm_tc_t<true>(g, st);
+  }
+  return launch_gemm_tc_t<false>(g, st);
+}
+
+namespace {
+template <bool F8>
+cudaError_t launch_gemm_tc_t(const TcGemm& g, cudaStream_t st) {
   // The kernel's B tile (and the expected TMA byte count) must match the box
   // the tensor map was encoded with; refuse any mismatch before launching.
   if (g.mode == TC_BRANCH) {
     if (g.box_b != 32 || g.k < 1 || g.k > 3) return cudaErrorInvalidValue;
     switch (g.k) {
-      case 1: return launch_bn_mode<32, TC_BRANCH>(g, st);
-      case 2: return launch_bn_mode<64, TC_BRANCH>(g, st);
-      default: return launch_bn_mode<96, TC_BRANCH>(g, st);
+      case 1: return launch_bn_mode<32, TC_BRANCH, 1, F8>(g, st);
+      case 2: return launch_bn_mode<64, TC_BRANCH, 1, F8>(g, st);
+      default: return launch_bn_mode<96, TC_BRANCH, 1, F8>(g, st);
     }
   }
   if (g.box_b != g.bn) return cudaErrorInvalidValue;
   if (g.mode == TC_BRANCH_BWD) {
     if (g.bn != 32 || g.k < 1 || g.k > 3) return cudaErrorInvalidValue;
     switch (g.k) {
-      case 1: return launch_bn_mode<32, TC_BRANCH_BWD, 1>(g, st);
-      case 2: return launch_bn_mode<32, TC_BRANCH_BWD, 2>(g, st);
-      default: return launch_bn_mode<32, TC_BRANCH_BWD, 3>(g, st);
+      case 1: return launch_bn_mode<32, TC_BRANCH_BWD, 1, F8>(g, st);
+      case 2: return launch_bn_mode<32, TC_BRANCH_BWD, 2, F8>(g, st);
+      default: return launch_bn_mode<32, TC_BRANCH_BWD, 3, F8>(g, st);
     }
   }
   switch (g.bn) {
-    case 32: return launch_bn_mode<32, TC_PLAIN>(g, st);
-    case 64: return launch_bn_mode<64, TC_PLAIN>(g, st);
-    case 128: return launch_bn_mode<128, TC_PLAIN>(g, st);
+    case 32: return launch_bn_mode<32, TC_PLAIN, 1, F8>(g, st);
+    case 64: return launch_bn_mode<64, TC_PLAIN, 1, F8>(g, st);
+    case 128: return launch_bn_mode<128, TC_PLAIN, 1, F8>(g, st);
     default: return cudaErrorInvalidValue;
   }
 }
+}  // namespace
 
 }  // namespace edpc

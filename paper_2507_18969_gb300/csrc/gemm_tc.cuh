@@ -21,10 +21,11 @@ namespace edpc {
 enum TcMode { TC_PLAIN = 0, TC_BRANCH = 1, TC_BRANCH_BWD = 2 };
 
 // C[m][n] = sum_k A[m][k] B[n][k] (+ epilogue); A is M x K and B is N x K,
-// both BF16 and K-contiguous; accumulation is FP32 in TMEM.
+// both BF16 (or both FP8 e4m3 with power-of-two per-tensor scales) and
+// K-contiguous; accumulation is FP32 in TMEM.
 struct TcGemm {
-  CUtensorMap ta;  // A: box 64 (K) x 128 (M), 128-byte swizzle
-  CUtensorMap tb;  // B: box 64 (K) x bn (N) (TC_BRANCH: 64 x 32 per section)
+  CUtensorMap ta;  // A: box 128 bytes of K x 128 (M), 128-byte swizzle
+  CUtensorMap tb;  // B: box 128 bytes of K x bn (N) (TC_BRANCH: x 32 per section)
   int M = 0, N = 0, K = 0;
   int bn = 64;     // N tile: 32, 64 or 128 (TC_BRANCH: 32 * k); must equal tb's box rows
   int box_b = 0;   // rows of tb's box, recorded by the plan (checked at launch)
@@ -42,6 +43,10 @@ struct TcGemm {
   const float* Aux = nullptr;
   int ldaux = 0;
   int* err = nullptr;  // set to kErrTcTimeout if a bounded wait expired
+  bool fp8 = false;    // operands are e4m3; acc is multiplied by inv_a[0] * inv_b[0]
+  bool b_early = true; // B was written two or more launches back: prefetch it before the PDL wait
+  const float* inv_a = nullptr;
+  const float* inv_b = nullptr;
 };
 
 constexpr int kErrTcTimeout = 4;
@@ -50,6 +55,9 @@ constexpr int kErrTcTimeout = 4;
 // elements, for boxes of 64 columns x box_rows rows. Returns 0 or an EDPC code.
 int make_tmap_bf16(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
                    uint32_t box_rows);
+// The same for a byte matrix (FP8 e4m3) with row stride ld bytes and boxes of
+// 128 columns x box_rows rows.
+int make_tmap_u8(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
 
 cudaError_t launch_gemm_tc(const TcGemm& g, cudaStream_t st);
 

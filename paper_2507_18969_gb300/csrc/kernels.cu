@@ -4,6 +4,10 @@
 // memory in warp order), and nothing is accumulated with floating-point
 // atomics. So the encoder and the decoder, which launch the same kernels on
 // the same values, compute bit-identical probabilities and CDFs.
+#include <cuda_fp8.h>
+
+#include <algorithm>
+
 #include "kernels.cuh"
 #include "launch.cuh"
 
@@ -1488,6 +1492,94 @@ cudaError_t launch_to_bf16(const float* X, int rows, int cols, int ldx, __nv_bfl
                            __nv_bfloat16* YT, int ldt, cudaStream_t st) {
   dim3 grid(div_up(cols, 32), div_up(rows, 32));
   return launch_k(to_bf16_kernel, dim3(grid), dim3(256), 0, st, X, rows, cols, ldx, Y, ldy, YT, ldt);
+}
+
+// ============================================================================================
+// FP8 e4m3 operand quantization: amax pass (integer atomicMax on the float bits
+// of |x|, order-independent), then the convert pass with s = 2^k.
+// ============================================================================================
+__device__ __forceinline__ int fp8_exp(float amax) {
+  if (!(amax > 0.f)) return 0;
+  int e;
+  frexpf(amax, &e);  // amax = m 2^e, m in [0.5, 1)
+  int k = 9 - e;     // amax 2^k in [256, 512)
+  if (ldexpf(amax, k) > 448.f) k -= 1;
+  return k < -120 ? -120 : (k > 120 ? 120 : k);
+}
+
+__global__ void fp8_amax_kernel(Fp8Jobs J) {
+  pdl_wait();
+  pdl_launch();
+  const Fp8Job& jb = J.job[blockIdx.y];
+  const long long n8 = (long long)jb.rows * (jb.cols / 8);  // 8 BF16 per 16-byte load
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n8; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / (jb.cols / 8), c = (i % (jb.cols / 8)) * 8;
+    const uint4 v = *reinterpret_cast<const uint4*>(jb.src + r * jb.ld + c);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2 f = __bfloat1622float2(h[q]);
+      m = fmaxf(m, fmaxf(fabsf(f.x), fabsf(f.y)));
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float wm[32];
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wm[w]);
+    atomicMax(J.amax + jb.slot, __float_as_uint(m));
+  }
+}
+
+__global__ void fp8_convert_kernel(Fp8Jobs J) {
+  pdl_wait();
+  pdl_launch();
+  const Fp8Job& jb = J.job[blockIdx.y];
+  const int k = fp8_exp(__uint_as_float(J.amax[jb.slot]));
+  const float sc = ldexpf(1.f, k);
+  if (blockIdx.x == 0 && threadIdx.x == 0) J.inv[jb.slot] = ldexpf(1.f, -k);
+  const long long n8 = (long long)jb.rows * (jb.cols / 8);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n8; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / (jb.cols / 8), c = (i % (jb.cols / 8)) * 8;
+    const uint4 v = *reinterpret_cast<const uint4*>(jb.src + r * jb.ld + c);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+    uint8_t o[8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      float2 f = __bfloat1622float2(h[q]);
+      o[2 * q] = (uint8_t)__nv_cvt_float_to_fp8(f.x * sc, __NV_SATFINITE, __NV_E4M3);
+      o[2 * q + 1] = (uint8_t)__nv_cvt_float_to_fp8(f.y * sc, __NV_SATFINITE, __NV_E4M3);
+    }
+    *reinterpret_cast<uint2*>(jb.dst + r * jb.ld8 + c) = *reinterpret_cast<const uint2*>(o);
+  }
+}
+
+cudaError_t launch_fp8_quantize(const Fp8Jobs& J, cudaStream_t st) {
+  if (J.n <= 0) return cudaSuccess;
+  if (J.n > kMaxFp8Jobs) return cudaErrorInvalidValue;
+  long long most = 0;
+  for (int j = 0; j < J.n; ++j) {
+    const Fp8Job& jb = J.job[j];
+    // 16-byte loads and 8-byte stores: cols and both strides in whole vectors
+    if (jb.cols % 8 || jb.ld % 8 || jb.ld8 % 8) return cudaErrorInvalidValue;
+    most = std::max(most, (long long)jb.rows * (jb.cols / 8));
+  }
+  const int per_job = (int)std::min<long long>(std::max<long long>(1, (most + 255) / 256), 2 * 152);
+  cudaError_t e = launch_k(fp8_amax_kernel, dim3(per_job, J.n), dim3(256), 0, st, J);
+  if (e != cudaSuccess) return e;
+  return launch_k(fp8_convert_kernel, dim3(per_job, J.n), dim3(256), 0, st, J);
+}
+
+__global__ void zero_u32_kernel(unsigned* p, int n) {
+  pdl_wait();
+  pdl_launch();
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0u;
+}
+
+cudaError_t launch_zero_u32(unsigned* p, int n, cudaStream_t st) {
+  return launch_k(zero_u32_kernel, dim3(1), dim3(256), 0, st, p, n);
 }
 
 }  // namespace edpc

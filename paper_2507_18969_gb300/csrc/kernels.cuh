@@ -186,4 +186,28 @@ cudaError_t launch_transpose_tiles(const __nv_bfloat16* Pb, __nv_bfloat16* PbT, 
 cudaError_t launch_to_bf16(const float* X, int rows, int cols, int ldx, __nv_bfloat16* Y, int ldy,
                            __nv_bfloat16* YT, int ldt, cudaStream_t st);
 
+// ---- FP8 e4m3 operands (per-tensor power-of-two scales) --------------------------------------
+// Each job quantizes a BF16 matrix src [rows][ld] (cols used) into e4m3 bytes
+// dst [rows][ld8] with scale s = 2^k, k the largest integer with
+// amax * 2^k <= 448 (amax = max |src|; k = 0 when amax = 0). inv[slot]
+// receives 2^-k. amax[slot] (float bits, non-negative) must start at 0: the
+// max is taken with integer atomicMax, which gives the same result in any
+// order.
+constexpr int kMaxFp8Jobs = 16;
+struct Fp8Job {
+  const __nv_bfloat16* src;
+  int rows, cols, ld;
+  uint8_t* dst;
+  int ld8;
+  int slot;
+};
+struct Fp8Jobs {
+  Fp8Job job[kMaxFp8Jobs];
+  int n;
+  unsigned* amax;
+  float* inv;
+};
+cudaError_t launch_fp8_quantize(const Fp8Jobs& jobs, cudaStream_t st);  // two launches: amax, convert
+cudaError_t launch_zero_u32(unsigned* p, int n, cudaStream_t st);
+
 }  // namespace edpc
