@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="skip the FP32, decompress, e2e and CPU legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle model steps for cpu_baseline (0 = auto)")
+    ap.add_argument("--precision-sweep", action="store_true",
+                    help="also compress the whole workload in FP32, BF16 and FP8 e4m3 (bits/byte, MB/s)")
     return ap.parse_args()
 
 
@@ -389,6 +391,27 @@ def run_ours(args, d: Dist):
         assert torch.equal(outd.cpu(), host), "decompressed bytes differ from the input"
         decomp_value, _ = aggregate(donedec * b, tdec, d)
 
+    # ---- whole workload in each GEMM precision (bits/byte and throughput) ----------------------
+    sweep = None
+    if args.precision_sweep:
+        sweep = {}
+        for name, prec in (("fp32", edpc.EDPC_FP32), ("bf16", edpc.EDPC_BF16), ("fp8e4m3", edpc.EDPC_FP8E4M3)):
+            enc = edpc.Encoder(make_cfg(prec), device_ptr=xd.data_ptr(), length=x.size, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bits = enc.finish()
+            tt = time.perf_counter() - t0
+            enc.close()
+            _, n, be = edpc.peek(bits)
+            sweep[name] = {"bits_per_byte": 8 * (len(bits) - (88 + 4 * be + 4)) / n, "compress_mbs": n / tt / 1e6,
+                           "seconds": tt}
+            if name == "fp8e4m3":
+                outd = torch.empty(x.size, dtype=torch.uint8, device="cuda")
+                dec = edpc.Decoder(bits, out_device_ptr=outd.data_ptr(), stream=stream.cuda_stream)
+                dec.finish(to_host=False)
+                dec.close()
+                assert torch.equal(outd, xd), "FP8 round trip failed"
+
     # ---- roofline of the dominant kernel ------------------------------------------------------
     # Per model step the FDM moves 24 B per element in its Adam update (read U,
     # m, v; write U, m, v) and 4 B in each of the forward and the dx' adjoint.
@@ -401,9 +424,16 @@ def run_ours(args, d: Dist):
     def gbs(nbytes, ms):
         return nbytes / (ms / 1e3) / 1e9 if ms else None
 
-    kname, prof, alg, ms = ("fdm_bwd_kernel (FDM adjoint + Adam)", "fdm_bwd_adam_" + args.workload,
-                            24 * fdm_elems, st.fdm_bwd_ms)
-    others = {}
+    if st.fdm_adam_ms:
+        # dx' on the step's stream, the update of U, m, v on its own stream
+        kname, prof, alg, ms = ("fdm_adam_kernel (FDM update: Adam on U, m, v)", "fdm_adam_" + args.workload,
+                                24 * fdm_elems, st.fdm_adam_ms)
+        others = {"fdm_dx": {"alg_bytes_per_launch": 4 * fdm_elems, "mean_ms": st.fdm_bwd_ms,
+                             "achieved": gbs(4 * fdm_elems, st.fdm_bwd_ms)}}
+    else:
+        kname, prof, alg, ms = ("fdm_bwd_kernel (FDM adjoint + Adam)", "fdm_bwd_adam_" + args.workload,
+                                24 * fdm_elems, st.fdm_bwd_ms)
+        others = {}
     achieved = gbs(alg, ms)
     others["fdm_fwd"] = {"alg_bytes_per_launch": 4 * fdm_elems, "mean_ms": st.fdm_fwd_ms,
                          "achieved": gbs(4 * fdm_elems, st.fdm_fwd_ms)}
@@ -441,6 +471,8 @@ def run_ours(args, d: Dist):
             "e2e": e2e, "gpu_launches": out["launches"],
             "roofline": roof, "cpu_baseline": cpu, "clocks": out["clocks"],
         }
+        if sweep:
+            line["precision_sweep"] = sweep
         print(json.dumps(line), flush=True)
 
 
@@ -532,7 +564,8 @@ def run_files(args, d: Dist):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     peak = peaks.get("hbm_gbs", 6800.0)
     alg = 24 * fdm_elems_active
-    ach = alg / (st.fdm_bwd_ms / 1e3) / 1e9 if st.fdm_bwd_ms else None
+    upd_ms = st.fdm_adam_ms or st.fdm_bwd_ms
+    ach = alg / (upd_ms / 1e3) / 1e9 if upd_ms else None
     if d.rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "MB/s", "n_gpus": d.world, "steps": K, "warmup": W,
@@ -549,9 +582,10 @@ def run_files(args, d: Dist):
                          "open_seconds_with_tile_tuning": t_open},
             "window_bytes": nbytes, "decompress_mbs": decomp, "bits_per_byte": bpb,
             "bits_per_byte_input": "the e2e sample files, whole", "e2e": e2e, "gpu_launches": launches,
-            "roofline": {"kernel": "fdm_bwd_kernel (FDM adjoint + Adam)", "bound": "hbm", "achieved": ach,
+            "roofline": {"kernel": "fdm_adam_kernel (FDM update)" if st.fdm_adam_ms else
+                         "fdm_bwd_kernel (FDM adjoint + Adam)", "bound": "hbm", "achieved": ach,
                          "peak": peak, "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": None,
-                         "alg_bytes_per_launch": alg, "mean_ms": st.fdm_bwd_ms,
+                         "alg_bytes_per_launch": alg, "mean_ms": upd_ms,
                          "note": "algorithmic bytes count the streams active at the window's start"},
             "cpu_baseline": None, "clocks": ck,
         }

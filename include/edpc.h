@@ -63,6 +63,11 @@ extern "C" {
 #define EDPC_FLAG_NO_GRAPH 2u     /* launch every kernel eagerly (no CUDA graph) */
 #define EDPC_FLAG_TUNE_TILES 4u   /* BF16: time each GEMM's N tile at open and record the
                                      choice in the header (file sets always do) */
+#define EDPC_FLAG_OVERLAP_FDM 8u  /* BF16/FP8: run the FDM's Adam update as a persistent
+                                     kernel on its own stream, overlapping the rest of
+                                     the step and the next step's first layers (same
+                                     results; slower on GB300 at the measured sizes,
+                                     kept for comparison) */
 
 /*
  * Model and coder configuration. Everything here that changes the bitstream

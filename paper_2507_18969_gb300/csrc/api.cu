@@ -358,19 +358,22 @@ struct edpc_session {
   uint64_t steps_total = 0, steps_run = 0;
   bool finished = false;
 
-  // graph
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  int graph_kernels = 0;
-  cudaGraphNode_t ev_nodes[6] = {};
+  // CUDA graphs: `chunk` consecutive steps (so each step's FDM update can run
+  // under the next step's first layers), instantiated twice with separate
+  // timing events and launched alternately; and a one-step graph for step
+  // counts that do not fill a chunk.
+  cudaGraph_t g_chunk = nullptr, g_one = nullptr;
+  cudaGraphExec_t x_chunk[2] = {}, x_one = nullptr;
+  int graph_kernels = 0;  // kernels per step
 
-  // FDM kernel timing
+  // FDM kernel timing: event set k of chunk execution p is tev[p * chunk + k];
+  // the one-step graph (and eager steps) use the sets after those.
   bool profiling = false;
-  static constexpr int kEvSets = 64;
-  static constexpr int kEv = 6;  // FDM forward, adjoint (dx'), side Adam: start/end each
+  static constexpr int kChunk = 64;
+  static constexpr int kEvSets = 2 * kChunk + 1;
+  static constexpr int kEv = 6;  // FDM forward, adjoint (dx'), FDM update: start/end each
   cudaEvent_t tev[kEvSets][kEv] = {};
   bool has_adam_ev = false;
-  uint64_t tev_step[kEvSets] = {};
   bool tev_live[kEvSets] = {};
   double fwd_ms = 0, bwd_ms = 0, adam_ms = 0;
   uint64_t samples = 0;
@@ -380,7 +383,8 @@ struct edpc_session {
   ~edpc_session();
   int setup_common(const edpc_cfg& c, uint64_t n_, void* stream, const StreamLayout* explicit_lay = nullptr);
   int capture_graph();
-  int launch_step();
+  int capture(int nsteps, int set0, cudaGraph_t* g);
+  int launch_steps(uint64_t n);
   int code_pending();
   int join();
   int harvest(int k);
@@ -389,8 +393,11 @@ struct edpc_session {
 edpc_session::~edpc_session() {
   if (st) cudaStreamSynchronize(st);
   if (st_coder) cudaStreamSynchronize(st_coder);
-  if (exec) cudaGraphExecDestroy(exec);
-  if (graph) cudaGraphDestroy(graph);
+  for (auto& x : x_chunk)
+    if (x) cudaGraphExecDestroy(x);
+  if (x_one) cudaGraphExecDestroy(x_one);
+  if (g_chunk) cudaGraphDestroy(g_chunk);
+  if (g_one) cudaGraphDestroy(g_one);
   for (auto& e : ev_model)
     if (e) cudaEventDestroy(e);
   for (auto& e : ev_coder)
@@ -481,42 +488,63 @@ int edpc_session::setup_common(const edpc_cfg& c, uint64_t n_, void* stream, con
   return EDPC_OK;
 }
 
-int edpc_session::capture_graph() {
-  if (!use_graph || steps_total == 0) return EDPC_OK;
-  // Four FDM timing events are recorded in the graph; their nodes are re-pointed
-  // at per-step event sets when profiling (cudaGraphExecEventRecordNodeSetEvent).
-  for (int k = 0; k < kEv; ++k) model.ev_fdm[k] = tev[0][k];
+// Captures `nsteps` model steps (timing event sets set0, set0 + 1, ...) into
+// one graph that ends with every stream joined (the last FDM update waited for).
+int edpc_session::capture(int nsteps, int set0, cudaGraph_t* g) {
   model.timing = true;
   EDPC_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  int r = model.step(io, st);
-  cudaGraph_t g = nullptr;
-  cudaError_t ce = cudaStreamEndCapture(st, &g);
+  int r = EDPC_OK;
+  for (int k = 0; k < nsteps && r == EDPC_OK; ++k) {
+    for (int q = 0; q < kEv; ++q) model.ev_fdm[q] = tev[set0 + k][q];
+    r = model.step(io, st);
+  }
+  if (r == EDPC_OK) r = model.flush(st);
+  cudaError_t ce = cudaStreamEndCapture(st, g);
   model.timing = false;
   if (r != EDPC_OK) {
-    if (g) cudaGraphDestroy(g);
+    if (*g) cudaGraphDestroy(*g);
+    *g = nullptr;
     return r;
   }
   if (ce != cudaSuccess) return fail(EDPC_ECUDA, std::string("stream capture: ") + cudaGetErrorString(ce));
-  graph = g;
-  EDPC_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  return EDPC_OK;
+}
+
+int edpc_session::capture_graph() {
+  has_adam_ev = model.side_fdm != nullptr;
+  if (!use_graph || steps_total == 0) return EDPC_OK;
+  chunk = kChunk;
+  EDPC_TRY(capture(1, 2 * kChunk, &g_one));
+  EDPC_CUDA(cudaGraphInstantiate(&x_one, g_one, 0));
   size_t nn = 0;
-  EDPC_CUDA(cudaGraphGetNodes(graph, nullptr, &nn));
+  EDPC_CUDA(cudaGraphGetNodes(g_one, nullptr, &nn));
   std::vector<cudaGraphNode_t> nodes(nn);
-  EDPC_CUDA(cudaGraphGetNodes(graph, nodes.data(), &nn));
+  EDPC_CUDA(cudaGraphGetNodes(g_one, nodes.data(), &nn));
   graph_kernels = 0;
-  for (auto& nd : ev_nodes) nd = nullptr;
   for (auto nd : nodes) {
     cudaGraphNodeType t;
     EDPC_CUDA(cudaGraphNodeGetType(nd, &t));
     if (t == cudaGraphNodeTypeKernel) ++graph_kernels;
-    if (t == cudaGraphNodeTypeEventRecord) {
-      cudaEvent_t e;
-      EDPC_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &e));
-      for (int k = 0; k < kEv; ++k)
-        if (e == tev[0][k]) ev_nodes[k] = nd;
-    }
   }
-  has_adam_ev = ev_nodes[4] && ev_nodes[5];
+  if (steps_total < (uint64_t)kChunk) return EDPC_OK;
+  EDPC_TRY(capture(kChunk, 0, &g_chunk));
+  EDPC_CUDA(cudaGraphInstantiate(&x_chunk[0], g_chunk, 0));
+  EDPC_CUDA(cudaGraphInstantiate(&x_chunk[1], g_chunk, 0));
+  // the second instantiation records into event sets kChunk .. 2 kChunk - 1
+  nn = 0;
+  EDPC_CUDA(cudaGraphGetNodes(g_chunk, nullptr, &nn));
+  nodes.resize(nn);
+  EDPC_CUDA(cudaGraphGetNodes(g_chunk, nodes.data(), &nn));
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    EDPC_CUDA(cudaGraphNodeGetType(nd, &t));
+    if (t != cudaGraphNodeTypeEventRecord) continue;
+    cudaEvent_t e;
+    EDPC_CUDA(cudaGraphEventRecordNodeGetEvent(nd, &e));
+    for (int k = 0; k < kChunk; ++k)
+      for (int q = 0; q < kEv; ++q)
+        if (e == tev[k][q]) EDPC_CUDA(cudaGraphExecEventRecordNodeSetEvent(x_chunk[1], nd, tev[kChunk + k][q]));
+  }
   return EDPC_OK;
 }
 
@@ -538,35 +566,44 @@ int edpc_session::harvest(int k) {
   return EDPC_OK;
 }
 
-int edpc_session::launch_step() {
-  const uint64_t j = steps_run;
-  if (encoder && pipeline && j % chunk == 0 && j >= (uint64_t)(2 * chunk))
-    EDPC_CUDA(cudaStreamWaitEvent(st, ev_coder[(j / chunk) % 2], 0));
-  int k = (int)(j % kEvSets);
-  if (profiling) {
-    EDPC_TRY(harvest(k));
-    if (exec) {
-      for (int q = 0; q < kEv; ++q)
-        if (ev_nodes[q]) EDPC_CUDA(cudaGraphExecEventRecordNodeSetEvent(exec, ev_nodes[q], tev[k][q]));
+// Launches the next n model steps: whole chunks through the chunk graph when
+// aligned, else one step at a time (one-step graph, or eagerly).
+int edpc_session::launch_steps(uint64_t n) {
+  uint64_t k = 0;
+  while (k < n) {
+    const uint64_t j = steps_run;
+    if (encoder && pipeline && j % chunk == 0 && j >= (uint64_t)(2 * chunk))
+      EDPC_CUDA(cudaStreamWaitEvent(st, ev_coder[(j / chunk) % 2], 0));
+    uint64_t adv = 1;
+    if (x_chunk[0] && j % chunk == 0 && n - k >= (uint64_t)chunk && steps_total - j >= (uint64_t)chunk) {
+      const int p = (int)((j / chunk) % 2);
+      if (profiling)
+        for (int q = 0; q < chunk; ++q) EDPC_TRY(harvest(p * chunk + q));
+      EDPC_CUDA(cudaGraphLaunch(x_chunk[p], st));
+      if (profiling)
+        for (int q = 0; q < chunk; ++q) tev_live[p * chunk + q] = true;
+      adv = (uint64_t)chunk;
+    } else if (x_one) {
+      const int set = 2 * kChunk;
+      if (profiling) EDPC_TRY(harvest(set));
+      EDPC_CUDA(cudaGraphLaunch(x_one, st));
+      if (profiling) tev_live[set] = true;
     } else {
-      for (int q = 0; q < kEv; ++q) model.ev_fdm[q] = tev[k][q];
-      model.timing = true;
-      has_adam_ev = model.side && model.d.Fp % 128 == 0;
+      const int set = (int)(j % (2 * kChunk));
+      if (profiling) {
+        EDPC_TRY(harvest(set));
+        for (int q = 0; q < kEv; ++q) model.ev_fdm[q] = tev[set][q];
+        model.timing = true;
+      }
+      int r = model.step(io, st);
+      model.timing = false;
+      if (r != EDPC_OK) return r;
+      if (profiling) tev_live[set] = true;
     }
+    steps_run += adv;
+    k += adv;
+    if (encoder && steps_run % chunk == 0) EDPC_TRY(code_pending());
   }
-  if (exec) {
-    EDPC_CUDA(cudaGraphLaunch(exec, st));
-  } else {
-    int r = model.step(io, st);
-    model.timing = false;
-    if (r != EDPC_OK) return r;
-  }
-  if (profiling) {
-    tev_live[k] = true;
-    tev_step[k] = j;
-  }
-  ++steps_run;
-  if (encoder && steps_run % chunk == 0) EDPC_TRY(code_pending());
   return EDPC_OK;
 }
 
@@ -590,6 +627,7 @@ int edpc_session::code_pending() {
 }
 
 int edpc_session::join() {
+  EDPC_TRY(model.flush(st));  // eager steps leave the last FDM update pending
   if (encoder && pipeline) {
     EDPC_CUDA(cudaEventRecord(ev_join, st_coder));
     EDPC_CUDA(cudaStreamWaitEvent(st, ev_join, 0));
@@ -702,7 +740,7 @@ extern "C" int edpc_session_run(edpc_session* s, uint64_t max_steps, int sync, u
   if (s->finished) return fail(EDPC_EINVAL, "session already finished");
   uint64_t left = s->steps_total - s->steps_run;
   uint64_t n = std::min(left, max_steps);
-  for (uint64_t k = 0; k < n; ++k) EDPC_TRY(s->launch_step());
+  EDPC_TRY(s->launch_steps(n));
   EDPC_TRY(s->join());
   if (sync) EDPC_CUDA(cudaStreamSynchronize(s->st));
   if (steps_done) *steps_done = n;
@@ -1245,6 +1283,7 @@ extern "C" int edpc_model_train_step(edpc_model* mm, const uint8_t* ctx, const u
   EDPC_TRY(model_prepare(mm, ctx, targets, active, mm->t + 1, &io));
   io.update = 1;
   EDPC_TRY(m.step(io, 0));
+  EDPC_TRY(m.flush(0));
   EDPC_CUDA(cudaDeviceSynchronize());
   mm->t += 1;
   return EDPC_OK;

@@ -102,6 +102,7 @@ int probe(const edpc_cfg& c, int b, size_t* bytes, double* ms) {
   io.ring_slots = 1;
   if (r == EDPC_OK && cu(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "capture")) {
     int rs = m.step(io, st);
+    if (rs == EDPC_OK) rs = m.flush(st);
     cudaError_t ce = cudaStreamEndCapture(st, &g);
     if (rs != EDPC_OK && r == EDPC_OK) r = rs;
     cu(ce, "capture end");

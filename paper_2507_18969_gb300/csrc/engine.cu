@@ -128,7 +128,10 @@ Model::~Model() {
     if (e) cudaEventDestroy(e);
   if (join_ev) cudaEventDestroy(join_ev);
   if (tr_ev) cudaEventDestroy(tr_ev);
+  if (dx_ev) cudaEventDestroy(dx_ev);
+  if (adam_ev) cudaEventDestroy(adam_ev);
   if (side) cudaStreamDestroy(side);
+  if (side_fdm) cudaStreamDestroy(side_fdm);
   if (gU) cudaFree(gU);
   if (f8_arena) cudaFree(f8_arena);
   if (arena_) cudaFree(arena_);
@@ -145,6 +148,7 @@ int Model::init(const edpc_cfg& cfg, int streams) {
   const int kH = d.k * d.H;
   const size_t bkH = (size_t)d.b * kH, fdm = (size_t)d.b * d.Fp * d.Fp;
   const bool bf16 = precision != EDPC_FP32;  // BF16 operand copies (also the FP8 mode's sources)
+  const bool overlap = bf16 && (cfg.flags & EDPC_FLAG_OVERLAP_FDM);
   const size_t T = d.ldT;
 
   // weight matrices that need transposed BF16 copies (32 x 32 tiles)
@@ -193,6 +197,11 @@ int Model::init(const edpc_cfg& cfg, int streams) {
     dz = a.take<float>((size_t)d.b * 256);
     dY = a.take<float>(bFp);
     dXp = a.take<float>(bFp);
+    if (overlap) {  // the FDM update runs on its own stream from these copies
+      xp_pend = a.take<float>(bFp);
+      dy_pend = a.take<float>(bFp);
+      pend = a.take<FdmPend>(1);
+    }
     emb_part = a.take<float>((size_t)embed_bwd_chunks(d.b, d.K) * 256 * d.D);
     if (!bf16) {
       dXa = a.take<float>(bF);
@@ -277,6 +286,11 @@ int Model::init(const edpc_cfg& cfg, int streams) {
     EDPC_TRY(refresh_bf16_weights(st));
     EDPC_TRY(build_tc_plan());
     EDPC_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
+    if (overlap) {
+      EDPC_CUDA(cudaStreamCreateWithFlags(&side_fdm, cudaStreamNonBlocking));
+      EDPC_CUDA(cudaEventCreateWithFlags(&dx_ev, cudaEventDisableTiming));
+      EDPC_CUDA(cudaEventCreateWithFlags(&adam_ev, cudaEventDisableTiming));
+    }
     for (auto& e : fork) EDPC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     EDPC_CUDA(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
     EDPC_CUDA(cudaEventCreateWithFlags(&tr_ev, cudaEventDisableTiming));
@@ -334,12 +348,19 @@ int Model::block_fwd(int j, const float* Xin, float* Xout, cudaStream_t st) {
 }
 
 int Model::fdm_fwd_call(const StepIO& io, cudaStream_t st) {
+  const bool waited = fdm_pending;
+  EDPC_TRY(flush(st));  // the previous step's FDM update must have landed
   if (timing && ev_fdm[0]) EDPC_CUDA(record_timing(ev_fdm[0], st));
   FdmAct act;
   act.ctl = ctl;
   act.sp = io.sp;
   act.active = io.mode == 2 ? io.active : nullptr;
-  EDPC_CUDA(launch_fdm_fwd(Xp, U, Y, d.b, d.Fp, st, Yb, YbT, d.ldT, &ctl->err, act));  // Eq. 15
+  if (waited) {
+    NoPdl scope;  // first launch after a cross-stream wait
+    EDPC_CUDA(launch_fdm_fwd(Xp, U, Y, d.b, d.Fp, st, Yb, YbT, d.ldT, &ctl->err, act));  // Eq. 15
+  } else {
+    EDPC_CUDA(launch_fdm_fwd(Xp, U, Y, d.b, d.Fp, st, Yb, YbT, d.ldT, &ctl->err, act));  // Eq. 15
+  }
   if (timing && ev_fdm[1]) EDPC_CUDA(record_timing(ev_fdm[1], st));
   return EDPC_OK;
 }
@@ -376,7 +397,51 @@ int Model::block_bwd(int j, const float* dOut, float* dXnew, cudaStream_t st) {
   return EDPC_OK;
 }
 
+int Model::flush(cudaStream_t st) {
+  if (!fdm_pending) return EDPC_OK;
+  EDPC_CUDA(cudaStreamWaitEvent(st, adam_ev, 0));
+  fdm_pending = false;
+  return EDPC_OK;
+}
+
 int Model::fdm_bwd_call(const StepIO& io, cudaStream_t st) {
+  if (side_fdm && io.update) {
+    // dx' now (the rest of the adjoint needs it); U's Adam update on its own
+    // stream, overlapping the rest of this step and the next step's layers up
+    // to the FDM forward, which waits for it (flush).
+    FdmSplitArgs sa{};
+    sa.Xp = Xp;
+    sa.dY = dY;
+    sa.U = U;
+    sa.Um = Um;
+    sa.Uv = Uv;
+    sa.dXp = dXp;
+    sa.dXpb = dXpb;
+    sa.dXpbT = dXpbT;
+    sa.ldT = d.ldT;
+    sa.xp_pend = xp_pend;
+    sa.dy_pend = dy_pend;
+    sa.pend = pend;
+    sa.ctl = ctl;
+    sa.sp = io.sp;
+    sa.active = io.mode == 2 ? io.active : nullptr;
+    sa.b = d.b;
+    sa.Fp = d.Fp;
+    if (timing && ev_fdm[2]) EDPC_CUDA(record_timing(ev_fdm[2], st));
+    EDPC_CUDA(launch_fdm_dx(sa, st));
+    if (timing && ev_fdm[3]) EDPC_CUDA(record_timing(ev_fdm[3], st));
+    EDPC_CUDA(cudaEventRecord(dx_ev, st));
+    EDPC_CUDA(cudaStreamWaitEvent(side_fdm, dx_ev, 0));
+    {
+      NoPdl scope;
+      if (timing && ev_fdm[4]) EDPC_CUDA(record_timing(ev_fdm[4], side_fdm));
+      EDPC_CUDA(launch_fdm_adam(sa, side_fdm));
+      if (timing && ev_fdm[5]) EDPC_CUDA(record_timing(ev_fdm[5], side_fdm));
+    }
+    EDPC_CUDA(cudaEventRecord(adam_ev, side_fdm));
+    fdm_pending = true;
+    return EDPC_OK;
+  }
   FdmBwdArgs fa{};
   fa.Xp = Xp;
   fa.dY = dY;

@@ -73,9 +73,17 @@ class Model {
   cudaEvent_t fork[kForks] = {};
   cudaEvent_t join_ev = nullptr;
   cudaEvent_t tr_ev = nullptr;                             // transposed weight copies ready
+  // FDM update off the critical path (BF16/FP8): dx' on the step's stream, the
+  // Adam update of U, m, v on side_fdm from the pending copies; the next FDM
+  // forward waits for adam_ev.
+  cudaStream_t side_fdm = nullptr;
+  cudaEvent_t dx_ev = nullptr, adam_ev = nullptr;
+  float *xp_pend = nullptr, *dy_pend = nullptr;
+  FdmPend* pend = nullptr;
+  bool fdm_pending = false;                                // an update was launched and not yet waited for
   bool emb_in_adam = false;                                // dE left to Adam this step
 
-  // FDM kernel timing (optional): forward [0,1], adjoint [2,3], split Adam [4,5]
+  // FDM kernel timing (optional): forward [0,1], adjoint dx' [2,3], update [4,5]
   cudaEvent_t ev_fdm[6] = {};
   bool timing = false;
 
@@ -104,6 +112,9 @@ class Model {
   int backward(const StepIO& io, cudaStream_t st);
   int adam(cudaStream_t st);
   int step(const StepIO& io, cudaStream_t st);
+  // Makes `st` wait for a pending FDM update (call before reading U, and before
+  // ending a graph capture).
+  int flush(cudaStream_t st);
   int launches_per_step() const;
   int refresh_bf16_weights(cudaStream_t st);
   size_t device_bytes() const { return arena_bytes_; }

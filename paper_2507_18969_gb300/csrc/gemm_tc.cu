@@ -33,7 +33,7 @@ constexpr int BKB = 128;  // bytes of K per stage row (one 128-byte swizzle span
 template <bool F8>
 constexpr int bk_elems() { return F8 ? 128 : 64; }
 // Pipeline depth: enough stages to hold the whole K panel in flight for the
-// small-N tiles (8 x 20-24 KB), 4 for 128-wide tiles.
+// small-N tiles (8 x 20-24 KB), 4 for wider tiles.
 template <int BN>
 constexpr int stages_for() { return BN <= 64 ? 8 : 4; }
 constexpr uint32_t kSpinLimit = 1u << 26;
@@ -475,6 +475,8 @@ cudaError_t launch_bn_mode(const TcGemm& g, cudaStream_t st) {
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
     attr_err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes<BN>());
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
   });
   if (attr_err != cudaSuccess) return attr_err;
   TcEpi e{g.M, g.N, g.K, g.H, g.k, g.C, g.ldc, g.Cb, g.ldcb, g.CbT, g.ldct, g.bias, g.R, g.ldr, g.Aux, g.ldaux, g.err,

@@ -550,6 +550,168 @@ __global__ void __launch_bounds__(256) fdm_bwd_kernel(FdmBwdArgs a) {
   }
 }
 
+// ---- split form: dx' on the critical path, the update on a side stream ------------------------
+__device__ __forceinline__ bool fdm_split_active(const FdmSplitArgs& a, int s, long long i) {
+  return a.active ? (a.active[s] != 0) : (i < a.sp.len(s));
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(256) fdm_dx_kernel(FdmSplitArgs a) {
+  pdl_wait();
+  pdl_launch();
+  const int s = blockIdx.y;
+  const int Fp = a.Fp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const StepCtl c = *a.ctl;
+  const int row0 = blockIdx.x * kFdmRowsPerCta;
+  if (blockIdx.x == 0 && s == 0 && threadIdx.x == 0) *a.pend = FdmPend{c.i, c.lr, c.bc1, c.bc2};
+  const bool act = fdm_split_active(a, s, c.i);
+  if (blockIdx.x == 0 && act) {  // the update's inputs, kept past this step's x' and dy
+    for (int j = threadIdx.x; j < Fp; j += blockDim.x) {
+      a.xp_pend[(size_t)s * Fp + j] = a.Xp[(size_t)s * Fp + j];
+      a.dy_pend[(size_t)s * Fp + j] = a.dY[(size_t)s * Fp + j];
+    }
+  }
+  FdmBwdArgs o{};
+  o.dXp = a.dXp;
+  o.dXpb = a.dXpb;
+  o.dXpbT = a.dXpbT;
+  o.ldT = a.ldT;
+  o.Fp = Fp;
+  if (!act) {
+    for (int r = warp; r < kFdmRowsPerCta; r += 8)
+      if (lane == 0 && row0 + r < Fp) store_dxp(o, s, row0 + r, 0.f);
+    return;
+  }
+  float4 dy[NCH];
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) dy[q] = reinterpret_cast<const float4*>(a.dY + (size_t)s * Fp)[lane + 32 * q];
+  for (int r = warp; r < kFdmRowsPerCta; r += 8) {
+    const int i = row0 + r;
+    if (i >= Fp) break;
+    const float4* U4 = reinterpret_cast<const float4*>(a.U + ((size_t)s * Fp + i) * Fp);
+    float4 u[NCH];
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) u[q] = __ldcs(U4 + lane + 32 * q);
+    float dot = 0.f;
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+      dot += u[q].x * dy[q].x;
+      dot += u[q].y * dy[q].y;
+      dot += u[q].z * dy[q].z;
+      dot += u[q].w * dy[q].w;
+    }
+    dot = warp_sum(dot);
+    if (lane == 0) store_dxp(o, s, i, dot);
+  }
+}
+
+template <int NCH>
+__global__ void __launch_bounds__(256) fdm_adam_kernel(FdmSplitArgs a) {
+  pdl_wait();
+  pdl_launch();
+  const int s = blockIdx.y;
+  const int Fp = a.Fp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const FdmPend pd = *a.pend;
+  if (!fdm_split_active(a, s, pd.i)) return;  // a finished stream's FDM is left as is
+  const int row0 = blockIdx.x * kFdmRowsPerCta;
+  float4 dy[NCH];
+#pragma unroll
+  for (int q = 0; q < NCH; ++q) dy[q] = reinterpret_cast<const float4*>(a.dy_pend + (size_t)s * Fp)[lane + 32 * q];
+  for (int r = warp; r < kFdmRowsPerCta; r += 8) {
+    const int i = row0 + r;
+    if (i >= Fp) break;
+    const float xi = a.xp_pend[(size_t)s * Fp + i];
+    const size_t ro = ((size_t)s * Fp + i) * Fp;
+    float4* U4 = reinterpret_cast<float4*>(a.U + ro);
+    float4* M4 = reinterpret_cast<float4*>(a.Um + ro);
+    float4* V4 = reinterpret_cast<float4*>(a.Uv + ro);
+    float4 u[NCH], m[NCH], v[NCH];
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+      u[q] = __ldcs(U4 + lane + 32 * q);
+      m[q] = __ldcs(M4 + lane + 32 * q);
+      v[q] = __ldcs(V4 + lane + 32 * q);
+    }
+#pragma unroll
+    for (int q = 0; q < NCH; ++q) {
+      adam1(u[q].x, m[q].x, v[q].x, xi * dy[q].x, pd.lr, pd.bc1, pd.bc2);
+      adam1(u[q].y, m[q].y, v[q].y, xi * dy[q].y, pd.lr, pd.bc1, pd.bc2);
+      adam1(u[q].z, m[q].z, v[q].z, xi * dy[q].z, pd.lr, pd.bc1, pd.bc2);
+      adam1(u[q].w, m[q].w, v[q].w, xi * dy[q].w, pd.lr, pd.bc1, pd.bc2);
+      __stcs(U4 + lane + 32 * q, u[q]);
+      __stcs(M4 + lane + 32 * q, m[q]);
+      __stcs(V4 + lane + 32 * q, v[q]);
+    }
+  }
+}
+
+// Persistent form of the update, built to run beside the step's other kernels:
+// one CTA of 512 threads per SM, at most 80 registers a thread and no shared
+// memory, so the step's tensor-core GEMM CTAs still fit on every SM. The FDM
+// rows are cut into units of 32 lanes x NU float4 (NU = min(NCH, 2)); warp w of
+// CTA c owns units u = c * 16 + w, u + W, u + 2W, ... (W = 16 * grid) and
+// updates two units per iteration, so every lane has 6 NU independent
+// 16-byte loads in flight. Warps never synchronise.
+constexpr int kAdamWarps = 16;
+
+template <int NCH>
+__global__ void __maxnreg__(80) fdm_adam_persist_kernel(FdmSplitArgs a) {
+  constexpr int FP = 128 * NCH;
+  constexpr int NU = NCH < 2 ? NCH : 2;  // float4 per lane per unit
+  constexpr int UPR = NCH / NU;          // units per FDM row
+  pdl_wait();
+  pdl_launch();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const FdmPend pd = *a.pend;
+  const int units = a.b * FP * UPR;      // < 2^31: at most 65535 x 1024 x 4
+  const int W = gridDim.x * kAdamWarps;
+  for (int u0 = blockIdx.x * kAdamWarps + warp; u0 < units; u0 += 2 * W) {
+    const int un[2] = {u0, u0 + W};
+    bool act[2];
+    float xi[2];
+    size_t base[2];
+    int dyo[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int g = un[h] / UPR;  // global FDM row: stream g / F', row g % F'
+      const int part = un[h] % UPR;
+      const int s = g / FP;
+      act[h] = un[h] < units && fdm_split_active(a, s, pd.i);
+      xi[h] = act[h] ? a.xp_pend[g] : 0.f;
+      base[h] = (size_t)g * FP + (size_t)part * 128 * NU;
+      dyo[h] = s * FP + part * 128 * NU;
+    }
+    float4 u[2][NU], m[2][NU], v[2][NU];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (act[h]) {
+#pragma unroll
+        for (int q = 0; q < NU; ++q) {
+          u[h][q] = __ldcs(reinterpret_cast<const float4*>(a.U + base[h]) + lane + 32 * q);
+          m[h][q] = __ldcs(reinterpret_cast<const float4*>(a.Um + base[h]) + lane + 32 * q);
+          v[h][q] = __ldcs(reinterpret_cast<const float4*>(a.Uv + base[h]) + lane + 32 * q);
+        }
+      }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (act[h]) {
+#pragma unroll
+        for (int q = 0; q < NU; ++q) {
+          const float4 dy = reinterpret_cast<const float4*>(a.dy_pend + dyo[h])[lane + 32 * q];
+          adam1(u[h][q].x, m[h][q].x, v[h][q].x, xi[h] * dy.x, pd.lr, pd.bc1, pd.bc2);
+          adam1(u[h][q].y, m[h][q].y, v[h][q].y, xi[h] * dy.y, pd.lr, pd.bc1, pd.bc2);
+          adam1(u[h][q].z, m[h][q].z, v[h][q].z, xi[h] * dy.z, pd.lr, pd.bc1, pd.bc2);
+          adam1(u[h][q].w, m[h][q].w, v[h][q].w, xi[h] * dy.w, pd.lr, pd.bc1, pd.bc2);
+          __stcs(reinterpret_cast<float4*>(a.U + base[h]) + lane + 32 * q, u[h][q]);
+          __stcs(reinterpret_cast<float4*>(a.Um + base[h]) + lane + 32 * q, m[h][q]);
+          __stcs(reinterpret_cast<float4*>(a.Uv + base[h]) + lane + 32 * q, v[h][q]);
+        }
+      }
+  }
+}
+
 // Generic fallback for F' not a multiple of 128: one element per lane step.
 __global__ void __launch_bounds__(256) fdm_bwd_generic_kernel(FdmBwdArgs a) {
   pdl_wait();
@@ -603,6 +765,111 @@ cudaError_t launch_fdm_bwd(const FdmBwdArgs& a, cudaStream_t st) {
     default: e = launch_k(fdm_bwd_generic_kernel, dim3(grid), dim3(256), 0, st, a); break;
   }
   return e;
+}
+
+__global__ void __launch_bounds__(256) fdm_dx_generic_kernel(FdmSplitArgs a) {
+  pdl_wait();
+  pdl_launch();
+  const int s = blockIdx.y;
+  const int Fp = a.Fp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const StepCtl c = *a.ctl;
+  if (blockIdx.x == 0 && s == 0 && threadIdx.x == 0) *a.pend = FdmPend{c.i, c.lr, c.bc1, c.bc2};
+  const bool act = fdm_split_active(a, s, c.i);
+  if (blockIdx.x == 0 && act)
+    for (int j = threadIdx.x; j < Fp; j += blockDim.x) {
+      a.xp_pend[(size_t)s * Fp + j] = a.Xp[(size_t)s * Fp + j];
+      a.dy_pend[(size_t)s * Fp + j] = a.dY[(size_t)s * Fp + j];
+    }
+  FdmBwdArgs o{};
+  o.dXp = a.dXp;
+  o.dXpb = a.dXpb;
+  o.dXpbT = a.dXpbT;
+  o.ldT = a.ldT;
+  o.Fp = Fp;
+  const int row0 = blockIdx.x * kFdmRowsPerCta;
+  for (int r = warp; r < kFdmRowsPerCta; r += 8) {
+    const int i = row0 + r;
+    if (i >= Fp) break;
+    float dot = 0.f;
+    if (act)
+      for (int j = lane; j < Fp; j += 32) dot += a.U[((size_t)s * Fp + i) * Fp + j] * a.dY[(size_t)s * Fp + j];
+    dot = warp_sum(dot);
+    if (lane == 0) store_dxp(o, s, i, act ? dot : 0.f);
+  }
+}
+
+__global__ void __launch_bounds__(256) fdm_adam_generic_kernel(FdmSplitArgs a) {
+  pdl_wait();
+  pdl_launch();
+  const int s = blockIdx.y;
+  const int Fp = a.Fp;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const FdmPend pd = *a.pend;
+  if (!fdm_split_active(a, s, pd.i)) return;
+  const int row0 = blockIdx.x * kFdmRowsPerCta;
+  for (int r = warp; r < kFdmRowsPerCta; r += 8) {
+    const int i = row0 + r;
+    if (i >= Fp) break;
+    const size_t ro = ((size_t)s * Fp + i) * Fp;
+    const float xi = a.xp_pend[(size_t)s * Fp + i];
+    for (int j = lane; j < Fp; j += 32) {
+      float u = a.U[ro + j], m = a.Um[ro + j], v = a.Uv[ro + j];
+      adam1(u, m, v, xi * a.dy_pend[(size_t)s * Fp + j], pd.lr, pd.bc1, pd.bc2);
+      a.U[ro + j] = u;
+      a.Um[ro + j] = m;
+      a.Uv[ro + j] = v;
+    }
+  }
+}
+
+cudaError_t launch_fdm_dx(const FdmSplitArgs& a, cudaStream_t st) {
+  dim3 grid(div_up(a.Fp, kFdmRowsPerCta), a.b);
+  switch (a.Fp) {
+    case 128: return launch_k(fdm_dx_kernel<1>, grid, dim3(256), 0, st, a);
+    case 256: return launch_k(fdm_dx_kernel<2>, grid, dim3(256), 0, st, a);
+    case 384: return launch_k(fdm_dx_kernel<3>, grid, dim3(256), 0, st, a);
+    case 512: return launch_k(fdm_dx_kernel<4>, grid, dim3(256), 0, st, a);
+    case 1024: return launch_k(fdm_dx_kernel<8>, grid, dim3(256), 0, st, a);
+    default: return launch_k(fdm_dx_generic_kernel, grid, dim3(256), 0, st, a);
+  }
+}
+
+template <int NCH>
+cudaError_t launch_adam_persist(const FdmSplitArgs& a, cudaStream_t st) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    // The CTA stays resident for the whole update: keep its SM configured for
+    // the largest shared-memory carveout, so GEMM CTAs still fit beside it.
+    e = cudaFuncSetAttribute(fdm_adam_persist_kernel<NCH>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  return launch_k(fdm_adam_persist_kernel<NCH>, dim3(sms), dim3(32 * kAdamWarps), 0, st, a);
+}
+
+cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st) {
+  switch (a.Fp) {
+    case 128: return launch_adam_persist<1>(a, st);
+    case 256: return launch_adam_persist<2>(a, st);
+    case 384: return launch_adam_persist<3>(a, st);
+    case 512: return launch_adam_persist<4>(a, st);
+    case 1024: return launch_adam_persist<8>(a, st);
+    default: break;
+  }
+  dim3 grid(div_up(a.Fp, kFdmRowsPerCta), a.b);
+  switch (a.Fp) {
+    case 128: return launch_k(fdm_adam_kernel<1>, grid, dim3(256), 0, st, a);
+    case 256: return launch_k(fdm_adam_kernel<2>, grid, dim3(256), 0, st, a);
+    case 384: return launch_k(fdm_adam_kernel<3>, grid, dim3(256), 0, st, a);
+    case 512: return launch_k(fdm_adam_kernel<4>, grid, dim3(256), 0, st, a);
+    case 1024: return launch_k(fdm_adam_kernel<8>, grid, dim3(256), 0, st, a);
+    default: return launch_k(fdm_adam_generic_kernel, grid, dim3(256), 0, st, a);
+  }
 }
 
 // ============================================================================================

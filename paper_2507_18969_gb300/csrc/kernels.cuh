@@ -93,6 +93,40 @@ struct FdmBwdArgs {
   int ldT;
 };
 cudaError_t launch_fdm_bwd(const FdmBwdArgs& a, cudaStream_t st);
+
+// The FDM adjoint split in two, so that the update leaves the critical path:
+//   fdm_dx    dx'_s = U_s dy_s with the pre-update U (the only part the rest of
+//             the adjoint waits for); also saves x'_s, dy_s and the step's Adam
+//             scalars in a pending record;
+//   fdm_adam  the Adam update of U, m, v from the pending record, on a side
+//             stream while the rest of the step (and the next step's layers up
+//             to Eq. 14) run; it must finish before the next FDM forward.
+// Together they compute exactly what fdm_bwd computes (same operations, same
+// order) at the cost of one more read of U.
+struct FdmPend {
+  int i;
+  float lr, bc1, bc2;
+};
+struct FdmSplitArgs {
+  const float* Xp;
+  const float* dY;
+  float* U;
+  float* Um;
+  float* Uv;
+  float* dXp;
+  __nv_bfloat16* dXpb;
+  __nv_bfloat16* dXpbT;
+  int ldT;
+  float* xp_pend;   // b x F' copy of x'
+  float* dy_pend;   // b x F' copy of dy
+  FdmPend* pend;
+  const StepCtl* ctl;
+  Split sp;
+  const uint8_t* active;
+  int b, Fp;
+};
+cudaError_t launch_fdm_dx(const FdmSplitArgs& a, cudaStream_t st);
+cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st);
 // dE[c][d] = sum over positions with ctx == c of dX[s][k*D + d], fixed order.
 // `part` is scratch of embed_bwd_chunks(b, K) * 256 * D floats.
 // With sum = false only the chunk partials are written and dE is left to Adam

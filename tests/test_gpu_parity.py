@@ -200,8 +200,16 @@ def test_gradient_against_central_differences():
     assert _rel(g[idx][big], fd[big]) <= 1e-3
 
 
-def test_adam_kernel_matches_closed_form_update():
-    c, o = cfgs(**SMALL)
+@pytest.mark.parametrize("prec,flags", [(edpc.EDPC_FP32, 0), (edpc.EDPC_BF16, 0), (edpc.EDPC_FP8E4M3, 0),
+                                        (edpc.EDPC_BF16, edpc.EDPC_FLAG_OVERLAP_FDM)],
+                         ids=["fp32", "bf16", "fp8", "bf16-overlap"])
+@pytest.mark.parametrize("dims", [SMALL, dict(SMALL, latent=128), dict(SMALL, latent=256, hidden=64)],
+                         ids=["latent72", "latent128", "latent256"])
+def test_adam_kernel_matches_closed_form_update(prec, flags, dims):
+    """One Adam step of every parameter, the FDMs included (with the overlap flag
+    the FDM update is the separate persistent kernel on its own stream), against
+    the closed form applied to the gradient the library reports at the same state."""
+    c, o = cfgs(precision=prec, flags=flags, **dims)
     b = 5
     m = edpc.Model(c, b)
     rng = np.random.default_rng(4)
