@@ -400,13 +400,15 @@ int edpc_model_train_step(edpc_model* m, const uint8_t* ctx, const uint8_t* targ
 
 /*
  * GEMM N tiles of a BF16 model (no effect in FP32). Each tcgen05 GEMM site
- * has a code: 0 = chosen from the problem size, 1/2/4 = N tile of 32/64/128.
+ * has a code: 0 = chosen from the problem size, 1/2/4/8 = N tile of
+ * 32/64/128/256 (for the fused branch GEMM of Eqs. 10-12: 32 * code hidden
+ * units of each branch per tile, at most 256 columns in all).
  * The codes fix how each output tile is accumulated, so a decoder must use
  * the encoder's (containers record them when tuned). There is no such
  * choice in the paper; it is a GPU implementation parameter.
  *   edpc_model_set_tiles   sets codes[0..n) (the rest 0). Errors: EARCH for
- *                          a code outside {0, 1, 2, 4}.
- *   edpc_model_tune_tiles  times N = 32, 64 and 128 at every site on the
+ *                          a code the site does not accept.
+ *   edpc_model_tune_tiles  times every accepted code at every site on the
  *                          model's buffers (before a step: it overwrites
  *                          activations and gradients), keeps the fastest, and
  *                          copies up to cap codes to `codes` (host, may be
@@ -414,6 +416,18 @@ int edpc_model_train_step(edpc_model* m, const uint8_t* ctx, const uint8_t* targ
  */
 int edpc_model_set_tiles(edpc_model* m, const uint8_t* codes, uint32_t n);
 int edpc_model_tune_tiles(edpc_model* m, uint8_t* codes, uint32_t cap, uint32_t* n);
+
+/*
+ * Measurement of the model's Linear layers (Eqs. 10, 13, 14, 16, the head and
+ * their adjoints; the paper reports no per-layer timing). Each tcgen05 GEMM
+ * site of a BF16 or FP8 model is launched alone: one warm-up launch, then
+ * `reps` launches between two CUDA events on the default stream. ms[i] (host)
+ * receives the mean milliseconds per launch of site i and flop[i] its
+ * 2*M*N*K; unused sites get 0. Writes min(cap, site count) entries and that
+ * count to *n. Like edpc_model_tune_tiles it overwrites activations and
+ * gradients (call it between steps). Errors: EINVAL (NULL, FP32 model), ECUDA.
+ */
+int edpc_model_time_gemms(edpc_model* m, uint32_t reps, double* ms, double* flop, uint32_t cap, uint32_t* n);
 
 #ifdef __cplusplus
 }

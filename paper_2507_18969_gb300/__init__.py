@@ -302,7 +302,8 @@ class Model:
         return g, gu
 
     def set_tiles(self, codes) -> None:
-        """GEMM N-tile codes per site (0 heuristic, 1/2/4 = N 32/64/128); BF16 only."""
+        """GEMM tile codes per site: 0 heuristic, w = 1/2/4/8 for an N tile of 32*w (capped
+        per site), w + 16 for the persistent kernel; BF16 and FP8 only."""
         a = np.ascontiguousarray(codes, dtype=np.uint8)
         check(load().edpc_model_set_tiles(self._h, _ptr(a), a.size), "edpc_model_set_tiles")
 
@@ -312,6 +313,15 @@ class Model:
         codes = np.zeros(512, np.uint8)
         check(load().edpc_model_tune_tiles(self._h, _ptr(codes), codes.size, C.byref(n)), "edpc_model_tune_tiles")
         return codes[:n.value].copy()
+
+    def time_gemms(self, reps: int = 8):
+        """Per tcgen05 GEMM site: (mean ms per launch, FLOP per launch); unused sites are 0."""
+        n = C.c_uint32()
+        ms = np.zeros(512, np.float64)
+        fl = np.zeros(512, np.float64)
+        check(load().edpc_model_time_gemms(self._h, reps, _ptr(ms), _ptr(fl), ms.size, C.byref(n)),
+              "edpc_model_time_gemms")
+        return ms[:n.value].copy(), fl[:n.value].copy()
 
     def train_step(self, ctx, targets, active):
         ctx = np.ascontiguousarray(ctx, dtype=np.uint8)

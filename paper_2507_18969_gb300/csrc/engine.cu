@@ -202,7 +202,24 @@ int Model::init(const edpc_cfg& cfg, int streams) {
       dy_pend = a.take<float>(bFp);
       pend = a.take<FdmPend>(1);
     }
-    emb_part = a.take<float>((size_t)embed_bwd_chunks(d.b, d.K) * 256 * d.D);
+    if (bf16) {
+      // column sums of one launch: at most 4 jobs of at most max(F, kH, 256) columns
+      cs_tiles = 4 * ((std::max(std::max(d.F, kH), 256) + 31) / 32);
+      cs_part = a.take<float>((size_t)cs_tiles * kColsumMaxChunks * 32);
+      cs_cnt = a.take<unsigned>((size_t)cs_tiles);
+      // split-K scratch: the largest splitk * M * N of any dW GEMM at any N tile
+      sk_ws_floats = 0;
+      const int dw[5][2] = {{d.F, d.H}, {kH, d.F}, {256, d.F}, {d.F, d.Fp}, {d.Fp, d.F}};
+      for (const auto& mn : dw)
+        for (int bn : {32, 64, 128, 256}) {
+          const int sk = tc_splitk(mn[0], mn[1], d.b, bn);
+          if (sk > 1) sk_ws_floats = std::max(sk_ws_floats, (size_t)sk * mn[0] * mn[1]);
+        }
+      if (sk_ws_floats) {
+        sk_ws = a.take<float>(sk_ws_floats);
+        sk_cnt = a.take<unsigned>(kSplitCounters);
+      }
+    }
     if (!bf16) {
       dXa = a.take<float>(bF);
       dXb = a.take<float>(bF);
@@ -490,8 +507,7 @@ int Model::backward_f32(const StepIO& io, cudaStream_t st) {
     EDPC_TRY(block_bwd(j, cur, nxt, st));
     std::swap(cur, nxt);
   }
-  emb_in_adam = io.update != 0;
-  EDPC_CUDA(launch_embed_bwd(ctx, cur, d.b, d.K, d.D, G + po.E, emb_part, st, !emb_in_adam));
+  EDPC_CUDA(launch_embed_bwd(ctx, cur, d.b, d.K, d.D, G + po.E, st));
   return EDPC_OK;
 }
 
@@ -583,7 +599,22 @@ int Model::build_tc_sites() {
   // bitstream); else 32 while 64-wide tiles would leave the GPU mostly idle
   // (small b), else 64.
   auto bn_heur = [&](int N) { return ((d.b + 127) / 128) * ((N + 63) / 64) < 2 * 152 ? 32 : 64; };
-  auto bn_site = [&](int id, int N) { return tile_code[id] ? 32 * (int)tile_code[id] : bn_heur(N); };
+  auto bn_site = [&](int id, int N) { return (tile_code[id] & 15) ? 32 * (tile_code[id] & 15) : bn_heur(N); };
+  // dW GEMMs (K = streams): split K when the output has too few tiles for the GPU
+  auto split_site = [&](int id) -> int {
+    TcGemm& g = tcp.site[id];
+    g.splitk = tc_splitk(g.M, g.N, g.K, g.bn);
+    if (g.splitk > 1) {
+      if (!sk_ws || (size_t)g.splitk * g.M * g.N > sk_ws_floats || tc_tiles(g.M, g.N, g.bn) > kSplitCounters)
+        return fail(EDPC_EINVAL, "split-K GEMM exceeds its scratch");
+      g.ws = sk_ws;
+      g.cnt = sk_cnt;
+    } else {
+      g.ws = nullptr;
+      g.cnt = nullptr;
+    }
+    return EDPC_OK;
+  };
   auto site = [&](int id, int M, int N, int K, const void* a, int a_rows, int a_cols, int a_ld, const void* b,
                   int b_rows, int b_cols, int b_ld, int bn, int box_b) -> int {
     TcGemm& g = tcp.site[id];
@@ -591,6 +622,9 @@ int Model::build_tc_sites() {
     g.N = N;
     g.K = K;
     g.bn = bn;
+    g.persistent = (tile_code[id] & 16) != 0;
+    g.mcast = g.persistent ? 1 << ((tile_code[id] >> 5) & 3) : 1;
+    box_b /= g.mcast;  // each CTA of a multicast cluster loads 1/mcast of the B tile
     g.box_b = box_b;
     g.err = &ctl->err;
     if (precision == EDPC_FP8E4M3) {
@@ -618,7 +652,10 @@ int Model::build_tc_sites() {
     // Eqs. 10-12: branch GEMM, B loaded as k sections of 32 hidden units
     {
       int id = blk_site(BR_FWD, j);
-      EDPC_TRY(site(id, b, kH, F, q.X0b, b, F, F, Pb + o.W, kH, F, F, 32 * d.k, 32));
+      // hidden units per branch section: 32 * code, halved until the k sections fit one MMA
+      int sw = (tile_code[id] & 15) ? 32 * (tile_code[id] & 15) : 32;
+      while (sw > 32 && (sw > 128 || sw * d.k > 256)) sw /= 2;
+      EDPC_TRY(site(id, b, kH, F, q.X0b, b, F, F, Pb + o.W, kH, F, F, sw * d.k, sw));
       TcGemm& g = tcp.site[id];
       g.mode = TC_BRANCH;
       g.H = H;
@@ -659,7 +696,8 @@ int Model::build_tc_sites() {
     // adjoint of Eq. 13 w.r.t. G, fused with the adjoint of Eqs. 11-12
     {
       int id = blk_site(OUT_DX, j);
-      EDPC_TRY(site(id, b, H, F, q.dOutb, b, F, F, PbT + o.Wo, H, F, F, 32, 32));
+      const int bn = (tile_code[id] & 15) ? std::min(128, 32 * (tile_code[id] & 15)) : 32;
+      EDPC_TRY(site(id, b, H, F, q.dOutb, b, F, F, PbT + o.Wo, H, F, F, bn, bn));
       TcGemm& g = tcp.site[id];
       g.mode = TC_BRANCH_BWD;
       g.H = H;
@@ -680,6 +718,7 @@ int Model::build_tc_sites() {
       TcGemm& g = tcp.site[id];
       g.C = G + o.Wo;
       g.ldc = H;
+      EDPC_TRY(split_site(id));
     }
     {  // dX0 = dA W
       int id = blk_site(BR_DX, j);
@@ -696,6 +735,7 @@ int Model::build_tc_sites() {
       TcGemm& g = tcp.site[id];
       g.C = G + o.W;
       g.ldc = F;
+      EDPC_TRY(split_site(id));
     }
   }
   {  // Eq. 14
@@ -715,7 +755,7 @@ int Model::build_tc_sites() {
     g.bias = P + po.b2;
   }
   {  // head
-    const int bh = tile_code[kSiteHeadFwd] ? 32 * (int)tile_code[kSiteHeadFwd] : 64;
+    const int bh = (tile_code[kSiteHeadFwd] & 15) ? 32 * (tile_code[kSiteHeadFwd] & 15) : 64;
     EDPC_TRY(site(kSiteHeadFwd, b, 256, F, Shead_b, b, F, F, Pb + po.Wh, 256, F, F, bh, bh));
     TcGemm& g = tcp.site[kSiteHeadFwd];
     g.C = z;
@@ -740,6 +780,7 @@ int Model::build_tc_sites() {
     TcGemm& g = tcp.site[kSiteHeadDw];
     g.C = G + po.Wh;
     g.ldc = F;
+    EDPC_TRY(split_site(kSiteHeadDw));
   }
   {  // LTE up adjoint: dY = dX W2
     int bn = bn_site(kSiteLteUpDx, Fp);
@@ -754,6 +795,7 @@ int Model::build_tc_sites() {
     TcGemm& g = tcp.site[kSiteLteUpDw];
     g.C = G + po.W2;
     g.ldc = Fp;
+    EDPC_TRY(split_site(kSiteLteUpDw));
   }
   {  // LTE down adjoint: dX = dX' W1 -> gradient of the last Local block's output
     int bn = bn_site(kSiteLteDownDx, F);
@@ -777,6 +819,7 @@ int Model::build_tc_sites() {
     TcGemm& g = tcp.site[kSiteLteDownDw];
     g.C = G + po.W1;
     g.ldc = F;
+    EDPC_TRY(split_site(kSiteLteDownDw));
   }
   tcp.ready = true;
   return EDPC_OK;
@@ -784,22 +827,38 @@ int Model::build_tc_sites() {
 
 void Model::tunable_sites(std::vector<int>* ids) const {
   ids->clear();
-  for (int kind : {OUT_FWD, OUT_DW, BR_DX, BR_DW})
+  for (int kind : {BR_FWD, OUT_FWD, OUT_DX, OUT_DW, BR_DX, BR_DW})
     for (int j = 0; j < d.n; ++j) ids->push_back(blk_site(kind, j));
   for (int id = kSiteLteDownFwd; id <= kSiteLteDownDx; ++id) ids->push_back(id);
+}
+
+// Tile codes: 0 (size heuristic), or w + v with w in {1, 2, 4, 8} and v in
+// {0, 16, 48, 80}. The N tile (for the fused branch GEMM: the section of
+// hidden units per branch) is 32 * w, capped at the widest the site supports
+// (128 for the branch adjoint; k sections of at most 128 within 256 columns
+// for the branch GEMM). v selects the kernel: 0 one tile per CTA, 16
+// persistent, 48 / 80 persistent in clusters of 2 / 4 that multicast B (BF16
+// only). Every kernel gives the same results for the same tile.
+bool Model::tile_code_ok(int, uint8_t c) const {
+  if (c == 0) return true;
+  const int w = c & 15, v = c >> 4;
+  if (w != 1 && w != 2 && w != 4 && w != 8) return false;
+  if (v == 0 || v == 1) return true;
+  return (v == 3 || v == 5) && precision == EDPC_BF16;
 }
 
 int Model::set_tiles(const uint8_t* code, int n) {
   if (precision == EDPC_FP32) return EDPC_OK;
   for (int i = 0; i < TcPlan::kMaxSites; ++i) tile_code[i] = (code && i < n) ? code[i] : 0;
   for (int i = 0; i < TcPlan::kMaxSites; ++i)
-    if (tile_code[i] != 0 && tile_code[i] != 1 && tile_code[i] != 2 && tile_code[i] != 4)
+    if (!tile_code_ok(i, tile_code[i]))
       return fail(EDPC_EARCH, "unknown GEMM tile code " + std::to_string(tile_code[i]));
   return build_tc_plan();
 }
 
-// Autotuner for the GEMM N tiles: every TC_PLAIN site of the step is timed
-// with N tiles of 32, 64 and 128 (CUDA events, after a warm-up launch) on the
+// Autotuner for the GEMM N tiles: every tcgen05 site of the step (but the head
+// GEMM) is timed with each tile code it accepts (N tiles of 32 to 256; branch
+// sections of 32 to 128) with CUDA events, after a warm-up launch, on the
 // model's own buffers, and keeps the fastest. Runs before the first step: the
 // GEMMs only overwrite per-step outputs (activations, BF16 copies, gradients).
 int Model::tune_tiles(cudaStream_t st) {
@@ -814,9 +873,18 @@ int Model::tune_tiles(cudaStream_t st) {
   for (int id : ids) {
     float best = 1e30f;
     uint8_t best_code = 1;
-    for (uint8_t code : {(uint8_t)1, (uint8_t)2, (uint8_t)4}) {
+    int seen[16] = {}, nseen = 0;
+    static const uint8_t kCodes[] = {1, 2, 4, 8, 17, 18, 20, 24, 49, 50, 52, 56, 81, 82, 84, 88};
+    for (uint8_t code : kCodes) {
+      if (!tile_code_ok(id, code)) continue;
       tile_code[id] = code;
       if ((r = build_tc_plan()) != EDPC_OK) break;
+      // a capped code repeats a (tile, kernel) pair already timed
+      const int key = tcp.site[id].bn * 16 + (tcp.site[id].persistent ? 8 : 0) + tcp.site[id].mcast;
+      bool dup = false;
+      for (int q = 0; q < nseen; ++q) dup |= seen[q] == key;
+      if (dup) continue;
+      seen[nseen++] = key;
       NoPdl scope;
       cudaError_t e = launch_gemm_tc(tcp.site[id], st);
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -843,6 +911,39 @@ int Model::tune_tiles(cudaStream_t st) {
   return build_tc_plan();
 }
 
+int Model::time_sites(cudaStream_t st, int reps, double* ms, double* flop, int cap) {
+  if (precision == EDPC_FP32 || !tcp.ready) return fail(EDPC_EINVAL, "no tcgen05 GEMM sites (FP32 model)");
+  if (reps < 1) reps = 1;
+  cudaEvent_t e0, e1;
+  EDPC_CUDA(cudaEventCreate(&e0));
+  EDPC_CUDA(cudaEventCreate(&e1));
+  int r = EDPC_OK;
+  for (int id = 0; id < TcPlan::kMaxSites && id < cap; ++id) {
+    const TcGemm& g = tcp.site[id];
+    ms[id] = 0;
+    flop[id] = 0;
+    if (g.M <= 0 || g.N <= 0 || g.K <= 0) continue;
+    NoPdl scope;
+    // (FP8: the operands' e4m3 shadows are timed as they stand; values do not change the time)
+    cudaError_t e = launch_gemm_tc(g, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    for (int q = 0; q < reps && e == cudaSuccess; ++q) e = launch_gemm_tc(g, st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e != cudaSuccess) {
+      r = fail(EDPC_ECUDA, std::string("GEMM site timing: ") + cudaGetErrorString(e));
+      break;
+    }
+    ms[id] = t / reps;
+    flop[id] = 2.0 * g.M * g.N * g.K;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return r;
+}
+
 int Model::run_tc(int site, cudaStream_t st) {
   if (st == side) {
     NoPdl scope;
@@ -852,6 +953,18 @@ int Model::run_tc(int site, cudaStream_t st) {
     if (precision == EDPC_FP8E4M3) EDPC_TRY(quantize_site(site, st));
     EDPC_CUDA(launch_gemm_tc(tcp.site[site], st));
   }
+  return EDPC_OK;
+}
+
+int Model::colsums(ColsumJobs cj, cudaStream_t st) {
+  NoPdl scope;
+  cj.chunk_rows = colsum_chunk_rows(d.b);
+  if (cj.chunk_rows > 0) {
+    if (colsum_tiles(cj) > cs_tiles) return fail(EDPC_EINVAL, "column-sum launch exceeds its scratch");
+    cj.part = cs_part;
+    cj.cnt = cs_cnt;
+  }
+  EDPC_CUDA(launch_colsum_multi(cj, st));
   return EDPC_OK;
 }
 
@@ -909,7 +1022,7 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
     ColsumJobs cj{};
     cj.job[0] = {dz, nullptr, d.b, 256, 256, G + po.bh};
     cj.n = 1;
-    { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj, side)); }
+    EDPC_TRY(colsums(cj, side));
   }
   {
     NoPdl scope;  // the stream also waits on the transposes' event
@@ -925,7 +1038,7 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
       ColsumJobs cj{};
       cj.job[0] = {dLte, nullptr, d.b, d.F, d.F, G + po.b2};
       cj.n = 1;
-      { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj, side)); }
+      EDPC_TRY(colsums(cj, side));
       EDPC_TRY(run_tc(kSiteLteUpDx, st));
       EDPC_TRY(fdm_bwd_call(io, st));
       EDPC_TRY(fork_side(st));
@@ -933,7 +1046,7 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
       ColsumJobs cj2{};
       cj2.job[0] = {dXp, nullptr, d.b, d.Fp, d.Fp, G + po.b1};
       cj2.n = 1;
-      { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj2, side)); }
+      EDPC_TRY(colsums(cj2, side));
       EDPC_TRY(run_tc(kSiteLteDownDx, st));
     }
     EDPC_TRY(fork_side(st));  // dOut_j is ready
@@ -950,7 +1063,7 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
       cj.job[2] = {q.dX0, ba[j].xhat, d.b, d.F, d.F, G + o.ln_g};
       cj.job[3] = {q.dX0, nullptr, d.b, d.F, d.F, G + o.ln_b};
       cj.n = 4;
-      { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj, side)); }
+      EDPC_TRY(colsums(cj, side));
     }
     // LN adjoint (Eq. 9) + residual path: gradient of the block input
     float* out;
@@ -976,7 +1089,7 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
     ColsumJobs cj{};
     cj.job[0] = {dLte, nullptr, d.b, d.F, d.F, G + po.b2};
     cj.n = 1;
-    { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj, side)); }
+    EDPC_TRY(colsums(cj, side));
     EDPC_TRY(run_tc(kSiteLteUpDx, st));
     EDPC_TRY(fdm_bwd_call(io, st));
     EDPC_TRY(fork_side(st));
@@ -984,11 +1097,10 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
     ColsumJobs cj2{};
     cj2.job[0] = {dXp, nullptr, d.b, d.Fp, d.Fp, G + po.b1};
     cj2.n = 1;
-    { NoPdl scope; EDPC_CUDA(launch_colsum_multi(cj2, side)); }
+    EDPC_TRY(colsums(cj2, side));
     EDPC_TRY(run_tc(kSiteLteDownDx, st));  // writes dh0
   }
-  emb_in_adam = io.update != 0;
-  EDPC_CUDA(launch_embed_bwd(ctx, dh0, d.b, d.K, d.D, G + po.E, emb_part, st, !emb_in_adam));
+  EDPC_CUDA(launch_embed_bwd(ctx, dh0, d.b, d.K, d.D, G + po.E, st));
   // join the side stream
   EDPC_CUDA(cudaEventRecord(join_ev, side));
   EDPC_CUDA(cudaStreamWaitEvent(st, join_ev, 0));
@@ -1032,15 +1144,12 @@ int Model::backward(const StepIO& io, cudaStream_t st) {
 }
 
 int Model::adam(cudaStream_t st) {
-  EmbGrad eg{nullptr, 0, 0, 0};
-  if (emb_in_adam) eg = EmbGrad{emb_part, embed_bwd_chunks(d.b, d.K), po.E, (size_t)256 * d.D};
   if (precision != EDPC_FP32) {
     NoPdl scope;  // follows the join of the side stream
-    EDPC_CUDA(launch_adam_bf16(P, G, M, V, Pb, nparam, ctl, st, eg));
+    EDPC_CUDA(launch_adam_bf16(P, G, M, V, Pb, nparam, ctl, st));
   } else {
-    EDPC_CUDA(launch_adam(P, G, M, V, nparam, ctl, st, eg));
+    EDPC_CUDA(launch_adam(P, G, M, V, nparam, ctl, st));
   }
-  emb_in_adam = false;
   return EDPC_OK;
 }
 

@@ -51,7 +51,13 @@ class Model {
   float *Xp = nullptr, *Y = nullptr, *z = nullptr, *p = nullptr, *dz = nullptr;
   float *dXa = nullptr, *dXb = nullptr, *dX0 = nullptr, *dA = nullptr, *dG = nullptr;
   float *dY = nullptr, *dXp = nullptr;
-  float* emb_part = nullptr;              // embedding-adjoint partial sums
+  float* cs_part = nullptr;               // column-sum chunk partials (side stream)
+  unsigned* cs_cnt = nullptr;             // column-sum arrival counters, one per 32-column tile
+  int cs_tiles = 0;                       // tiles cs_part and cs_cnt are sized for
+  float* sk_ws = nullptr;                 // split-K partial tiles of the dW GEMMs (side stream)
+  unsigned* sk_cnt = nullptr;             // split-K arrival counters
+  size_t sk_ws_floats = 0;
+  static constexpr int kSplitCounters = 1024;
 
   // BF16 mode
   __nv_bfloat16* Pb = nullptr;   // row-major weight copies (flat layout of P)
@@ -81,7 +87,6 @@ class Model {
   float *xp_pend = nullptr, *dy_pend = nullptr;
   FdmPend* pend = nullptr;
   bool fdm_pending = false;                                // an update was launched and not yet waited for
-  bool emb_in_adam = false;                                // dE left to Adam this step
 
   // FDM kernel timing (optional): forward [0,1], adjoint dx' [2,3], update [4,5]
   cudaEvent_t ev_fdm[6] = {};
@@ -123,7 +128,7 @@ class Model {
   // change the accumulation layout, so a bitstream records the ones its
   // encoder used and the decoder sets the same.
   uint8_t tile_code[TcPlan::kMaxSites] = {};
-  int set_tiles(const uint8_t* code, int n);  // codes 0, 1, 2 or 4; rebuilds the plan
+  int set_tiles(const uint8_t* code, int n);  // codes 0, 1, 2, 4 or 8; rebuilds the plan
 
   // FP8 e4m3 mode: one e4m3 shadow per distinct BF16 GEMM operand, with a
   // per-tensor power-of-two scale computed every step (amax slot + inverse).
@@ -142,8 +147,13 @@ class Model {
   float* f8_inv = nullptr;
   std::vector<char> f8_done;
   int site_fa[TcPlan::kMaxSites] = {}, site_fb[TcPlan::kMaxSites] = {};
-  int tune_tiles(cudaStream_t st);            // times 32/64/128 at every TC_PLAIN site
+  int tune_tiles(cudaStream_t st);            // times the N tiles of every tcgen05 site
   void tunable_sites(std::vector<int>* ids) const;
+  bool tile_code_ok(int id, uint8_t code) const;
+  // CUDA-event time of each tcgen05 site launched alone (mean of `reps`
+  // launches after one warm-up; like tune_tiles it overwrites per-step outputs)
+  // and its FLOP count 2*M*N*K; sites the step does not use get 0.
+  int time_sites(cudaStream_t st, int reps, double* ms, double* flop, int cap);
 
  private:
   void* arena_ = nullptr;
@@ -169,6 +179,7 @@ class Model {
   bool f8_collect = false;
   int run_tc(int site, cudaStream_t st);
   int fork_side(cudaStream_t st);  // the side stream waits for the work issued so far on st
+  int colsums(ColsumJobs cj, cudaStream_t st);  // column sums with the model's chunk scratch
   int fdm_fwd_call(const StepIO& io, cudaStream_t st);
   int fdm_bwd_call(const StepIO& io, cudaStream_t st);
 };

@@ -27,8 +27,26 @@ struct TcGemm {
   CUtensorMap ta;  // A: box 128 bytes of K x 128 (M), 128-byte swizzle
   CUtensorMap tb;  // B: box 128 bytes of K x bn (N) (TC_BRANCH: x 32 per section)
   int M = 0, N = 0, K = 0;
-  int bn = 64;     // N tile: 32, 64 or 128 (TC_BRANCH: 32 * k); must equal tb's box rows
-  int box_b = 0;   // rows of tb's box, recorded by the plan (checked at launch)
+  int bn = 64;     // N tile: 32, 64, 128 or 256 (TC_BRANCH: k * section, section 32, 64 or 128)
+  int box_b = 0;   // rows of tb's box, recorded by the plan (checked at launch): bn, or
+                   // the section width in TC_BRANCH mode
+  // Split-K (TC_PLAIN with no bias, residual or BF16 outputs): grid.z = splitk
+  // CTAs per output tile each take a contiguous range of K blocks and write
+  // their FP32 partial tile to ws ([splitk][M][N]); the last CTA of a tile to
+  // arrive (counter cnt[tile], zero between launches) adds the partials in
+  // split order and writes C. Launches that share ws and cnt must not overlap.
+  int splitk = 1;
+  float* ws = nullptr;
+  unsigned* cnt = nullptr;
+  // Persistent kernel: one CTA per SM walks the output tiles, with two TMEM
+  // accumulators so that a tile's epilogue overlaps the next tile's MMAs.
+  // Same K order and epilogue arithmetic as the one-tile kernel, so the
+  // results are identical for the same bn.
+  bool persistent = false;
+  // Persistent kernel only: clusters of mcast (1, 2 or 4; BF16) CTAs along M
+  // share each B tile through TMA multicast; tb's box is then bn / mcast rows
+  // (TC_BRANCH: section / mcast). Same results as mcast = 1.
+  int mcast = 1;
   int mode = TC_PLAIN;
   int H = 0, k = 1;        // TC_BRANCH / TC_BRANCH_BWD: hidden width and branch count
   float* C = nullptr;
@@ -60,6 +78,16 @@ int make_tmap_bf16(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t co
 int make_tmap_u8(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
 
 cudaError_t launch_gemm_tc(const TcGemm& g, cudaStream_t st);
+// The persistent kernel (g.persistent), dispatched by launch_gemm_tc; its
+// multicast variants (g.mcast > 1).
+cudaError_t launch_gemm_tcp(const TcGemm& g, cudaStream_t st);
+cudaError_t launch_gemm_tcp_mc(const TcGemm& g, cudaStream_t st);
+
+// Split-K factor of a TC_PLAIN GEMM with an N tile of bn: enough CTAs to give
+// every SM about two, at least 8 K blocks (of 64) per CTA, at most 32 splits.
+int tc_splitk(int M, int N, int K, int bn);
+// Output tiles of a launch (the size of its counter array when split).
+inline int tc_tiles(int M, int N, int bn) { return ((M + 127) / 128) * ((N + bn - 1) / bn); }
 
 // One tcgen05 GEMM per call site of the step (maps are bound to fixed buffers).
 struct TcPlan {

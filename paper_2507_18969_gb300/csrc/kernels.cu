@@ -873,139 +873,83 @@ cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st) {
 }
 
 // ============================================================================================
-// Embedding backward: scatter-add of dh0 into E's rows, in a fixed order.
-// Stage 1: the b*K positions are cut into chunks of kEmbChunk (one CTA each).
-//   The chunk's positions are sorted by context byte with a stable counting
-//   sort (warp match + per-warp counts, so equal bytes keep position order);
-//   then thread (c, half) sums, in that order, the dh0 rows of byte c for its
-//   half of the D columns -> part[q][c][d]. Work per thread = occurrences of c.
-// Stage 2: dE[c][d] = sum over chunks q of part[q][c][d], in a fixed order.
+// Embedding backward: scatter-add of dh0 into E's rows, owner computes.
+// CTA c owns byte value c and writes dE[c][0..D) once. Thread t of 256 looks
+// at positions p = 4u + q with u = t, t + 256, ... (four context bytes per
+// 32-bit load, coalesced) and adds dh0[p][0..D) for each p with ctx[p] == c
+// in increasing p. The 256 thread sums are then added by a butterfly within
+// each warp (fixed shuffle order) and the 8 warp sums in warp order, so the
+// result is the same on every run. Position p = s*K + k has its D gradient
+// values at dX[p*D .. p*D + D).
 // ============================================================================================
-constexpr int kEmbChunk = 256;  // = threads of stage 1 (one position each)
-
-__global__ void __launch_bounds__(512) embed_bwd_part_kernel(const uint8_t* __restrict__ ctx,
-                                                             const float* __restrict__ dX, int P, int D,
-                                                             float* __restrict__ part) {
+template <int DM>
+__global__ void __launch_bounds__(256) embed_bwd_owner_kernel(const uint8_t* __restrict__ ctx,
+                                                              const float* __restrict__ dX, int P, int D,
+                                                              float* __restrict__ dE) {
   pdl_wait();
   pdl_launch();
-  extern __shared__ float sx[];                 // kEmbChunk x D rows of dh0
-  __shared__ int cnt_w[kEmbChunk / 32][256];    // per warp, per byte: occurrences
-  __shared__ int start[256];                    // first sorted slot of each byte
-  __shared__ short order[kEmbChunk];            // positions sorted by byte (stable)
-  const int q = blockIdx.x, tid = threadIdx.x;
-  const int p0 = q * kEmbChunk;
-  const int n = min(kEmbChunk, P - p0);
-  // position p = s*K + k has its D gradient values at dX[p*D .. p*D + D)
-  const float* src = dX + (size_t)p0 * D;
-  for (int i = tid; i < n * D; i += blockDim.x) sx[i] = src[i];
-  for (int i = tid; i < (kEmbChunk / 32) * 256; i += blockDim.x) (&cnt_w[0][0])[i] = 0;
-  __syncthreads();
-  const int w = tid >> 5, lane = tid & 31;
-  int key = -1, rank = 0;
-  if (tid < kEmbChunk) {
-    key = tid < n ? (int)ctx[p0 + tid] : 256 + lane;  // padding keys never match a byte
-    const unsigned grp = __match_any_sync(0xffffffffu, key);
-    rank = __popc(grp & ((1u << lane) - 1u));
-    if (key < 256 && rank == 0) cnt_w[w][key] = __popc(grp);
-  }
-  __syncthreads();
-  if (tid < 32) {  // exclusive scan over the 256 bytes of the chunk totals (8 per lane)
-    int v[8], run = 0;
+  __shared__ float wsum[8][DM];
+  const int c = blockIdx.x, t = threadIdx.x;
+  float acc[DM];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      int tot = 0;
-#pragma unroll
-      for (int ww = 0; ww < kEmbChunk / 32; ++ww) tot += cnt_w[ww][tid * 8 + u];
-      v[u] = run;
-      run += tot;
+  for (int d = 0; d < DM; ++d) acc[d] = 0.f;
+  const int nw = (P + 3) / 4;
+  const bool al4 = (reinterpret_cast<uintptr_t>(ctx) & 3) == 0;
+  for (int u = t; u < nw; u += 256) {
+    uint32_t w4;
+    const int p0 = 4 * u;
+    if (al4 && p0 + 4 <= P) {
+      w4 = *reinterpret_cast<const uint32_t*>(ctx + p0);
+    } else {
+      w4 = 0;
+      for (int q = 0; q < 4; ++q) w4 |= (uint32_t)(p0 + q < P ? ctx[p0 + q] : (uint8_t)(c ^ 1)) << (8 * q);
     }
-    int incl = run;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (tid >= o) incl += y;
+    for (int q = 0; q < 4; ++q) {
+      if (((w4 >> (8 * q)) & 0xffu) == (uint32_t)c) {
+        const float* row = dX + (size_t)(p0 + q) * D;
+#pragma unroll
+        for (int d = 0; d < DM; ++d)
+          if (d < D) acc[d] += row[d];
+      }
     }
-    const int excl = incl - run;
+  }
+  const int lane = t & 31, w = t >> 5;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) start[tid * 8 + u] = excl + v[u];
+  for (int d = 0; d < DM; ++d) {
+    float v = acc[d];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[w][d] = v;
   }
   __syncthreads();
-  if (tid < kEmbChunk && key < 256) {
-    int before = 0;  // occurrences of this byte in earlier warps
-    for (int ww = 0; ww < w; ++ww) before += cnt_w[ww][key];
-    order[start[key] + before + rank] = (short)tid;
+  if (t < D) {
+    float s = wsum[0][t];
+#pragma unroll
+    for (int ww = 1; ww < 8; ++ww) s += wsum[ww][t];
+    dE[(size_t)c * D + t] = s;
   }
-  __syncthreads();
-  const int c = tid >> 1, half = tid & 1;
-  int tot = 0;
-#pragma unroll
-  for (int ww = 0; ww < kEmbChunk / 32; ++ww) tot += cnt_w[ww][c];
-  const int Dh = (D + 1) / 2, d0 = half * Dh, d1 = min(D, d0 + Dh);
-  float acc[32];
-#pragma unroll
-  for (int t = 0; t < 32; ++t) acc[t] = 0.f;
-  const int j0 = start[c];
-  for (int j = 0; j < tot; ++j) {
-    const float* row = sx + (int)order[j0 + j] * D;
-#pragma unroll
-    for (int t = 0; t < 32; ++t)
-      if (d0 + t < d1) acc[t] += row[d0 + t];
-  }
-  float* out = part + ((size_t)q * 256 + c) * D;
-#pragma unroll
-  for (int t = 0; t < 32; ++t)
-    if (d0 + t < d1) out[d0 + t] = acc[t];
 }
 
-// Fixed-order sum of the chunk partials of one embedding-gradient element:
-// chunk q goes to accumulator q % 8, then the 8 are added pairwise.
-__device__ __forceinline__ float emb_grad_sum(const float* __restrict__ part, int nchunks, size_t stride, size_t e) {
-  float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  int q = 0;
-  for (; q + 8 <= nchunks; q += 8) {
-#pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] += part[(size_t)(q + u) * stride + e];
-  }
-  for (int u = 0; q < nchunks; ++q, ++u) a[u] += part[(size_t)q * stride + e];
-  return ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-}
-
-__global__ void embed_bwd_sum_kernel(const float* __restrict__ part, int nchunks, int D, float* __restrict__ dE) {
-  pdl_wait();
-  pdl_launch();
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 256 * D) return;
-  dE[e] = emb_grad_sum(part, nchunks, (size_t)256 * D, (size_t)e);
-}
-
-int embed_bwd_chunks(int b, int K) { return (b * K + kEmbChunk - 1) / kEmbChunk; }
-
-cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, float* part,
-                             cudaStream_t st, bool sum) {
-  if (D > 64) return cudaErrorInvalidValue;
-  const int P = b * K, nq = embed_bwd_chunks(b, K);
-  const size_t smem = (size_t)kEmbChunk * D * sizeof(float);  // <= 64 KB for D <= 64
-  if (smem > 48 * 1024) {
-    cudaError_t a = cudaFuncSetAttribute(embed_bwd_part_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (a != cudaSuccess) return a;
-  }
-  cudaError_t e = launch_k(embed_bwd_part_kernel, dim3(nq), dim3(512), smem, st, ctx, dX, P, D, part);
-  if (e != cudaSuccess || !sum) return e;
-  return launch_k(embed_bwd_sum_kernel, dim3(div_up(256 * D, 256)), dim3(256), 0, st, part, nq, D, dE);
+cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, cudaStream_t st) {
+  const int P = b * K;
+  if (D <= 16) return launch_k(embed_bwd_owner_kernel<16>, dim3(256), dim3(256), 0, st, ctx, dX, P, D, dE);
+  if (D <= 32) return launch_k(embed_bwd_owner_kernel<32>, dim3(256), dim3(256), 0, st, ctx, dX, P, D, dE);
+  if (D <= 64) return launch_k(embed_bwd_owner_kernel<64>, dim3(256), dim3(256), 0, st, ctx, dX, P, D, dE);
+  return cudaErrorInvalidValue;
 }
 
 // ============================================================================================
 // Adam on the shared parameters (Sec. 4.1: lr 1e-3; beta, eps as documented).
 // ============================================================================================
 __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
-                            float* __restrict__ V, size_t n, const StepCtl* __restrict__ ctl, EmbGrad eg) {
+                            float* __restrict__ V, size_t n, const StepCtl* __restrict__ ctl) {
   pdl_wait();
   pdl_launch();
   const StepCtl c = *ctl;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     float p = P[e], m = M[e], v = V[e];
-    const float gr = (eg.part && e >= eg.off && e < eg.off + eg.n) ? emb_grad_sum(eg.part, eg.nchunks, eg.n, e - eg.off)
-                                                                   : G[e];
+    const float gr = G[e];
     adam1(p, m, v, gr, c.lr, c.bc1, c.bc2);
     P[e] = p;
     M[e] = m;
@@ -1014,10 +958,10 @@ __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, 
 }
 
 cudaError_t launch_adam(float* P, const float* G, float* M, float* V, size_t n, const StepCtl* ctl,
-                        cudaStream_t st, EmbGrad eg) {
+                        cudaStream_t st) {
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
-  return launch_k(adam_kernel, dim3(grid), dim3(256), 0, st, P, G, M, V, n, ctl, eg);
+  return launch_k(adam_kernel, dim3(grid), dim3(256), 0, st, P, G, M, V, n, ctl);
 }
 
 // ============================================================================================
@@ -1625,13 +1569,18 @@ cudaError_t launch_ln_bwd_bf16(const float* dX0, const float* xhat, const float*
 
 // ============================================================================================
 // Batched column sums (bias and LN-affine gradients), fixed order: CTA = one
-// 32-column tile of one job; warp w sums rows w, w+16, ... with four
-// interleaved accumulators; warps are then added in order.
+// 32-column tile of one job and one chunk of rows; warp w sums the chunk's rows
+// w, w+16, ... with four interleaved accumulators; warps are then added in
+// order. With several chunks, the last CTA of a tile to arrive adds the chunk
+// partials in chunk order (a fence before the arrival counter makes the
+// partials visible to it).
 // ============================================================================================
 __global__ void __launch_bounds__(512) colsum_multi_kernel(ColsumJobs jobs) {
   pdl_wait();
   pdl_launch();
   __shared__ float part[16][33];
+  __shared__ int is_last;
+  const int tile = blockIdx.x;
   int t = blockIdx.x, j = 0;
   while (j < jobs.n - 1 && t >= (jobs.job[j].cols + 31) / 32) {
     t -= (jobs.job[j].cols + 31) / 32;
@@ -1640,42 +1589,87 @@ __global__ void __launch_bounds__(512) colsum_multi_kernel(ColsumJobs jobs) {
   const ColsumJob jb = jobs.job[j];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int c = t * 32 + lane;
+  const int nch = gridDim.y;
+  const int r_lo = (nch > 1) ? blockIdx.y * jobs.chunk_rows : 0;
+  const int r_hi = (nch > 1) ? min(jb.rows, r_lo + jobs.chunk_rows) : jb.rows;
   float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
   if (c < jb.cols) {
-    int r = w;
+    int r = r_lo + w;
     if (jb.Y) {
-      for (; r + 48 < jb.rows; r += 64) {
+      for (; r + 48 < r_hi; r += 64) {
         a0 += jb.X[(size_t)r * jb.ld + c] * jb.Y[(size_t)r * jb.ld + c];
         a1 += jb.X[(size_t)(r + 16) * jb.ld + c] * jb.Y[(size_t)(r + 16) * jb.ld + c];
         a2 += jb.X[(size_t)(r + 32) * jb.ld + c] * jb.Y[(size_t)(r + 32) * jb.ld + c];
         a3 += jb.X[(size_t)(r + 48) * jb.ld + c] * jb.Y[(size_t)(r + 48) * jb.ld + c];
       }
-      for (; r < jb.rows; r += 16) a0 += jb.X[(size_t)r * jb.ld + c] * jb.Y[(size_t)r * jb.ld + c];
+      for (; r < r_hi; r += 16) a0 += jb.X[(size_t)r * jb.ld + c] * jb.Y[(size_t)r * jb.ld + c];
     } else {
-      for (; r + 48 < jb.rows; r += 64) {
+      for (; r + 48 < r_hi; r += 64) {
         a0 += jb.X[(size_t)r * jb.ld + c];
         a1 += jb.X[(size_t)(r + 16) * jb.ld + c];
         a2 += jb.X[(size_t)(r + 32) * jb.ld + c];
         a3 += jb.X[(size_t)(r + 48) * jb.ld + c];
       }
-      for (; r < jb.rows; r += 16) a0 += jb.X[(size_t)r * jb.ld + c];
+      for (; r < r_hi; r += 16) a0 += jb.X[(size_t)r * jb.ld + c];
     }
   }
   part[w][lane] = (a0 + a1) + (a2 + a3);
   __syncthreads();
-  if (w == 0 && c < jb.cols) {
+  if (nch == 1) {
+    if (w == 0 && c < jb.cols) {
+      float s = part[0][lane];
+#pragma unroll
+      for (int i = 1; i < 16; ++i) s += part[i][lane];
+      jb.out[c] = s;
+    }
+    return;
+  }
+  if (w == 0) {
     float s = part[0][lane];
 #pragma unroll
     for (int i = 1; i < 16; ++i) s += part[i][lane];
-    jb.out[c] = s;
+    jobs.part[((size_t)tile * nch + blockIdx.y) * 32 + lane] = s;
+    __threadfence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) is_last = (atomicAdd(&jobs.cnt[tile], 1u) == (unsigned)(nch - 1));
+  __syncthreads();
+  if (is_last && w == 0) {
+    __threadfence();
+    const float* src = jobs.part + (size_t)tile * nch * 32 + lane;
+    float s = 0.f;
+    for (int q = 0; q < nch; ++q) s += __ldcg(src + (size_t)q * 32);
+    if (c < jb.cols) jb.out[c] = s;
+    if (lane == 0) jobs.cnt[tile] = 0u;
   }
 }
 
-cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st) {
+int colsum_tiles(const ColsumJobs& jobs) {
   int tiles = 0;
   for (int j = 0; j < jobs.n; ++j) tiles += (jobs.job[j].cols + 31) / 32;
+  return tiles;
+}
+
+int colsum_chunk_rows(int rows) {
+  if (rows <= 512) return 0;
+  int cr = (rows + kColsumMaxChunks - 1) / kColsumMaxChunks;
+  cr = (cr + 15) / 16 * 16;
+  return cr < 256 ? 256 : cr;
+}
+
+cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st) {
+  const int tiles = colsum_tiles(jobs);
   if (tiles == 0) return cudaSuccess;
-  return launch_k(colsum_multi_kernel, dim3(tiles), dim3(512), 0, st, jobs);
+  int rows = 0;
+  for (int j = 0; j < jobs.n; ++j) rows = max(rows, jobs.job[j].rows);
+  int nch = 1;
+  if (jobs.chunk_rows > 0 && jobs.part && jobs.cnt) {
+    for (int j = 0; j < jobs.n; ++j)
+      if (jobs.job[j].rows != rows) return cudaErrorInvalidValue;  // one chunking for every job
+    nch = (rows + jobs.chunk_rows - 1) / jobs.chunk_rows;
+    if (nch > kColsumMaxChunks) return cudaErrorInvalidValue;
+  }
+  return launch_k(colsum_multi_kernel, dim3(tiles, nch), dim3(512), 0, st, jobs);
 }
 
 // ============================================================================================
@@ -1684,14 +1678,13 @@ cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st) {
 // ============================================================================================
 __global__ void adam_bf16_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
                                  float* __restrict__ V, __nv_bfloat16* __restrict__ Pb, size_t n,
-                                 const StepCtl* __restrict__ ctl, EmbGrad eg) {
+                                 const StepCtl* __restrict__ ctl) {
   pdl_wait();
   pdl_launch();
   const StepCtl c = *ctl;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
     float p = P[e], m = M[e], v = V[e];
-    const float gr = (eg.part && e >= eg.off && e < eg.off + eg.n) ? emb_grad_sum(eg.part, eg.nchunks, eg.n, e - eg.off)
-                                                                   : G[e];
+    const float gr = G[e];
     adam1(p, m, v, gr, c.lr, c.bc1, c.bc2);
     P[e] = p;
     M[e] = m;
@@ -1701,10 +1694,10 @@ __global__ void adam_bf16_kernel(float* __restrict__ P, const float* __restrict_
 }
 
 cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
-                             const StepCtl* ctl, cudaStream_t st, EmbGrad eg) {
+                             const StepCtl* ctl, cudaStream_t st) {
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
-  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, G, M, V, Pb, n, ctl, eg);
+  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, G, M, V, Pb, n, ctl);
 }
 
 __global__ void transpose_tiles_kernel(const __nv_bfloat16* __restrict__ Pb, __nv_bfloat16* __restrict__ PbT,

@@ -127,23 +127,12 @@ struct FdmSplitArgs {
 };
 cudaError_t launch_fdm_dx(const FdmSplitArgs& a, cudaStream_t st);
 cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st);
-// dE[c][d] = sum over positions with ctx == c of dX[s][k*D + d], fixed order.
-// `part` is scratch of embed_bwd_chunks(b, K) * 256 * D floats.
-// With sum = false only the chunk partials are written and dE is left to Adam
-// (EmbGrad below).
-int embed_bwd_chunks(int b, int K);
-cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, float* part,
-                             cudaStream_t st, bool sum = true);
-// The embedding gradient as chunk partials for Adam to reduce on the fly:
-// elements [off, off + n) of the flat gradient come from part (nchunks x n).
-struct EmbGrad {
-  const float* part;  // null: every gradient element is read from G
-  int nchunks;
-  size_t off, n;
-};
+// dE[c][d] = sum over positions with ctx == c of dX[s][k*D + d], fixed order
+// (one CTA per byte value c); D <= 64.
+cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, cudaStream_t st);
 // Adam over the flat shared parameters; bf16 != nullptr also refreshes the BF16 copy.
 cudaError_t launch_adam(float* P, const float* G, float* M, float* V, size_t n, const StepCtl* ctl,
-                        cudaStream_t st, EmbGrad eg = EmbGrad{nullptr, 0, 0, 0});
+                        cudaStream_t st);
 // i += 1 and the derived per-step scalars.
 cudaError_t launch_step_advance(StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st);
 
@@ -199,14 +188,28 @@ struct ColsumJob {
   int rows, cols, ld;
   float* out;
 };
+// With chunk_rows > 0 the rows are cut into chunks of chunk_rows (one CTA per
+// 32-column tile and chunk); each CTA writes its partial sums to `part` and the
+// last CTA of a tile to arrive adds the chunks' partials in chunk order, so the
+// result does not depend on which CTA finishes last. `part` holds
+// colsum_tiles(jobs) * chunks * 32 floats and `cnt` one zero-initialised counter
+// per tile; the last CTA sets its counter back to zero. Launches that share
+// part and cnt must not overlap (they run on one stream).
 struct ColsumJobs {
   ColsumJob job[kMaxColsumJobs];
   int n;
+  float* part = nullptr;
+  unsigned* cnt = nullptr;
+  int chunk_rows = 0;
 };
+int colsum_tiles(const ColsumJobs& jobs);
+// Rows per chunk for a column sum over `rows` rows (0: one chunk).
+int colsum_chunk_rows(int rows);
+constexpr int kColsumMaxChunks = 64;
 cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st);
 // Adam that also writes the BF16 copy Pb of every updated parameter (same flat layout).
 cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
-                             const StepCtl* ctl, cudaStream_t st, EmbGrad eg = EmbGrad{nullptr, 0, 0, 0});
+                             const StepCtl* ctl, cudaStream_t st);
 // Transposed BF16 copies of several matrices in one launch: PbT[off + c*rows + r] = Pb[off + r*cols + c].
 struct TransposeTile {
   unsigned long long off;

@@ -7,9 +7,10 @@ here the GPU path is checked for:
     autotuned stream count, FP32 and BF16;
   * code length against the FP64 oracle on the same split (FP32, within
     0.5 % of the oracle's total, as for the single-input workload);
-  * GEMM tile codes: every N tile (32, 64, 128) at every site gives the
-    oracle's logits and gradients within the BF16 tolerance, the tuner
-    returns valid codes, and a container made with tuned tiles decodes.
+  * GEMM tile codes: every N tile (32 to 256) at every site, and the split-K
+    weight-gradient GEMMs, give the oracle's logits and gradients within the
+    BF16 tolerance, the tuner returns valid codes, and a container made with
+    tuned tiles decodes.
 """
 import numpy as np
 import pytest
@@ -96,10 +97,16 @@ def test_autotuned_file_set_roundtrip_bf16():
         assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("code", [1, 2, 4])
-def test_every_tile_code_matches_oracle(code):
-    dims = dict(context=8, embed_dim=16, latent=136, hidden=200, blocks=2, branches=3, lr=1e-3, seed=5)
-    b = 300
+@pytest.mark.parametrize("code,k,b", [(1, 3, 300), (2, 3, 300), (4, 3, 300), (8, 3, 300), (4, 2, 300), (8, 2, 300),
+                                      (8, 1, 300), (1, 2, 2100), (8, 2, 2100), (17, 3, 300), (24, 2, 300),
+                                      (18, 2, 2100), (24, 2, 2100), (49, 3, 300), (56, 2, 2100), (81, 3, 300),
+                                      (88, 2, 2100)])
+def test_every_tile_code_matches_oracle(code, k, b):
+    """Every N tile (32-256; branch sections 32-128) at every site, one-tile,
+    persistent (codes + 16) and multicast-cluster kernels (+ 48: 2 CTAs, + 80:
+    4 CTAs), and, with 2100 streams, the split-K weight-gradient GEMMs
+    (K = streams)."""
+    dims = dict(context=8, embed_dim=16, latent=136, hidden=200, blocks=2, branches=k, lr=1e-3, seed=5)
     c = edpc.make_cfg(precision=edpc.EDPC_BF16, **dims)
     m = edpc.Model(c, b)
     m.set_tiles(np.full(512, code, np.uint8)[:200])
@@ -120,10 +127,36 @@ def test_every_tile_code_matches_oracle(code):
     m.close()
 
 
+@pytest.mark.parametrize("w", [1, 2, 4, 8])
+def test_persistent_gemm_is_bit_identical(w):
+    """The persistent kernel (every CTA walks several tiles and alternates two
+    TMEM accumulators), alone and in clusters of 2 and 4 that multicast B,
+    gives bit-identical logits and gradients to the one-tile kernel (20000
+    streams: 157 M tiles, so the last cluster of 4 has a spare CTA, and the
+    weight-gradient GEMMs are split)."""
+    dims = dict(context=8, embed_dim=16, latent=16, hidden=64, blocks=2, branches=2, lr=1e-3, seed=9)
+    b = 20000
+    rng = np.random.default_rng(w)
+    ctx = rng.integers(0, 256, size=(b, 8)).astype(np.uint8)
+    tg = rng.integers(0, 256, size=b).astype(np.uint8)
+    out = []
+    for code in (w, w + 16, w + 48, w + 80):
+        m = edpc.Model(edpc.make_cfg(precision=edpc.EDPC_BF16, **dims), b)
+        m.set_tiles(np.full(200, code, np.uint8))
+        z, _ = m.forward(ctx)
+        g, gu = m.backward(ctx, tg, np.ones(b, np.uint8))
+        out.append((z, g, gu))
+        m.close()
+    for o in out[1:]:
+        for a, c in zip(out[0], o):
+            assert np.array_equal(a, c)
+
+
 def test_tuned_tiles_single_input_roundtrip():
     m = edpc.Model(edpc.make_cfg(precision=edpc.EDPC_BF16, **C0), 512)
     codes = m.tune_tiles()
-    assert set(np.unique(codes)) <= {0, 1, 2, 4} and np.any(codes)
+    ok = {0} | {w + v for w in (1, 2, 4, 8) for v in (0, 16, 48, 80)}
+    assert set(np.unique(codes)) <= ok and np.any(codes)
     m.close()
     x = synth.multimedia_mix(200000, 8)
     cfg = edpc.make_cfg(streams=64, precision=edpc.EDPC_BF16, flags=edpc.EDPC_FLAG_TUNE_TILES, **C0)

@@ -78,7 +78,7 @@ def test_fp8_is_closer_to_bf16_than_the_format_bound():
     assert 0 < _rel(z8, zb) <= 0.15
 
 
-@pytest.mark.parametrize("code", [1, 2, 4])
+@pytest.mark.parametrize("code", [1, 2, 4, 8, 17, 24])
 def test_fp8_tile_codes(code):
     dims = dict(context=8, embed_dim=16, latent=136, hidden=200, blocks=2, branches=2, lr=1e-3, seed=6)
     b = 200
