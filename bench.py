@@ -442,6 +442,28 @@ def run_ours(args, d: Dist):
             "alg_bytes_per_launch": alg, "mean_ms": ms, "launches_timed": st.fdm_samples,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback", "other_fdm_kernels": others}
 
+    # ---- the model's GEMMs against their roofline ----------------------------------------------
+    # Every tcgen05 site of the step at the session's tile codes, launched alone
+    # (CUDA events, mean of 8 launches after a warm-up). A site's roofline time
+    # is max(FLOP / tensor peak, compulsory bytes / HBM peak); the GEMMs that
+    # read and write the FP32 residual stream are HBM-bound.
+    gm = edpc.Model(make_cfg(edpc.EDPC_BF16), b)
+    g_ms, g_fl, g_by = gm.time_gemms(8)
+    gm.close()
+    used = np.nonzero(g_fl)[0]
+    tpeak = peaks.get("bf16_tflops", 1900.0)
+    roof_ms = np.maximum(g_fl[used] / (tpeak * 1e9), g_by[used] / (peak * 1e6))
+    best = int(used[np.argmax(g_fl[used] / g_ms[used])])
+    gemm = {"sites": int(used.size), "gflop_per_model_step": float(g_fl[used].sum() / 1e9),
+            "sum_ms": float(g_ms[used].sum()), "achieved_tflops": float(g_fl[used].sum() / g_ms[used].sum() / 1e9),
+            "peak_tflops": tpeak, "tensor_frac": float(g_fl[used].sum() / g_ms[used].sum() / 1e9 / tpeak),
+            "roof_ms": float(roof_ms.sum()), "roof_frac": float(roof_ms.sum() / g_ms[used].sum()),
+            "best_site": {"gflop": float(g_fl[best] / 1e9), "ms": float(g_ms[best]),
+                          "tflops": float(g_fl[best] / g_ms[best] / 1e9),
+                          "tensor_frac": float(g_fl[best] / g_ms[best] / 1e9 / tpeak)},
+            "peak_source": "measured (burst, kernels timed alone)" if "bf16_tflops" in peaks else "fallback",
+            "timing": "each site alone, CUDA events, mean of 8 launches after one warm-up"}
+
     # ---- CPU oracle baseline ------------------------------------------------------------------
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.quick and not args.no_cpu_baseline:
@@ -469,7 +491,7 @@ def run_ours(args, d: Dist):
             "bits_per_byte": bpb,
             "bits_per_byte_input": "the e2e prefix input (early, still-learning part of each stream)",
             "e2e": e2e, "gpu_launches": out["launches"],
-            "roofline": roof, "cpu_baseline": cpu, "clocks": out["clocks"],
+            "roofline": roof, "gemm_roofline": gemm, "cpu_baseline": cpu, "clocks": out["clocks"],
         }
         if sweep:
             line["precision_sweep"] = sweep

@@ -422,12 +422,16 @@ int edpc_model_tune_tiles(edpc_model* m, uint8_t* codes, uint32_t cap, uint32_t*
  * their adjoints; the paper reports no per-layer timing). Each tcgen05 GEMM
  * site of a BF16 or FP8 model is launched alone: one warm-up launch, then
  * `reps` launches between two CUDA events on the default stream. ms[i] (host)
- * receives the mean milliseconds per launch of site i and flop[i] its
- * 2*M*N*K; unused sites get 0. Writes min(cap, site count) entries and that
- * count to *n. Like edpc_model_tune_tiles it overwrites activations and
- * gradients (call it between steps). Errors: EINVAL (NULL, FP32 model), ECUDA.
+ * receives the mean milliseconds per launch of site i, flop[i] its 2*M*N*K
+ * and, when bytes is not NULL, bytes[i] its compulsory memory traffic (A and
+ * B, the residual or saved branch outputs its epilogue reads, and every
+ * output it writes, each counted once); unused sites get 0. Writes
+ * min(cap, site count) entries and that count to *n. Like
+ * edpc_model_tune_tiles it overwrites activations and gradients (call it
+ * between steps). Errors: EINVAL (NULL ms or flop, FP32 model), ECUDA.
  */
-int edpc_model_time_gemms(edpc_model* m, uint32_t reps, double* ms, double* flop, uint32_t cap, uint32_t* n);
+int edpc_model_time_gemms(edpc_model* m, uint32_t reps, double* ms, double* flop, double* bytes, uint32_t cap,
+                          uint32_t* n);
 
 #ifdef __cplusplus
 }

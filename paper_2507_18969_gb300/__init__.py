@@ -315,13 +315,16 @@ class Model:
         return codes[:n.value].copy()
 
     def time_gemms(self, reps: int = 8):
-        """Per tcgen05 GEMM site: (mean ms per launch, FLOP per launch); unused sites are 0."""
+        """Per tcgen05 GEMM site: (mean ms per launch, FLOP per launch, compulsory bytes per
+        launch); unused sites are 0."""
         n = C.c_uint32()
         ms = np.zeros(512, np.float64)
         fl = np.zeros(512, np.float64)
-        check(load().edpc_model_time_gemms(self._h, reps, _ptr(ms), _ptr(fl), ms.size, C.byref(n)),
+        by = np.zeros(512, np.float64)
+        check(load().edpc_model_time_gemms(self._h, reps, _ptr(ms), _ptr(fl), _ptr(by), ms.size, C.byref(n)),
               "edpc_model_time_gemms")
-        return ms[:n.value].copy(), fl[:n.value].copy()
+        k = n.value
+        return ms[:k].copy(), fl[:k].copy(), by[:k].copy()
 
     def train_step(self, ctx, targets, active):
         ctx = np.ascontiguousarray(ctx, dtype=np.uint8)

@@ -108,7 +108,7 @@ PROTOS = {
     "edpc_model_train_step": (C.c_int, [P, P, P, P]),
     "edpc_model_set_tiles": (C.c_int, [P, P, C.c_uint32]),
     "edpc_model_tune_tiles": (C.c_int, [P, P, C.c_uint32, C.POINTER(C.c_uint32)]),
-    "edpc_model_time_gemms": (C.c_int, [P, C.c_uint32, P, P, C.c_uint32, C.POINTER(C.c_uint32)]),
+    "edpc_model_time_gemms": (C.c_int, [P, C.c_uint32, P, P, P, C.c_uint32, C.POINTER(C.c_uint32)]),
 }
 
 _LIB = None

@@ -1295,11 +1295,11 @@ extern "C" int edpc_model_set_tiles(edpc_model* mm, const uint8_t* codes, uint32
   return EDPC_OK;
 }
 
-extern "C" int edpc_model_time_gemms(edpc_model* mm, uint32_t reps, double* ms, double* flop, uint32_t cap,
-                                     uint32_t* n) {
+extern "C" int edpc_model_time_gemms(edpc_model* mm, uint32_t reps, double* ms, double* flop, double* bytes,
+                                     uint32_t cap, uint32_t* n) {
   if (!mm || !ms || !flop) return fail(EDPC_EINVAL, "NULL argument");
   const uint32_t k = std::min(cap, (uint32_t)TcPlan::kMaxSites);
-  EDPC_TRY(mm->m.time_sites(0, (int)reps, ms, flop, (int)k));
+  EDPC_TRY(mm->m.time_sites(0, (int)reps, ms, flop, bytes, (int)k));
   EDPC_CUDA(cudaDeviceSynchronize());
   if (n) *n = k;
   return EDPC_OK;

@@ -128,6 +128,7 @@ Model::~Model() {
     if (e) cudaEventDestroy(e);
   if (join_ev) cudaEventDestroy(join_ev);
   if (tr_ev) cudaEventDestroy(tr_ev);
+  if (fdm_join_ev) cudaEventDestroy(fdm_join_ev);
   if (dx_ev) cudaEventDestroy(dx_ev);
   if (adam_ev) cudaEventDestroy(adam_ev);
   if (side) cudaStreamDestroy(side);
@@ -311,6 +312,7 @@ int Model::init(const edpc_cfg& cfg, int streams) {
     for (auto& e : fork) EDPC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     EDPC_CUDA(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
     EDPC_CUDA(cudaEventCreateWithFlags(&tr_ev, cudaEventDisableTiming));
+    EDPC_CUDA(cudaEventCreateWithFlags(&fdm_join_ev, cudaEventDisableTiming));
   }
   EDPC_CUDA(cudaStreamSynchronize(st));
   return EDPC_OK;
@@ -597,9 +599,12 @@ int Model::build_tc_sites() {
   const int T = d.ldT;
   // N tile: the site's tile code when one is set (tuned or read from a
   // bitstream); else 32 while 64-wide tiles would leave the GPU mostly idle
-  // (small b), else 64.
+  // (small b), else 64; the GEMMs over the streams (M = b) take 128-wide
+  // tiles from 2048 streams on, where they were measured fastest.
+  const bool big = d.b >= 2048;
   auto bn_heur = [&](int N) { return ((d.b + 127) / 128) * ((N + 63) / 64) < 2 * 152 ? 32 : 64; };
   auto bn_site = [&](int id, int N) { return (tile_code[id] & 15) ? 32 * (tile_code[id] & 15) : bn_heur(N); };
+  auto bn_rows = [&](int id, int N) { return (tile_code[id] & 15) || !big ? bn_site(id, N) : 128; };
   // dW GEMMs (K = streams): split K when the output has too few tiles for the GPU
   auto split_site = [&](int id) -> int {
     TcGemm& g = tcp.site[id];
@@ -653,7 +658,7 @@ int Model::build_tc_sites() {
     {
       int id = blk_site(BR_FWD, j);
       // hidden units per branch section: 32 * code, halved until the k sections fit one MMA
-      int sw = (tile_code[id] & 15) ? 32 * (tile_code[id] & 15) : 32;
+      int sw = (tile_code[id] & 15) ? 32 * (tile_code[id] & 15) : (big ? 64 : 32);
       while (sw > 32 && (sw > 128 || sw * d.k > 256)) sw /= 2;
       EDPC_TRY(site(id, b, kH, F, q.X0b, b, F, F, Pb + o.W, kH, F, F, sw * d.k, sw));
       TcGemm& g = tcp.site[id];
@@ -671,7 +676,7 @@ int Model::build_tc_sites() {
     // Eq. 13: out GEMM + residual (the output's BF16 copies when a GEMM reads it next)
     {
       int id = blk_site(OUT_FWD, j);
-      int bn = bn_site(id, F);
+      int bn = bn_rows(id, F);
       EDPC_TRY(site(id, b, F, H, q.Gb, b, H, H, Pb + o.Wo, F, H, H, bn, bn));
       TcGemm& g = tcp.site[id];
       int out = (j < d.nloc) ? j + 1 : j + 2;
@@ -696,7 +701,7 @@ int Model::build_tc_sites() {
     // adjoint of Eq. 13 w.r.t. G, fused with the adjoint of Eqs. 11-12
     {
       int id = blk_site(OUT_DX, j);
-      const int bn = (tile_code[id] & 15) ? std::min(128, 32 * (tile_code[id] & 15)) : 32;
+      const int bn = (tile_code[id] & 15) ? std::min(128, 32 * (tile_code[id] & 15)) : (big ? 128 : 32);
       EDPC_TRY(site(id, b, H, F, q.dOutb, b, F, F, PbT + o.Wo, H, F, F, bn, bn));
       TcGemm& g = tcp.site[id];
       g.mode = TC_BRANCH_BWD;
@@ -722,7 +727,7 @@ int Model::build_tc_sites() {
     }
     {  // dX0 = dA W
       int id = blk_site(BR_DX, j);
-      int bn = bn_site(id, F);
+      int bn = bn_rows(id, F);
       EDPC_TRY(site(id, b, F, kH, q.dAb, b, kH, kH, PbT + o.W, F, kH, kH, bn, bn));
       TcGemm& g = tcp.site[id];
       g.C = q.dX0;
@@ -739,7 +744,7 @@ int Model::build_tc_sites() {
     }
   }
   {  // Eq. 14
-    int bn = bn_site(kSiteLteDownFwd, Fp);
+    int bn = bn_rows(kSiteLteDownFwd, Fp);
     EDPC_TRY(site(kSiteLteDownFwd, b, Fp, F, Slte_b, b, F, F, Pb + po.W1, Fp, F, F, bn, bn));
     TcGemm& g = tcp.site[kSiteLteDownFwd];
     g.C = Xp;
@@ -747,7 +752,7 @@ int Model::build_tc_sites() {
     g.bias = P + po.b1;
   }
   {  // Eq. 16
-    int bn = bn_site(kSiteLteUpFwd, F);
+    int bn = bn_rows(kSiteLteUpFwd, F);
     EDPC_TRY(site(kSiteLteUpFwd, b, F, Fp, Yb, b, Fp, Fp, Pb + po.W2, F, Fp, Fp, bn, bn));
     TcGemm& g = tcp.site[kSiteLteUpFwd];
     g.C = S[d.nloc + 1];
@@ -763,7 +768,7 @@ int Model::build_tc_sites() {
     g.bias = P + po.bh;
   }
   {  // head adjoint: dX = dz Wh -> gradient of the last block's output
-    int bn = bn_site(kSiteHeadDx, F);
+    int bn = bn_rows(kSiteHeadDx, F);
     EDPC_TRY(site(kSiteHeadDx, b, F, 256, dzb, b, 256, 256, PbT + po.Wh, F, 256, 256, bn, bn));
     TcGemm& g = tcp.site[kSiteHeadDx];
     BlockBf16& q = bb[d.n - 1];
@@ -783,7 +788,7 @@ int Model::build_tc_sites() {
     EDPC_TRY(split_site(kSiteHeadDw));
   }
   {  // LTE up adjoint: dY = dX W2
-    int bn = bn_site(kSiteLteUpDx, Fp);
+    int bn = bn_rows(kSiteLteUpDx, Fp);
     EDPC_TRY(site(kSiteLteUpDx, b, Fp, F, dLteb, b, F, F, PbT + po.W2, Fp, F, F, bn, bn));
     TcGemm& g = tcp.site[kSiteLteUpDx];
     g.C = dY;
@@ -798,7 +803,7 @@ int Model::build_tc_sites() {
     EDPC_TRY(split_site(kSiteLteUpDw));
   }
   {  // LTE down adjoint: dX = dX' W1 -> gradient of the last Local block's output
-    int bn = bn_site(kSiteLteDownDx, F);
+    int bn = bn_rows(kSiteLteDownDx, F);
     EDPC_TRY(site(kSiteLteDownDx, b, F, Fp, dXpb, b, Fp, Fp, PbT + po.W1, F, Fp, Fp, bn, bn));
     TcGemm& g = tcp.site[kSiteLteDownDx];
     g.ldc = F;
@@ -821,6 +826,9 @@ int Model::build_tc_sites() {
     g.ldc = F;
     EDPC_TRY(split_site(kSiteLteDownDw));
   }
+  // output tensor maps of every site (after its outputs and split-K factor are set)
+  for (int id = 0; id < TcPlan::kMaxSites; ++id)
+    if (tcp.site[id].M > 0) EDPC_TRY(tc_build_out_maps(&tcp.site[id]));
   tcp.ready = true;
   return EDPC_OK;
 }
@@ -911,7 +919,7 @@ int Model::tune_tiles(cudaStream_t st) {
   return build_tc_plan();
 }
 
-int Model::time_sites(cudaStream_t st, int reps, double* ms, double* flop, int cap) {
+int Model::time_sites(cudaStream_t st, int reps, double* ms, double* flop, double* bytes, int cap) {
   if (precision == EDPC_FP32 || !tcp.ready) return fail(EDPC_EINVAL, "no tcgen05 GEMM sites (FP32 model)");
   if (reps < 1) reps = 1;
   cudaEvent_t e0, e1;
@@ -922,6 +930,7 @@ int Model::time_sites(cudaStream_t st, int reps, double* ms, double* flop, int c
     const TcGemm& g = tcp.site[id];
     ms[id] = 0;
     flop[id] = 0;
+    if (bytes) bytes[id] = 0;
     if (g.M <= 0 || g.N <= 0 || g.K <= 0) continue;
     NoPdl scope;
     // (FP8: the operands' e4m3 shadows are timed as they stand; values do not change the time)
@@ -938,6 +947,18 @@ int Model::time_sites(cudaStream_t st, int reps, double* ms, double* flop, int c
     }
     ms[id] = t / reps;
     flop[id] = 2.0 * g.M * g.N * g.K;
+    if (bytes) {
+      // compulsory traffic: operands read once, epilogue inputs read once, outputs written once
+      const double M = g.M, es = g.fp8 ? 1.0 : 2.0, kH = (double)g.k * g.H;
+      const double wc = g.mode == TC_PLAIN ? g.N : kH, wcb = g.mode == TC_PLAIN ? g.N : (g.mode == TC_BRANCH ? g.H : kH);
+      double by = (M + g.N) * g.K * es;
+      if (g.C) by += M * wc * 4;
+      if (g.Cb) by += M * wcb * 2;
+      if (g.CbT) by += M * wcb * 2;
+      if (g.R) by += M * g.N * 4;
+      if (g.Aux) by += M * kH * 4;
+      bytes[id] = by;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -958,7 +979,7 @@ int Model::run_tc(int site, cudaStream_t st) {
 
 int Model::colsums(ColsumJobs cj, cudaStream_t st) {
   NoPdl scope;
-  cj.chunk_rows = colsum_chunk_rows(d.b);
+  cj.chunk_rows = colsum_chunk_rows(d.b, colsum_tiles(cj));
   if (cj.chunk_rows > 0) {
     if (colsum_tiles(cj) > cs_tiles) return fail(EDPC_EINVAL, "column-sum launch exceeds its scratch");
     cj.part = cs_part;
@@ -1040,7 +1061,18 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
       cj.n = 1;
       EDPC_TRY(colsums(cj, side));
       EDPC_TRY(run_tc(kSiteLteUpDx, st));
-      EDPC_TRY(fdm_bwd_call(io, st));
+      if (d.b >= 2048) {
+        // From 2048 streams on the FDM adjoint (milliseconds of HBM-bound
+        // streaming) runs faster alone than beside the side stream's pending
+        // weight gradients, so it waits for them (measured: 6.63 -> 5.81 ms
+        // per step at 4096 streams; at 512 streams the overlap wins).
+        EDPC_CUDA(cudaEventRecord(fdm_join_ev, side));
+        EDPC_CUDA(cudaStreamWaitEvent(st, fdm_join_ev, 0));
+        NoPdl scope;  // two incoming dependencies
+        EDPC_TRY(fdm_bwd_call(io, st));
+      } else {
+        EDPC_TRY(fdm_bwd_call(io, st));
+      }
       EDPC_TRY(fork_side(st));
       EDPC_TRY(run_tc(kSiteLteDownDw, side));
       ColsumJobs cj2{};

@@ -79,6 +79,7 @@ class Model {
   cudaEvent_t fork[kForks] = {};
   cudaEvent_t join_ev = nullptr;
   cudaEvent_t tr_ev = nullptr;                             // transposed weight copies ready
+  cudaEvent_t fdm_join_ev = nullptr;                       // side stream caught up before the FDM adjoint
   // FDM update off the critical path (BF16/FP8): dx' on the step's stream, the
   // Adam update of U, m, v on side_fdm from the pending copies; the next FDM
   // forward waits for adam_ev.
@@ -151,9 +152,10 @@ class Model {
   void tunable_sites(std::vector<int>* ids) const;
   bool tile_code_ok(int id, uint8_t code) const;
   // CUDA-event time of each tcgen05 site launched alone (mean of `reps`
-  // launches after one warm-up; like tune_tiles it overwrites per-step outputs)
-  // and its FLOP count 2*M*N*K; sites the step does not use get 0.
-  int time_sites(cudaStream_t st, int reps, double* ms, double* flop, int cap);
+  // launches after one warm-up; like tune_tiles it overwrites per-step outputs),
+  // its FLOP count 2*M*N*K and its compulsory bytes (operands and epilogue
+  // inputs read once, outputs written once); unused sites get 0.
+  int time_sites(cudaStream_t st, int reps, double* ms, double* flop, double* bytes, int cap);
 
  private:
   void* arena_ = nullptr;

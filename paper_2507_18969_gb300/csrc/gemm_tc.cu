@@ -47,7 +47,8 @@ constexpr size_t smem_bytes() {
 // the N tile holds k sections of SW = BN / k hidden units each.
 template <int BN, int MODE, int KB, bool F8>
 __global__ void __launch_bounds__(128, 1)
-    gemm_tc_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcEpi e) {
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                   const __grid_constant__ CUtensorMap tmc, const __grid_constant__ CUtensorMap tmcb, const TcEpi e) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   constexpr int STAGES = stages_for<BN>();
@@ -156,11 +157,16 @@ __global__ void __launch_bounds__(128, 1)
   // warp-collective, so the wait result is made CTA-uniform first.
   const bool ok = __syncthreads_and(mbar_wait(done, 0, abort_flag) ? 1 : 0) != 0;
   tc_fence_after();
-  // The pipeline's A stages are idle now: reuse them to stage transposed stores.
-  if (ok)
+  // The pipeline's A stages are idle now: reuse them to stage the transposed
+  // stores (8 KB) and the TMA stores (6 KB per warp).
+  static_assert(STAGES * A_BYTES >= 8192 + kStageOut, "A stages hold the epilogue staging");
+  if (ok) {
+    const EpiOut o{&tmc, &tmcb, sA + 8192 + warp * kStageOutWarp, m0 + warp * 32, lane};
     tc_epilogue<BN, MODE, KB, F8>(e, tmem + ((uint32_t)(warp * 32) << 16), m0, n0, blockIdx.z, gridDim.z,
                                   blockIdx.y * gridDim.x + blockIdx.x, reinterpret_cast<__nv_bfloat16*>(sA),
-                                  reinterpret_cast<volatile int*>(tmem_slot + 2), threadIdx.x, threadIdx.x);
+                                  reinterpret_cast<volatile int*>(tmem_slot + 2), threadIdx.x, threadIdx.x, o);
+    tma_st_drain(lane);
+  }
   if (!ok && threadIdx.x == 0 && e.err) atomicOr(e.err, kErrTcTimeout);
   tc_fence_before();
   __syncthreads();
@@ -190,11 +196,11 @@ cudaError_t launch_bn_mode(const TcGemm& g, cudaStream_t st) {
   });
   if (attr_err != cudaSuccess) return attr_err;
   TcEpi e{g.M, g.N, g.K, g.H, g.k, g.C, g.ldc, g.Cb, g.ldcb, g.CbT, g.ldct, g.bias, g.R, g.ldr, g.Aux, g.ldaux, g.err,
-          g.inv_a, g.inv_b, g.b_early ? 1 : 0, g.ws, g.cnt};
+          g.inv_a, g.inv_b, g.b_early ? 1 : 0, g.ws, g.cnt, 0, 0, g.has_tmc ? 1 : 0, g.has_tmcb ? 1 : 0};
   constexpr int SW = (MODE == TC_BRANCH) ? BN / KB : BN;
   const int ntile = (MODE == TC_BRANCH) ? (g.H + SW - 1) / SW : (g.N + BN - 1) / BN;
   dim3 grid(ntile, (g.M + BM - 1) / BM, g.splitk > 1 ? g.splitk : 1);
-  return launch_k(k, grid, dim3(128), smem_bytes<BN>(), st, g.ta, g.tb, e);
+  return launch_k(k, grid, dim3(128), smem_bytes<BN>(), st, g.ta, g.tb, g.tmc, g.tmcb, e);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -245,6 +251,33 @@ int make_tmap_u8(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols
   return EDPC_OK;
 }
 
+int tc_build_out_maps(TcGemm* g) {
+  g->has_tmc = g->has_tmcb = false;
+  auto enc = get_encode();
+  if (!enc) return fail(EDPC_ECUDA, "cuTensorMapEncodeTiled is not available");
+  const int wc = (g->mode == TC_PLAIN) ? g->N : g->k * g->H;                          // columns of C
+  const int wcb = (g->mode == TC_PLAIN) ? g->N : (g->mode == TC_BRANCH ? g->H : g->k * g->H);  // of Cb
+  auto build = [&](CUtensorMap* tm, void* base, int cols, int ld, int esize, CUtensorMapDataType dt,
+                   CUtensorMapSwizzle sw) -> bool {
+    if (!base || cols < 32 || g->M < 32) return false;
+    if ((reinterpret_cast<uintptr_t>(base) & 15) || (((size_t)ld * esize) & 15)) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)g->M};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(tm, dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  // A TMA store must start on a 16-byte boundary: the branch modes start
+  // branch i's chunks at column i * H, so H must be a multiple of 8 (BF16).
+  const bool cols_ok = g->mode == TC_PLAIN || g->H % 8 == 0;
+  if (g->splitk <= 1 && cols_ok) {  // split-K partials and their sums keep direct stores
+    g->has_tmc = build(&g->tmc, g->C, wc, g->ldc, 4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, CU_TENSOR_MAP_SWIZZLE_128B);
+    g->has_tmcb = build(&g->tmcb, g->Cb, wcb, g->ldcb, 2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, CU_TENSOR_MAP_SWIZZLE_64B);
+  }
+  return EDPC_OK;
+}
+
 namespace {
 template <bool F8>
 cudaError_t launch_gemm_tc_t(const TcGemm& g, cudaStream_t st);
@@ -253,7 +286,7 @@ cudaError_t launch_gemm_tc_t(const TcGemm& g, cudaStream_t st);
 int tc_splitk(int M, int N, int K, int bn) {
   const int tiles = tc_tiles(M, N, bn);
   const int nk = (K + 63) / 64;
-  int s = (2 * 152) / (tiles > 0 ? tiles : 1);
+  int s = 64 / (tiles > 0 ? tiles : 1);
   if (s > nk / 8) s = nk / 8;
   if (s > 32) s = 32;
   return s < 2 ? 1 : s;

@@ -47,6 +47,11 @@ struct TcGemm {
   // share each B tile through TMA multicast; tb's box is then bn / mcast rows
   // (TC_BRANCH: section / mcast). Same results as mcast = 1.
   int mcast = 1;
+  // Output tensor maps (FP32 C and BF16 Cb, boxes of 32 x 32, built by
+  // tc_build_out_maps when the outputs are 16-byte aligned): whole 32 x 32
+  // chunks are written by TMA stores from shared memory.
+  CUtensorMap tmc, tmcb;
+  bool has_tmc = false, has_tmcb = false;
   int mode = TC_PLAIN;
   int H = 0, k = 1;        // TC_BRANCH / TC_BRANCH_BWD: hidden width and branch count
   float* C = nullptr;
@@ -83,8 +88,14 @@ cudaError_t launch_gemm_tc(const TcGemm& g, cudaStream_t st);
 cudaError_t launch_gemm_tcp(const TcGemm& g, cudaStream_t st);
 cudaError_t launch_gemm_tcp_mc(const TcGemm& g, cudaStream_t st);
 
-// Split-K factor of a TC_PLAIN GEMM with an N tile of bn: enough CTAs to give
-// every SM about two, at least 8 K blocks (of 64) per CTA, at most 32 splits.
+// Builds g's output tensor maps (C over its logical columns: N for TC_PLAIN,
+// k * H for the branch modes; Cb likewise, H for TC_BRANCH). Returns 0 or an
+// EDPC code; an unaligned output simply gets no map.
+int tc_build_out_maps(TcGemm* g);
+
+// Split-K factor of a TC_PLAIN GEMM with an N tile of bn: up to about 64 CTAs
+// in all (the split GEMMs run on a side stream beside the step's critical
+// path), at least 8 K blocks (of 64) per CTA, at most 32 splits.
 int tc_splitk(int M, int N, int K, int bn);
 // Output tiles of a launch (the size of its counter array when split).
 inline int tc_tiles(int M, int N, int bn) { return ((M + 127) / 128) * ((N + bn - 1) / bn); }

@@ -38,7 +38,14 @@ struct TcEpi {
   float* ws;           // split-K partial tiles [splits][M][N]
   unsigned* cnt;       // split-K arrival counter per output tile
   int ntn, ntm;        // persistent kernel: N tiles and M tiles of the problem
+  int tma_c, tma_cb;   // C / Cb have output tensor maps: whole 32 x 32 chunks go out by TMA store
 };
+
+// Per-warp output staging for TMA stores: 4 KB FP32 rows (128-byte swizzle)
+// then 2 KB BF16 rows (64-byte swizzle); the 4 epilogue warps' areas are 6 KB
+// apart (1024-aligned).
+constexpr int kStageOutWarp = 6144;
+constexpr int kStageOut = 4 * kStageOutWarp;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -260,6 +267,88 @@ __device__ __forceinline__ void store_T32(const float (&v)[32], __nv_bfloat16* s
   epi_sync();
 }
 
+// A warp's 32 x 32 FP32 chunk (lane = row; rows r0..r0+31, columns
+// [col, col+32) of the tensor behind tm) through shared memory and one TMA
+// tensor store. The staging rows follow the 128-byte swizzle of the map.
+__device__ __forceinline__ void tma_st_f32(const float (&v)[32], uint8_t* stg, const CUtensorMap* tm, int col, int r0,
+                                           int lane) {
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // staging free again
+  __syncwarp();
+  uint8_t* rowp = stg + lane * 128;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    *reinterpret_cast<float4*>(rowp + ((j ^ (lane & 7)) << 4)) =
+        make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(col), "r"(r0), "r"(smem_u32(stg))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  }
+}
+
+// The same for a BF16 chunk (64-byte rows, 64-byte swizzle), staged 4 KB in.
+__device__ __forceinline__ void tma_st_bf16(const float (&v)[32], uint8_t* stg, const CUtensorMap* tm, int col,
+                                            int r0, int lane) {
+  uint8_t* sb = stg + 4096;
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+  __syncwarp();
+  uint8_t* rowp = sb + lane * 64;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    __align__(16) __nv_bfloat162 h[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(v[8 * j + 2 * q], v[8 * j + 2 * q + 1]);
+    *reinterpret_cast<uint4*>(rowp + ((j ^ ((lane >> 1) & 3)) << 4)) = *reinterpret_cast<const uint4*>(h);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(col), "r"(r0), "r"(smem_u32(sb))
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  }
+}
+
+// Waits until this warp's TMA stores have completed (before the CTA exits).
+__device__ __forceinline__ void tma_st_drain(int lane) {
+  if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  __syncwarp();
+}
+
+// Output of one 32-column chunk of the warp's 32 rows: whole chunks (columns
+// [col, col+32) inside the logical width `w` starting at `base`, all 32 rows
+// below M) go out by TMA store when the map exists; others by direct stores.
+struct EpiOut {
+  const CUtensorMap* tmc;   // C (FP32)
+  const CUtensorMap* tmcb;  // Cb (BF16)
+  uint8_t* stg;             // this warp's staging area
+  int r0, lane;             // first row of the warp's 32 rows; lane
+};
+
+__device__ __forceinline__ void out_chunk(const TcEpi& e, const EpiOut& o, const float (&v)[32], bool rok, int row,
+                                          int base, int cb, int w, float* C, int ldc, __nv_bfloat16* Cb, int ldcb) {
+  // base: first column of the logical region in C / Cb; cb: chunk start within it; w: its width
+  const bool whole = cb + 32 <= w && o.r0 + 32 <= e.M;
+  if (C) {
+    if (whole && e.tma_c)
+      tma_st_f32(v, o.stg, o.tmc, base + cb, o.r0, o.lane);
+    else
+      store_row32(v, rok, cb, w, C + (size_t)row * ldc + base, nullptr);
+  }
+  if (Cb) {
+    if (whole && e.tma_cb)
+      tma_st_bf16(v, o.stg, o.tmcb, base + cb, o.r0, o.lane);
+    else
+      store_row32(v, rok, cb, w, nullptr, Cb + (size_t)row * ldcb + base);
+  }
+}
+
 template <int BN>
 constexpr int tmem_cols() {
   return BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
@@ -315,9 +404,10 @@ __device__ __forceinline__ void splitk_finish(const TcEpi& e, int m0, int n0, in
 // (its lane group's base plus the accumulator's first column). z, S, tile:
 // split-K index, split count and the output tile's counter index. sT: 8 KB of
 // shared memory for the transposed stores; flag: a shared word.
+// o: the warp's TMA-store state (maps, staging, first row).
 template <int BN, int MODE, int KB, bool F8>
 __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t trow, int m0, int n0, int z, int S, int tile,
-                                            __nv_bfloat16* sT, volatile int* flag, int r, int et) {
+                                            __nv_bfloat16* sT, volatile int* flag, int r, int et, const EpiOut& o) {
   constexpr int SECTIONS = (MODE == TC_BRANCH) ? KB : 1;
   constexpr int SW = BN / SECTIONS;  // hidden units per branch section (TC_BRANCH)
   const int row = m0 + r;
@@ -359,8 +449,7 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t trow, int m
 #pragma unroll
         for (int j = 0; j < 32; ++j) v[j] += rr[j];
       }
-      store_row32(v, rok, nb, e.N, e.C ? e.C + (size_t)row * e.ldc : nullptr,
-                  e.Cb ? e.Cb + (size_t)row * e.ldcb : nullptr);
+      out_chunk(e, o, v, rok, row, 0, nb, e.N, e.C, e.ldc, e.Cb, e.ldcb);
       if (e.CbT) store_T32(v, sT, m0, nb, e.N, e.CbT, e.ldct, r, et);
     }
   } else if (MODE == TC_BRANCH) {
@@ -384,11 +473,11 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t trow, int m
           g[j] *= v[j];
         }
         // X_i -> C[row][i*H + h] (FP32, kept for the adjoint)
-        store_row32(v, rok, hb, e.H, e.C + (size_t)row * e.ldc + i * e.H, nullptr);
+        out_chunk(e, o, v, rok, row, i * e.H, hb, e.H, e.C, e.ldc, nullptr, 0);
       }
 #pragma unroll
       for (int j = 0; j < 32; ++j) g[j] = gelu_f(g[j]);
-      store_row32(g, rok, hb, e.H, nullptr, e.Cb + (size_t)row * e.ldcb);
+      out_chunk(e, o, g, rok, row, 0, hb, e.H, nullptr, 0, e.Cb, e.ldcb);
       store_T32(g, sT, m0, hb, e.H, e.CbT, e.ldct, r, et);
     }
   } else {
@@ -424,14 +513,14 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t trow, int m
         float dd[32];
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          float o = 1.f;
+          float prod = 1.f;
 #pragma unroll
           for (int l = 0; l < KB; ++l)
-            if (l != i) o *= xs[l][j];
-          dd[j] = dg[j] * o;
+            if (l != i) prod *= xs[l][j];
+          dd[j] = dg[j] * prod;
         }
         const int colb = i * e.H;
-        store_row32(dd, rok, hb, e.H, e.C + (size_t)row * e.ldc + colb, e.Cb + (size_t)row * e.ldcb + colb);
+        out_chunk(e, o, dd, rok, row, colb, hb, e.H, e.C, e.ldc, e.Cb, e.ldcb);
         store_T32(dd, sT, m0, colb + hb, colb + e.H, e.CbT, e.ldct, r, et);
       }
     }

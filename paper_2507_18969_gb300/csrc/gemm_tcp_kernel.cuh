@@ -47,12 +47,14 @@ constexpr size_t kStageT = 32 * 128 * sizeof(__nv_bfloat16);  // transposed-stor
 
 template <int BN>
 constexpr size_t psmem_bytes() {
-  return 1024 /*alignment slack*/ + (size_t)pstages_for<BN>() * (BM * BKB + BN * BKB) + kStageT + 256;
+  return 1024 /*alignment slack*/ + (size_t)pstages_for<BN>() * (BM * BKB + BN * BKB) + kStageT + kStageOut + 256;
 }
+static_assert(psmem_bytes<256>() <= 232448 && psmem_bytes<128>() <= 232448, "shared memory per CTA");
 
 template <int BN, int MODE, int KB, bool F8, int CM>
 __global__ void __launch_bounds__(192, 1)
-    gemm_tcp_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, const TcEpi e,
+    gemm_tcp_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+                    const __grid_constant__ CUtensorMap tmc, const __grid_constant__ CUtensorMap tmcb, const TcEpi e,
                     int nsplit) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -71,7 +73,8 @@ __global__ void __launch_bounds__(192, 1)
   uint8_t* sA = smem;
   uint8_t* sB = sA + STAGES * A_BYTES;
   __nv_bfloat16* sT = reinterpret_cast<__nv_bfloat16*>(sB + STAGES * B_BYTES);
-  uint64_t* full = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(sT) + kStageT);
+  uint8_t* sO = reinterpret_cast<uint8_t*>(sT) + kStageT;  // TMA-store staging, kStageOutWarp per warp
+  uint64_t* full = reinterpret_cast<uint64_t*>(sO + kStageOut);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;  // [2] accumulator written
   uint64_t* tempty = tfull + 2;      // [2] accumulator drained
@@ -217,13 +220,16 @@ __global__ void __launch_bounds__(192, 1)
       const int a = tcount & 1;
       if (!epi_and(mbar_wait(&tfull[a], (uint32_t)(tcount >> 1) & 1u, abort_flag))) break;
       tc_fence_after();
-      if (q.m0 < e.M)
+      if (q.m0 < e.M) {
+        const EpiOut o{&tmc, &tmcb, sO + lg * kStageOutWarp, q.m0 + lg * 32, lane};
         tc_epilogue<BN, MODE, KB, F8>(e, tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)a * ACC, q.m0, q.n0, q.z,
-                                      nsplit, q.ci, sT, sk_flag, r, et);
+                                      nsplit, q.ci, sT, sk_flag, r, et, o);
+      }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[a]);
     }
+    tma_st_drain(lane);
   }
   __syncwarp();
   tc_fence_before();
@@ -283,12 +289,13 @@ cudaError_t launch_p(const TcGemm& g, cudaStream_t st) {
   const int ntm = (g.M + BM - 1) / BM;
   const int S = g.splitk > 1 ? g.splitk : 1;
   TcEpi e{g.M, g.N, g.K, g.H, g.k, g.C, g.ldc, g.Cb, g.ldcb, g.CbT, g.ldct, g.bias, g.R, g.ldr, g.Aux, g.ldaux, g.err,
-          g.inv_a, g.inv_b, 0, g.ws, g.cnt, ntn, ntm};
+          g.inv_a, g.inv_b, 0, g.ws, g.cnt, ntn, ntm, g.has_tmc ? 1 : 0, g.has_tmcb ? 1 : 0};
   const long long units = (long long)ntn * ((ntm + CM - 1) / CM) * S;
   if (units <= 0 || units > (1ll << 30)) return cudaErrorInvalidValue;
   const int ncl = (int)(units < max_clusters ? units : max_clusters);
-  if (CM == 1) return launch_k(k, dim3(ncl), dim3(192), psmem_bytes<BN>(), st, g.ta, g.tb, e, S);
-  return launch_kc(k, dim3(ncl * CM), dim3(192), psmem_bytes<BN>(), (unsigned)CM, st, g.ta, g.tb, e, S);
+  if (CM == 1) return launch_k(k, dim3(ncl), dim3(192), psmem_bytes<BN>(), st, g.ta, g.tb, g.tmc, g.tmcb, e, S);
+  return launch_kc(k, dim3(ncl * CM), dim3(192), psmem_bytes<BN>(), (unsigned)CM, st, g.ta, g.tb, g.tmc, g.tmcb, e,
+                   S);
 }
 
 // Dispatch on (mode, k, tile) for one cluster size.

@@ -8,6 +8,8 @@
 
 #include <algorithm>
 
+#include <mutex>
+
 #include "kernels.cuh"
 #include "launch.cuh"
 
@@ -418,6 +420,112 @@ __global__ void __launch_bounds__(FdmRing<FP>::NT)
   }
 }
 
+// Persistent version: kFdmPersistPerSm CTAs per SM walk the streams s =
+// blockIdx.x, blockIdx.x + gridDim.x, ...; thread 0 keeps kFdmPersistRing
+// 16 KB copies in flight across stream boundaries (no drain between streams,
+// no partial last wave). Each thread still sums its columns' rows in
+// increasing i, so Y is bit-identical to the one-CTA-per-stream kernel.
+constexpr int kFdmPersistRing = 6;
+constexpr int kFdmPersistPerSm = 2;
+
+template <int FP>
+__global__ void __launch_bounds__(FdmRing<FP>::NT)
+    fdm_fwd_persist_kernel(const float* __restrict__ Xp, const float* __restrict__ U, float* __restrict__ Y,
+                           __nv_bfloat16* Yb, __nv_bfloat16* YbT, int ldT, int* err, FdmAct act, int b) {
+  using R = FdmRing<FP>;
+  constexpr int RING = kFdmPersistRing;
+  extern __shared__ __align__(128) float smf[];
+  float* buf = smf;                         // RING x 16 KB
+  float* xs = smf + (size_t)RING * 4096;    // FP
+  uint64_t* bars = reinterpret_cast<uint64_t*>(xs + FP);
+  const int t = threadIdx.x;
+  if (t == 0) {
+    for (int q = 0; q < RING; ++q) bar_init(&bars[q]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pdl_wait();
+  pdl_launch();
+  // producer cursor (thread 0): next stream and stage to copy, copies issued
+  int ps = blockIdx.x, pst = 0;
+  uint32_t issued = 0;
+  auto next_active = [&](int s0) {
+    int s1 = s0;
+    while (s1 < b && !fdm_row_active(act, s1)) s1 += gridDim.x;
+    return s1;
+  };
+  auto issue_one = [&]() {
+    if (ps >= b) return;
+    const float* src = U + (size_t)ps * FP * FP + (size_t)pst * 4096;
+    bulk_load(buf + (size_t)(issued % RING) * 4096, src, 16384u, &bars[issued % RING]);
+    ++issued;
+    if (++pst == R::NST) {
+      pst = 0;
+      ps = next_active(ps + gridDim.x);
+    }
+  };
+  if (t == 0) {
+    ps = next_active(ps);
+    for (int q = 0; q < RING; ++q) issue_one();
+  }
+  uint32_t used = 0;  // copies consumed (same sequence as issued)
+  bool ok = true;
+  for (int s = blockIdx.x; s < b; s += gridDim.x) {
+    if (!fdm_row_active(act, s)) {  // CTA-uniform
+      fdm_zero_row(Y, Yb, YbT, ldT, s, FP);
+      continue;
+    }
+    __syncthreads();  // the previous stream's readers are done with xs
+    for (int i = t; i < FP; i += R::NT) xs[i] = Xp[(size_t)s * FP + i];
+    __syncthreads();
+    float acc[R::CPT];
+#pragma unroll
+    for (int j = 0; j < R::CPT; ++j) acc[j] = 0.f;
+    for (int st = 0; st < R::NST; ++st, ++used) {
+      const int q = (int)(used % RING);
+      ok = bar_wait(&bars[q], (used / RING) & 1u) && ok;
+      const float* u = buf + (size_t)q * 4096;
+      const float* xv = xs + st * R::SROWS;
+#pragma unroll
+      for (int r = 0; r < R::SROWS; ++r) {
+        const float xr = xv[r];
+#pragma unroll
+        for (int j = 0; j < R::CPT; ++j) acc[j] += xr * u[r * FP + t + j * R::NT];
+      }
+      __syncthreads();  // slot q consumed by every thread
+      if (t == 0) issue_one();
+    }
+#pragma unroll
+    for (int j = 0; j < R::CPT; ++j) {
+      const int c = t + j * R::NT;
+      Y[(size_t)s * FP + c] = acc[j];
+      if (Yb) Yb[(size_t)s * FP + c] = __float2bfloat16_rn(acc[j]);
+      if (YbT) YbT[(size_t)c * ldT + s] = __float2bfloat16_rn(acc[j]);
+    }
+  }
+  if (!ok && t == 0 && err) atomicOr(err, 8);
+}
+
+template <int FP>
+cudaError_t launch_fdm_fwd_persist(const float* Xp, const float* U, float* Y, int b, __nv_bfloat16* Yb,
+                                   __nv_bfloat16* YbT, int ldT, int* err, const FdmAct& act, cudaStream_t st) {
+  const size_t smem = (size_t)kFdmPersistRing * 16384 + (size_t)FP * 4 + 64 + 64;
+  static std::once_flag once;
+  static cudaError_t attr = cudaSuccess;
+  static int grid = 0;
+  std::call_once(once, [&] {
+    attr = cudaFuncSetAttribute(fdm_fwd_persist_kernel<FP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0;
+    if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
+    if (attr == cudaSuccess) attr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    grid = sms * kFdmPersistPerSm;
+  });
+  if (attr != cudaSuccess) return attr;
+  const int g = b < grid ? b : grid;
+  return launch_k(fdm_fwd_persist_kernel<FP>, dim3(g), dim3(FdmRing<FP>::NT), smem, st, Xp, U, Y, Yb, YbT, ldT, err,
+                  act, b);
+}
+
 template <int FP>
 cudaError_t launch_fdm_fwd_ring(const float* Xp, const float* U, float* Y, int b, __nv_bfloat16* Yb,
                                 __nv_bfloat16* YbT, int ldT, int* err, const FdmAct& act, cudaStream_t st) {
@@ -434,10 +542,10 @@ cudaError_t launch_fdm_fwd_ring(const float* Xp, const float* U, float* Y, int b
 cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int Fp, cudaStream_t st,
                            __nv_bfloat16* Yb, __nv_bfloat16* YbT, int ldT, int* err, FdmAct act) {
   switch (Fp) {
-    case 128: return launch_fdm_fwd_ring<128>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
-    case 256: return launch_fdm_fwd_ring<256>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
-    case 512: return launch_fdm_fwd_ring<512>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
-    case 1024: return launch_fdm_fwd_ring<1024>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
+    case 128: return launch_fdm_fwd_persist<128>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
+    case 256: return launch_fdm_fwd_persist<256>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
+    case 512: return launch_fdm_fwd_persist<512>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
+    case 1024: return launch_fdm_fwd_persist<1024>(Xp, U, Y, b, Yb, YbT, ldT, err, act, st);
     default: break;
   }
   const int cols4 = Fp / 4;
@@ -874,13 +982,14 @@ cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st) {
 
 // ============================================================================================
 // Embedding backward: scatter-add of dh0 into E's rows, owner computes.
-// CTA c owns byte value c and writes dE[c][0..D) once. Thread t of 256 looks
-// at positions p = 4u + q with u = t, t + 256, ... (four context bytes per
-// 32-bit load, coalesced) and adds dh0[p][0..D) for each p with ctx[p] == c
-// in increasing p. The 256 thread sums are then added by a butterfly within
-// each warp (fixed shuffle order) and the 8 warp sums in warp order, so the
-// result is the same on every run. Position p = s*K + k has its D gradient
-// values at dX[p*D .. p*D + D).
+// CTA c owns byte value c and writes dE[c][0..D) once. The b*K context bytes
+// are cut into 64-byte segments; thread t of 256 takes segments t, t + 256,
+// ... (four 16-byte loads per segment, issued together and coalesced across
+// the warp) and adds dh0[p][0..D) for each position p of its segments with
+// ctx[p] == c, in increasing p. The 256 thread sums are then added by a
+// butterfly within each warp (fixed shuffle order) and the 8 warp sums in
+// warp order, so the result is the same on every run. Position p = s*K + k
+// has its D gradient values at dX[p*D .. p*D + D).
 // ============================================================================================
 template <int DM>
 __global__ void __launch_bounds__(256) embed_bwd_owner_kernel(const uint8_t* __restrict__ ctx,
@@ -893,41 +1002,48 @@ __global__ void __launch_bounds__(256) embed_bwd_owner_kernel(const uint8_t* __r
   float acc[DM];
 #pragma unroll
   for (int d = 0; d < DM; ++d) acc[d] = 0.f;
-  const int nw = (P + 3) / 4;
-  const bool al4 = (reinterpret_cast<uintptr_t>(ctx) & 3) == 0;
-  for (int u = t; u < nw; u += 256) {
-    uint32_t w4;
-    const int p0 = 4 * u;
-    if (al4 && p0 + 4 <= P) {
-      w4 = *reinterpret_cast<const uint32_t*>(ctx + p0);
+  const int nseg = (P + 63) / 64;
+  const bool al16 = (reinterpret_cast<uintptr_t>(ctx) & 15) == 0;
+  for (int sg = t; sg < nseg; sg += 256) {
+    const int p0 = sg * 64;
+    uint4 w[4];
+    if (al16 && p0 + 64 <= P) {
+      const uint4* src = reinterpret_cast<const uint4*>(ctx + p0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) w[q] = __ldg(src + q);
     } else {
-      w4 = 0;
-      for (int q = 0; q < 4; ++q) w4 |= (uint32_t)(p0 + q < P ? ctx[p0 + q] : (uint8_t)(c ^ 1)) << (8 * q);
+      uint8_t* wb = reinterpret_cast<uint8_t*>(w);
+      for (int q = 0; q < 64; ++q) wb[q] = p0 + q < P ? ctx[p0 + q] : (uint8_t)(c ^ 1);
     }
+    const uint32_t* wv = reinterpret_cast<const uint32_t*>(w);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (((w4 >> (8 * q)) & 0xffu) == (uint32_t)c) {
-        const float* row = dX + (size_t)(p0 + q) * D;
+    for (int q = 0; q < 16; ++q) {
+      const uint32_t x = wv[q];
 #pragma unroll
-        for (int d = 0; d < DM; ++d)
-          if (d < D) acc[d] += row[d];
+      for (int u = 0; u < 4; ++u) {
+        if (((x >> (8 * u)) & 0xffu) == (uint32_t)c) {
+          const float* row = dX + (size_t)(p0 + 4 * q + u) * D;
+#pragma unroll
+          for (int d = 0; d < DM; ++d)
+            if (d < D) acc[d] += row[d];
+        }
       }
     }
   }
-  const int lane = t & 31, w = t >> 5;
+  const int lane = t & 31, wp = t >> 5;
 #pragma unroll
   for (int d = 0; d < DM; ++d) {
     float v = acc[d];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) wsum[w][d] = v;
+    if (lane == 0) wsum[wp][d] = v;
   }
   __syncthreads();
   if (t < D) {
-    float s = wsum[0][t];
+    float sum = wsum[0][t];
 #pragma unroll
-    for (int ww = 1; ww < 8; ++ww) s += wsum[ww][t];
-    dE[(size_t)c * D + t] = s;
+    for (int ww = 1; ww < 8; ++ww) sum += wsum[ww][t];
+    dE[(size_t)c * D + t] = sum;
   }
 }
 
@@ -1650,11 +1766,16 @@ int colsum_tiles(const ColsumJobs& jobs) {
   return tiles;
 }
 
-int colsum_chunk_rows(int rows) {
-  if (rows <= 512) return 0;
-  int cr = (rows + kColsumMaxChunks - 1) / kColsumMaxChunks;
-  cr = (cr + 15) / 16 * 16;
-  return cr < 256 ? 256 : cr;
+int colsum_chunk_rows(int rows, int tiles) {
+  // about 256 CTAs in all: the column sums run on a side stream beside the
+  // step's critical path, and a wider grid would take SMs from it
+  if (rows <= 512 || tiles <= 0) return 0;
+  int nch = 256 / tiles;
+  if (nch > kColsumMaxChunks) nch = kColsumMaxChunks;
+  if (nch > rows / 256) nch = rows / 256;
+  if (nch < 2) return 0;
+  int cr = (rows + nch - 1) / nch;
+  return (cr + 15) / 16 * 16;
 }
 
 cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st) {

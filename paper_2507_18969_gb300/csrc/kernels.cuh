@@ -203,8 +203,9 @@ struct ColsumJobs {
   int chunk_rows = 0;
 };
 int colsum_tiles(const ColsumJobs& jobs);
-// Rows per chunk for a column sum over `rows` rows (0: one chunk).
-int colsum_chunk_rows(int rows);
+// Rows per chunk for a column sum over `rows` rows and `tiles` 32-column
+// tiles (0: one chunk).
+int colsum_chunk_rows(int rows, int tiles);
 constexpr int kColsumMaxChunks = 64;
 cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st);
 // Adam that also writes the BF16 copy Pb of every updated parameter (same flat layout).
