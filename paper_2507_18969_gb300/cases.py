@@ -1,0 +1,82 @@
+"""Named timing cases of the library (for step timing and kernel profiles).
+
+  python -m paper_2507_18969_gb300.cases steps CASE [CHUNKS]
+      An encoder session on CASE's model and stream count over random bytes
+      already on the device (the kernels' work does not depend on the byte
+      values): one warm-up chunk of 64 model steps, then CHUNKS timed chunks;
+      prints milliseconds per model step (CUDA events).
+  python -m paper_2507_18969_gb300.cases gemm CASE CODE
+      Every tcgen05 GEMM site of CASE's model with every tile code set to CODE,
+      each launched alone (Model.time_gemms): ms, GFLOP and TFLOP/s per site.
+
+Cases: c1 (K=32, F'=256, 4 MBRBs of 256; 512 streams, the 64 MiB workload's
+model), c1_32k (the same model, 32768 streams), c4 (K=64, F'=512, 6 MBRBs of
+512; 4096 streams, the 1 GiB workload's model) and c4_gemm (c4's F, H and
+stream count with F'=16 and 2 blocks: c4's GEMM shapes in well under 1 GB).
+"""
+from __future__ import annotations
+
+import json
+import sys
+
+import numpy as np
+
+CASES = {
+    "c1": dict(b=512, K=32, Fp=256, H=256, n=4),
+    "c1_32k": dict(b=32768, K=32, Fp=256, H=256, n=4),
+    "c4": dict(b=4096, K=64, Fp=512, H=512, n=6),
+    "c4_gemm": dict(b=4096, K=64, Fp=16, H=512, n=2),
+}
+
+
+def _cfg(c, edpc, **kw):
+    return edpc.make_cfg(streams=c["b"], context=c["K"], embed_dim=16, latent=c["Fp"], hidden=c["H"], blocks=c["n"],
+                         branches=2, lr=1e-3, seed=1, precision=edpc.EDPC_BF16, **kw)
+
+
+def steps(name: str, chunks: int = 2) -> dict:
+    import torch
+    import paper_2507_18969_gb300 as edpc
+    from paper_2507_18969_gb300 import Encoder
+    c = CASES[name]
+    n = c["b"] * (c["K"] + (chunks + 2) * 64 + 8)
+    x = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    enc = Encoder(_cfg(c, edpc), device_ptr=x.data_ptr(), length=n, stream=st.cuda_stream)
+    enc.run(64)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    done = enc.run(64 * chunks)
+    e1.record(st)
+    torch.cuda.synchronize()
+    enc.close()
+    ms = e0.elapsed_time(e1) / done
+    return dict(case=name, streams=c["b"], ms_per_model_step=ms, mbs=c["b"] / ms / 1e3)
+
+
+def gemm(name: str, code: int) -> list[dict]:
+    import paper_2507_18969_gb300 as edpc
+    c = CASES[name]
+    m = edpc.Model(_cfg(c, edpc), c["b"])
+    m.set_tiles(np.full(200, code, np.uint8))
+    ms, fl, _ = m.time_gemms(1)
+    m.close()
+    return [dict(site=int(i), gflop=fl[i] / 1e9, us=ms[i] * 1e3, tflops=fl[i] / ms[i] / 1e9) for i in np.nonzero(fl)[0]]
+
+
+def main(argv) -> int:
+    if len(argv) < 2 or argv[0] not in ("steps", "gemm") or argv[1] not in CASES:
+        print(__doc__)
+        return 2
+    if argv[0] == "steps":
+        print(json.dumps(steps(argv[1], int(argv[2]) if len(argv) > 2 else 2)), flush=True)
+    else:
+        for r in gemm(argv[1], int(argv[2]) if len(argv) > 2 else 0):
+            print(json.dumps(r), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main(sys.argv[1:]))

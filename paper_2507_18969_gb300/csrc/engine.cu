@@ -203,10 +203,17 @@ int Model::init(const edpc_cfg& cfg, int streams) {
       dy_pend = a.take<float>(bFp);
       pend = a.take<FdmPend>(1);
     }
+    if (embed_bwd_chunks(d.b, d.K) > 1) {
+      emb_part = a.take<float>((size_t)256 * embed_bwd_chunks(d.b, d.K) * d.D);
+      emb_cnt = a.take<unsigned>(256);
+    }
     if (bf16) {
       // column sums of one launch: at most 4 jobs of at most max(F, kH, 256) columns
-      cs_tiles = 4 * ((std::max(std::max(d.F, kH), 256) + 31) / 32);
-      cs_part = a.take<float>((size_t)cs_tiles * kColsumMaxChunks * 32);
+      // (32-column tiles, or 128-column tiles each rounded up: 4 * ceil(max / 128) * 128 columns)
+      const int maxc = std::max(std::max(d.F, kH), 256);
+      cs_tiles = 4 * ((maxc + 31) / 32);
+      cs_cols = 4 * ((maxc + 127) / 128) * 128;
+      cs_part = a.take<float>((size_t)cs_cols * kColsumMaxChunks);
       cs_cnt = a.take<unsigned>((size_t)cs_tiles);
       // split-K scratch: the largest splitk * M * N of any dW GEMM at any N tile
       sk_ws_floats = 0;
@@ -509,7 +516,7 @@ int Model::backward_f32(const StepIO& io, cudaStream_t st) {
     EDPC_TRY(block_bwd(j, cur, nxt, st));
     std::swap(cur, nxt);
   }
-  EDPC_CUDA(launch_embed_bwd(ctx, cur, d.b, d.K, d.D, G + po.E, st));
+  EDPC_CUDA(launch_embed_bwd(ctx, cur, d.b, d.K, d.D, G + po.E, emb_part, emb_cnt, st));
   return EDPC_OK;
 }
 
@@ -981,7 +988,9 @@ int Model::colsums(ColsumJobs cj, cudaStream_t st) {
   NoPdl scope;
   cj.chunk_rows = colsum_chunk_rows(d.b, colsum_tiles(cj));
   if (cj.chunk_rows > 0) {
-    if (colsum_tiles(cj) > cs_tiles) return fail(EDPC_EINVAL, "column-sum launch exceeds its scratch");
+    const int tw = colsum_vec(cj) ? 128 : 32;
+    if (colsum_tiles(cj) > cs_tiles || colsum_tiles(cj) * tw > cs_cols)
+      return fail(EDPC_EINVAL, "column-sum launch exceeds its scratch");
     cj.part = cs_part;
     cj.cnt = cs_cnt;
   }
@@ -1132,7 +1141,7 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
     EDPC_TRY(colsums(cj2, side));
     EDPC_TRY(run_tc(kSiteLteDownDx, st));  // writes dh0
   }
-  EDPC_CUDA(launch_embed_bwd(ctx, dh0, d.b, d.K, d.D, G + po.E, st));
+  EDPC_CUDA(launch_embed_bwd(ctx, dh0, d.b, d.K, d.D, G + po.E, emb_part, emb_cnt, st));
   // join the side stream
   EDPC_CUDA(cudaEventRecord(join_ev, side));
   EDPC_CUDA(cudaStreamWaitEvent(st, join_ev, 0));

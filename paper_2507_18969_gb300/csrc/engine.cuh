@@ -51,9 +51,12 @@ class Model {
   float *Xp = nullptr, *Y = nullptr, *z = nullptr, *p = nullptr, *dz = nullptr;
   float *dXa = nullptr, *dXb = nullptr, *dX0 = nullptr, *dA = nullptr, *dG = nullptr;
   float *dY = nullptr, *dXp = nullptr;
+  float* emb_part = nullptr;              // embedding-adjoint chunk partials (many positions)
+  unsigned* emb_cnt = nullptr;            // their arrival counters, one per byte value
   float* cs_part = nullptr;               // column-sum chunk partials (side stream)
   unsigned* cs_cnt = nullptr;             // column-sum arrival counters, one per 32-column tile
-  int cs_tiles = 0;                       // tiles cs_part and cs_cnt are sized for
+  int cs_tiles = 0;                       // tiles cs_cnt is sized for
+  int cs_cols = 0;                        // tile columns (per chunk) cs_part is sized for
   float* sk_ws = nullptr;                 // split-K partial tiles of the dW GEMMs (side stream)
   unsigned* sk_cnt = nullptr;             // split-K arrival counters
   size_t sk_ws_floats = 0;

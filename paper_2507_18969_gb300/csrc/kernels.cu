@@ -982,77 +982,124 @@ cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st) {
 
 // ============================================================================================
 // Embedding backward: scatter-add of dh0 into E's rows, owner computes.
-// CTA c owns byte value c and writes dE[c][0..D) once. The b*K context bytes
-// are cut into 64-byte segments; thread t of 256 takes segments t, t + 256,
-// ... (four 16-byte loads per segment, issued together and coalesced across
-// the warp) and adds dh0[p][0..D) for each position p of its segments with
-// ctx[p] == c, in increasing p. The 256 thread sums are then added by a
-// butterfly within each warp (fixed shuffle order) and the 8 warp sums in
-// warp order, so the result is the same on every run. Position p = s*K + k
-// has its D gradient values at dX[p*D .. p*D + D).
+// CTA (c, q) owns byte value c and chunk q of kEmbChunkPos consecutive
+// positions. Warp w of 8 takes a contiguous eighth of the chunk, read 128
+// positions at a time (one 32-bit word per lane, coalesced, four words
+// prefetched); ballots find the positions p with ctx[p] == c, which the warp
+// visits in increasing p: lane d adds dh0[p][d] (and d + 32 when D > 32),
+// eight rows' loads in flight at a time. The 8 warp sums are added in warp
+// order. With one chunk that is dE[c]; with several, each CTA writes its
+// partial and the last CTA of c to arrive adds the chunks' partials in chunk
+// order (a fence precedes the arrival counter), so the result does not depend
+// on timing. Position p = s*K + k has its D gradient values at dX[p*D ..).
 // ============================================================================================
-template <int DM>
 __global__ void __launch_bounds__(256) embed_bwd_owner_kernel(const uint8_t* __restrict__ ctx,
                                                               const float* __restrict__ dX, int P, int D,
-                                                              float* __restrict__ dE) {
+                                                              float* __restrict__ dE, float* __restrict__ part,
+                                                              unsigned* __restrict__ cnt) {
   pdl_wait();
   pdl_launch();
-  __shared__ float wsum[8][DM];
-  const int c = blockIdx.x, t = threadIdx.x;
-  float acc[DM];
+  __shared__ float wsum[8][64];
+  __shared__ int is_last;
+  const uint32_t c = blockIdx.x;
+  const int nq = gridDim.y, q = blockIdx.y;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c_lo = min(P, q * kEmbChunkPos), c_hi = min(P, c_lo + kEmbChunkPos);
+  const int per = ((c_hi - c_lo + 8 * 128 - 1) / (8 * 128)) * 128;  // positions per warp, a multiple of 128
+  const int p_lo = min(c_hi, c_lo + w * per), p_hi = min(c_hi, p_lo + per);
+  const bool al4 = (reinterpret_cast<uintptr_t>(ctx) & 3) == 0;
+  float a0 = 0.f, a1 = 0.f;  // dims lane and lane + 32
+  int pend[8];
+  int np = 0;
+  auto flush = [&]() {
+    float v0[8], v1[8];
 #pragma unroll
-  for (int d = 0; d < DM; ++d) acc[d] = 0.f;
-  const int nseg = (P + 63) / 64;
-  const bool al16 = (reinterpret_cast<uintptr_t>(ctx) & 15) == 0;
-  for (int sg = t; sg < nseg; sg += 256) {
-    const int p0 = sg * 64;
-    uint4 w[4];
-    if (al16 && p0 + 64 <= P) {
-      const uint4* src = reinterpret_cast<const uint4*>(ctx + p0);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) w[q] = __ldg(src + q);
-    } else {
-      uint8_t* wb = reinterpret_cast<uint8_t*>(w);
-      for (int q = 0; q < 64; ++q) wb[q] = p0 + q < P ? ctx[p0 + q] : (uint8_t)(c ^ 1);
+    for (int k = 0; k < 8; ++k) {
+      v0[k] = (k < np && lane < D) ? dX[(size_t)pend[k] * D + lane] : 0.f;
+      v1[k] = (k < np && lane + 32 < D) ? dX[(size_t)pend[k] * D + lane + 32] : 0.f;
     }
-    const uint32_t* wv = reinterpret_cast<const uint32_t*>(w);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-      const uint32_t x = wv[q];
+    for (int k = 0; k < 8; ++k) {
+      if (k < np) {
+        a0 += v0[k];
+        a1 += v1[k];
+      }
+    }
+    np = 0;
+  };
+  auto word = [&](int pw) -> uint32_t {  // positions pw..pw+3 (a non-matching byte past p_hi)
+    if (al4 && pw + 4 <= p_hi) return *reinterpret_cast<const uint32_t*>(ctx + pw);
+    uint32_t x = 0;
+    for (int u = 0; u < 4; ++u) x |= (uint32_t)(pw + u < p_hi ? ctx[pw + u] : (uint8_t)(c ^ 1u)) << (8 * u);
+    return x;
+  };
+  for (int pb = p_lo; pb < p_hi; pb += 4 * 128) {
+    uint32_t xs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) xs[k] = (pb + k * 128 < p_hi) ? word(pb + k * 128 + 4 * lane) : (c ^ 1u) * 0x01010101u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int p0 = pb + k * 128;
+      uint32_t m[4], any = 0;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        if (((x >> (8 * u)) & 0xffu) == (uint32_t)c) {
-          const float* row = dX + (size_t)(p0 + 4 * q + u) * D;
+        m[u] = __ballot_sync(0xffffffffu, ((xs[k] >> (8 * u)) & 0xffu) == c);
+        any |= m[u];
+      }
+      while (any) {  // warp-uniform: lanes l in increasing order, then their bytes u
+        const int l = __ffs(any) - 1;
+        any &= any - 1;
 #pragma unroll
-          for (int d = 0; d < DM; ++d)
-            if (d < D) acc[d] += row[d];
+        for (int u = 0; u < 4; ++u) {
+          if ((m[u] >> l) & 1u) {
+            pend[np++] = p0 + 4 * l + u;
+            if (np == 8) flush();
+          }
         }
       }
     }
   }
-  const int lane = t & 31, wp = t >> 5;
-#pragma unroll
-  for (int d = 0; d < DM; ++d) {
-    float v = acc[d];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) wsum[wp][d] = v;
-  }
+  flush();
+  wsum[w][lane] = a0;
+  wsum[w][lane + 32] = a1;
   __syncthreads();
+  const int t = threadIdx.x;
+  float sum = 0.f;
   if (t < D) {
-    float sum = wsum[0][t];
+    sum = wsum[0][t];
 #pragma unroll
     for (int ww = 1; ww < 8; ++ww) sum += wsum[ww][t];
-    dE[(size_t)c * D + t] = sum;
+  }
+  if (nq == 1) {
+    if (t < D) dE[(size_t)c * D + t] = sum;
+    return;
+  }
+  if (t < D) {
+    part[((size_t)c * nq + q) * D + t] = sum;
+    __threadfence();
+  }
+  __syncthreads();
+  if (t == 0) is_last = (atomicAdd(&cnt[c], 1u) == (unsigned)(nq - 1));
+  __syncthreads();
+  if (is_last && t < D) {
+    __threadfence();
+    const float* src = part + (size_t)c * nq * D + t;
+    float acc = 0.f;
+    for (int k = 0; k < nq; ++k) acc += __ldcg(src + (size_t)k * D);
+    dE[(size_t)c * D + t] = acc;
+    if (t == 0) cnt[c] = 0u;
   }
 }
 
-cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, cudaStream_t st) {
-  const int P = b * K;
-  if (D <= 16) return launch_k(embed_bwd_owner_kernel<16>, dim3(256), dim3(256), 0, st, ctx, dX, P, D, dE);
-  if (D <= 32) return launch_k(embed_bwd_owner_kernel<32>, dim3(256), dim3(256), 0, st, ctx, dX, P, D, dE);
-  if (D <= 64) return launch_k(embed_bwd_owner_kernel<64>, dim3(256), dim3(256), 0, st, ctx, dX, P, D, dE);
-  return cudaErrorInvalidValue;
+int embed_bwd_chunks(int b, int K) { return (b * K + kEmbChunkPos - 1) / kEmbChunkPos; }
+
+cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, float* part,
+                             unsigned* cnt, cudaStream_t st) {
+  if (D > 64) return cudaErrorInvalidValue;
+  const int nq = embed_bwd_chunks(b, K);
+  if (nq > 1 && (!part || !cnt)) return cudaErrorInvalidValue;
+  return launch_k(embed_bwd_owner_kernel, dim3(256, nq < 1 ? 1 : nq), dim3(256), 0, st, ctx, dX, b * K, D, dE, part,
+                  cnt);
 }
 
 // ============================================================================================
@@ -1685,31 +1732,64 @@ cudaError_t launch_ln_bwd_bf16(const float* dX0, const float* xhat, const float*
 
 // ============================================================================================
 // Batched column sums (bias and LN-affine gradients), fixed order: CTA = one
-// 32-column tile of one job and one chunk of rows; warp w sums the chunk's rows
-// w, w+16, ... with four interleaved accumulators; warps are then added in
-// order. With several chunks, the last CTA of a tile to arrive adds the chunk
-// partials in chunk order (a fence before the arrival counter makes the
-// partials visible to it).
+// tile of TW columns of one job and one chunk of rows; warp w sums the chunk's
+// rows w, w+16, ...; warps are then added in order. TW = 32 (one column per
+// lane, four interleaved row accumulators) below 2048 rows; from there, when
+// every job allows 16-byte loads, TW = 128 (four columns per lane, eight
+// interleaved row accumulators: rows r, r+16, ..., r+112 of each pass). With
+// several chunks, the last CTA of a tile to arrive adds the chunk partials in
+// chunk order (a fence before the arrival counter makes the partials visible
+// to it).
 // ============================================================================================
+template <bool VEC>
 __global__ void __launch_bounds__(512) colsum_multi_kernel(ColsumJobs jobs) {
   pdl_wait();
   pdl_launch();
-  __shared__ float part[16][33];
+  constexpr int TW = VEC ? 128 : 32;
+  constexpr int CPL = VEC ? 4 : 1;  // columns per lane
+  __shared__ float part[16][TW + 1];
   __shared__ int is_last;
   const int tile = blockIdx.x;
   int t = blockIdx.x, j = 0;
-  while (j < jobs.n - 1 && t >= (jobs.job[j].cols + 31) / 32) {
-    t -= (jobs.job[j].cols + 31) / 32;
+  while (j < jobs.n - 1 && t >= (jobs.job[j].cols + TW - 1) / TW) {
+    t -= (jobs.job[j].cols + TW - 1) / TW;
     ++j;
   }
   const ColsumJob jb = jobs.job[j];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c = t * 32 + lane;
+  const int c = t * TW + lane * CPL;
   const int nch = gridDim.y;
   const int r_lo = (nch > 1) ? blockIdx.y * jobs.chunk_rows : 0;
   const int r_hi = (nch > 1) ? min(jb.rows, r_lo + jobs.chunk_rows) : jb.rows;
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-  if (c < jb.cols) {
+  float a[8][CPL];
+#pragma unroll
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) a[k][q] = 0.f;
+  auto load = [&](int r, float (&v)[CPL]) {
+    const size_t o = (size_t)r * jb.ld + c;
+    if (VEC) {
+      float4 x = *reinterpret_cast<const float4*>(jb.X + o);
+      if (jb.Y) {
+        const float4 y = *reinterpret_cast<const float4*>(jb.Y + o);
+        x.x *= y.x;
+        x.y *= y.y;
+        x.z *= y.z;
+        x.w *= y.w;
+      }
+      v[0] = x.x;
+      if (CPL > 1) {
+        v[CPL > 1 ? 1 : 0] = x.y;
+        v[CPL > 2 ? 2 : 0] = x.z;
+        v[CPL > 3 ? 3 : 0] = x.w;
+      }
+    } else {
+      v[0] = jb.Y ? jb.X[o] * jb.Y[o] : jb.X[o];
+    }
+  };
+  if (!VEC && c < jb.cols) {
+    // rows w, w+16, ... with four interleaved accumulators
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
     int r = r_lo + w;
     if (jb.Y) {
       for (; r + 48 < r_hi; r += 64) {
@@ -1728,41 +1808,77 @@ __global__ void __launch_bounds__(512) colsum_multi_kernel(ColsumJobs jobs) {
       }
       for (; r < r_hi; r += 16) a0 += jb.X[(size_t)r * jb.ld + c];
     }
+    a[0][0] = (a0 + a1) + (a2 + a3);
   }
-  part[w][lane] = (a0 + a1) + (a2 + a3);
-  __syncthreads();
-  if (nch == 1) {
-    if (w == 0 && c < jb.cols) {
-      float s = part[0][lane];
+  if (VEC && c < jb.cols) {
+    int r = r_lo + w;
+    for (; r + 112 < r_hi; r += 128) {
+      float v[8][CPL];
 #pragma unroll
-      for (int i = 1; i < 16; ++i) s += part[i][lane];
-      jb.out[c] = s;
+      for (int k = 0; k < 8; ++k) load(r + 16 * k, v[k]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) a[k][q] += v[k][q];
     }
+    for (; r < r_hi; r += 16) {
+      float v[CPL];
+      load(r, v);
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) a[0][q] += v[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < CPL; ++q)
+    part[w][lane * CPL + q] =
+        VEC ? ((a[0][q] + a[1][q]) + (a[2][q] + a[3][q])) + ((a[4][q] + a[5][q]) + (a[6][q] + a[7][q])) : a[0][q];
+  __syncthreads();
+  const int tc = threadIdx.x;  // column of the tile handled in the final sums
+  const int cc = t * TW + tc;
+  float sum = 0.f;
+  if (tc < TW) {
+    sum = part[0][tc];
+#pragma unroll
+    for (int i = 1; i < 16; ++i) sum += part[i][tc];
+  }
+  if (nch == 1) {
+    if (tc < TW && cc < jb.cols) jb.out[cc] = sum;
     return;
   }
-  if (w == 0) {
-    float s = part[0][lane];
-#pragma unroll
-    for (int i = 1; i < 16; ++i) s += part[i][lane];
-    jobs.part[((size_t)tile * nch + blockIdx.y) * 32 + lane] = s;
+  if (tc < TW) {
+    jobs.part[((size_t)tile * nch + blockIdx.y) * TW + tc] = sum;
     __threadfence();
   }
   __syncthreads();
   if (threadIdx.x == 0) is_last = (atomicAdd(&jobs.cnt[tile], 1u) == (unsigned)(nch - 1));
   __syncthreads();
-  if (is_last && w == 0) {
+  if (is_last && tc < TW) {
     __threadfence();
-    const float* src = jobs.part + (size_t)tile * nch * 32 + lane;
-    float s = 0.f;
-    for (int q = 0; q < nch; ++q) s += __ldcg(src + (size_t)q * 32);
-    if (c < jb.cols) jb.out[c] = s;
-    if (lane == 0) jobs.cnt[tile] = 0u;
+    const float* src = jobs.part + (size_t)tile * nch * TW + tc;
+    float acc = 0.f;
+    for (int k = 0; k < nch; ++k) acc += __ldcg(src + (size_t)k * TW);
+    if (cc < jb.cols) jb.out[cc] = acc;
+    if (tc == 0) jobs.cnt[tile] = 0u;
   }
 }
 
+bool colsum_vec(const ColsumJobs& jobs) {
+  // 128-column tiles only from 2048 rows on: below that the 32-column grid's
+  // parallelism matters more (the sums end the side stream before Adam)
+  for (int j = 0; j < jobs.n; ++j) {
+    const ColsumJob& b = jobs.job[j];
+    if (b.rows < 2048) return false;
+    if ((b.cols & 3) || (b.ld & 3) || (reinterpret_cast<uintptr_t>(b.X) & 15) ||
+        (b.Y && (reinterpret_cast<uintptr_t>(b.Y) & 15)))
+      return false;
+  }
+  return true;
+}
+
 int colsum_tiles(const ColsumJobs& jobs) {
+  const int tw = colsum_vec(jobs) ? 128 : 32;
   int tiles = 0;
-  for (int j = 0; j < jobs.n; ++j) tiles += (jobs.job[j].cols + 31) / 32;
+  for (int j = 0; j < jobs.n; ++j) tiles += (jobs.job[j].cols + tw - 1) / tw;
   return tiles;
 }
 
@@ -1790,7 +1906,8 @@ cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st) {
     nch = (rows + jobs.chunk_rows - 1) / jobs.chunk_rows;
     if (nch > kColsumMaxChunks) return cudaErrorInvalidValue;
   }
-  return launch_k(colsum_multi_kernel, dim3(tiles, nch), dim3(512), 0, st, jobs);
+  if (colsum_vec(jobs)) return launch_k(colsum_multi_kernel<true>, dim3(tiles, nch), dim3(512), 0, st, jobs);
+  return launch_k(colsum_multi_kernel<false>, dim3(tiles, nch), dim3(512), 0, st, jobs);
 }
 
 // ============================================================================================

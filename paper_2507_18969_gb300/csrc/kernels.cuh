@@ -128,8 +128,14 @@ struct FdmSplitArgs {
 cudaError_t launch_fdm_dx(const FdmSplitArgs& a, cudaStream_t st);
 cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st);
 // dE[c][d] = sum over positions with ctx == c of dX[s][k*D + d], fixed order
-// (one CTA per byte value c); D <= 64.
-cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, cudaStream_t st);
+// (CTAs per byte value c and chunk of kEmbChunkPos positions); D <= 64. With
+// more than one chunk, part (256 * chunks * D floats) and cnt (256 counters,
+// zero between launches) hold the chunk partials; launches sharing them must
+// not overlap.
+constexpr int kEmbChunkPos = 16384;
+int embed_bwd_chunks(int b, int K);
+cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, float* part,
+                             unsigned* cnt, cudaStream_t st);
 // Adam over the flat shared parameters; bf16 != nullptr also refreshes the BF16 copy.
 cudaError_t launch_adam(float* P, const float* G, float* M, float* V, size_t n, const StepCtl* ctl,
                         cudaStream_t st);
@@ -192,7 +198,7 @@ struct ColsumJob {
 // 32-column tile and chunk); each CTA writes its partial sums to `part` and the
 // last CTA of a tile to arrive adds the chunks' partials in chunk order, so the
 // result does not depend on which CTA finishes last. `part` holds
-// colsum_tiles(jobs) * chunks * 32 floats and `cnt` one zero-initialised counter
+// colsum_tiles(jobs) * chunks * (tile width) floats and `cnt` one zero-initialised counter
 // per tile; the last CTA sets its counter back to zero. Launches that share
 // part and cnt must not overlap (they run on one stream).
 struct ColsumJobs {
@@ -202,6 +208,9 @@ struct ColsumJobs {
   unsigned* cnt = nullptr;
   int chunk_rows = 0;
 };
+// Tiles of a launch: 128-column tiles when colsum_vec (every job's columns,
+// row stride and pointers allow 16-byte loads), else 32-column tiles.
+bool colsum_vec(const ColsumJobs& jobs);
 int colsum_tiles(const ColsumJobs& jobs);
 // Rows per chunk for a column sum over `rows` rows and `tiles` 32-column
 // tiles (0: one chunk).
