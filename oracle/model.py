@@ -13,6 +13,11 @@ Model(x_{i-t..i-1}) of Algorithm 1 (Sec. 2.1, Eq. 1), as read from Sec. 3:
   MBRB (Eqs. 9-13): X0 = LN(X); X_i = X0 W_i^T + c_i (i = 1..k);
   Xf = X_1 * ... * X_k; G = GELU(Xf); out = G Wo^T + co + X.
 
+  Variant "w/o LTE" (ablation of Table 4 and Sec. 4.4.3; latent = 0): no
+  projections; the per-stream FDM is F x F and acts on X itself,
+  y_s = x_s U_s and X = Y. Its parameter count exceeds the LTE model's by
+  b (F^2 - F'^2) - (2 F F' + F' + F), the reading of Table 4's gap.
+
 Readings where the paper is silent or ambiguous:
   * Layer order (Fig. 3 is missing): embedding, Local MBRBs, LTE, Global
     MBRBs, head. There is no residual around the LTE and no final norm.
@@ -62,7 +67,7 @@ INV_SQRT_2PI = 1.0 / math.sqrt(2.0 * math.pi)
 class Config:
     context: int = 16      # K: history bytes (t in Algorithm 1)
     embed_dim: int = 16    # D
-    latent: int = 128      # F' = F / r
+    latent: int = 128      # F' = F / r; 0: no LTE (the FDM is F x F, Table 4's "w/o LTE")
     hidden: int = 128      # H: MBRB branch width
     blocks: int = 2        # n: Local blocks n//2, Global blocks n - n//2
     branches: int = 2      # k: MBRB branches
@@ -76,6 +81,15 @@ class Config:
     @property
     def n_local(self) -> int:
         return self.blocks // 2
+
+    @property
+    def lte(self) -> bool:
+        return self.latent > 0
+
+    @property
+    def fdm_dim(self) -> int:
+        # side of each stream's FDM: F' with the LTE, F without it
+        return self.latent if self.lte else self.F
 
 
 def param_layout(cfg: Config):
@@ -97,11 +111,14 @@ def param_layout(cfg: Config):
             (f"blk{j}.Wo", (F, H), ("uniform", inv(H))),
             (f"blk{j}.co", (F,), ("uniform", inv(H))),
         ]
+    if cfg.lte:
+        out += [
+            ("lte.W1", (Fp, F), ("uniform", inv(F))),
+            ("lte.b1", (Fp,), ("uniform", inv(F))),
+            ("lte.W2", (F, Fp), ("uniform", inv(Fp))),
+            ("lte.b2", (F,), ("uniform", inv(Fp))),
+        ]
     out += [
-        ("lte.W1", (Fp, F), ("uniform", inv(F))),
-        ("lte.b1", (Fp,), ("uniform", inv(F))),
-        ("lte.W2", (F, Fp), ("uniform", inv(Fp))),
-        ("lte.b2", (F,), ("uniform", inv(Fp))),
         ("head.W", (256, F), ("uniform", inv(F))),
         ("head.b", (256,), ("uniform", inv(F))),
     ]
@@ -109,7 +126,7 @@ def param_layout(cfg: Config):
 
 
 def fdm_bound(cfg: Config) -> float:
-    return math.sqrt(3.0 / float(cfg.latent))
+    return math.sqrt(3.0 / float(cfg.fdm_dim))
 
 
 def gelu(x):
@@ -140,7 +157,7 @@ class Model:
                 self.P[name] = np.full(shape, float(val))
             else:
                 self.P[name] = init_values(cfg.seed, tid, size, val).reshape(shape)
-        Fp = cfg.latent
+        Fp = cfg.fdm_dim
         self.U = init_values(cfg.seed, FDM_TID, streams * Fp * Fp, fdm_bound(cfg)).reshape(streams, Fp, Fp)
         self.m = {k: np.zeros_like(v) for k, v in self.P.items()}
         self.v = {k: np.zeros_like(v) for k, v in self.P.items()}
@@ -195,11 +212,11 @@ class Model:
         for j in range(cfg.n_local):
             X = self._mbrb_fwd(j, X, cache)
         cache["lte_in"] = X
-        Xp = X @ P["lte.W1"].T + P["lte.b1"]                       # Eq. 14
+        Xp = X @ P["lte.W1"].T + P["lte.b1"] if cfg.lte else X     # Eq. 14 (w/o LTE: X itself)
         Us = self.U[rows]
         Y = np.matmul(Xp[:, None, :], Us)[:, 0, :]                 # Eq. 15
         cache["Xp"], cache["Y"], cache["Us"] = Xp, Y, Us
-        X = Y @ P["lte.W2"].T + P["lte.b2"]                        # Eq. 16
+        X = Y @ P["lte.W2"].T + P["lte.b2"] if cfg.lte else Y      # Eq. 16 (w/o LTE: Y itself)
         for j in range(cfg.n_local, cfg.blocks):
             X = self._mbrb_fwd(j, X, cache)
         cache["head_in"] = X
@@ -244,14 +261,20 @@ class Model:
         dX = dz @ P["head.W"]
         for j in reversed(range(cfg.n_local, cfg.blocks)):
             dX = self._mbrb_bwd(j, dX, cache, g)
-        g["lte.W2"] = dX.T @ cache["Y"]
-        g["lte.b2"] = dX.sum(axis=0)
-        dY = dX @ P["lte.W2"]
+        if cfg.lte:
+            g["lte.W2"] = dX.T @ cache["Y"]
+            g["lte.b2"] = dX.sum(axis=0)
+            dY = dX @ P["lte.W2"]
+        else:
+            dY = dX
         dU = cache["Xp"][:, :, None] * dY[:, None, :]
         dXp = np.matmul(cache["Us"], dY[:, :, None])[:, :, 0]
-        g["lte.W1"] = dXp.T @ cache["lte_in"]
-        g["lte.b1"] = dXp.sum(axis=0)
-        dX = dXp @ P["lte.W1"]
+        if cfg.lte:
+            g["lte.W1"] = dXp.T @ cache["lte_in"]
+            g["lte.b1"] = dXp.sum(axis=0)
+            dX = dXp @ P["lte.W1"]
+        else:
+            dX = dXp
         for j in reversed(range(cfg.n_local)):
             dX = self._mbrb_bwd(j, dX, cache, g)
         dh = dX.reshape(dX.shape[0], cfg.context, cfg.embed_dim)

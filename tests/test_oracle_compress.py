@@ -79,10 +79,12 @@ def test_archive_roundtrip_with_uneven_streams():
     assert np.array_equal(y, data)
 
 
-@pytest.mark.parametrize("n,b,K", [(0, 2, 2), (1, 2, 2), (5, 3, 2), (300, 4, 3), (257, 5, 2)])
-def test_roundtrip_small(n, b, K):
+@pytest.mark.parametrize("n,b,K,latent", [(0, 2, 2, 8), (1, 2, 2, 8), (5, 3, 2, 8), (300, 4, 3, 8), (257, 5, 2, 8),
+                                           (300, 4, 3, 0)])
+def test_roundtrip_small(n, b, K, latent):
+    # latent = 0: the "w/o LTE" variant of Table 4
     x = np.random.default_rng(n + b).integers(0, 256, size=n).astype(np.uint8)
-    cfg = tiny(K)
+    cfg = tiny(K, latent=latent)
     r = oracle_compress(x, cfg, b)
     y = oracle_decompress(r["streams"], n, cfg, b)
     assert np.array_equal(x, y)

@@ -163,6 +163,47 @@ def test_lte_flop_reduction_matches_paper():
     assert abs(red - g["value"]) < 0.02
 
 
+def test_without_lte_orientation_with_permutations():
+    """w/o LTE: with identity MBRBs and a permutation FDM, z is h0 shuffled by
+    the FDM alone (no projection touches it), so y = x U fixes the orientation."""
+    cfg = small_cfg(context=2, embed_dim=4, latent=0, hidden=4, blocks=2)
+    F = cfg.F
+    m = Model(cfg, streams=2)
+    assert m.U.shape == (2, F, F) and not any(n.startswith("lte.") for n, _, _ in m.layout)
+    for j in range(cfg.blocks):
+        m.P[f"blk{j}.Wo"][:] = 0.0
+        m.P[f"blk{j}.co"][:] = 0.0
+    p2 = np.array([3, 0, 6, 1, 7, 2, 4, 5])
+    U = np.zeros((F, F))
+    U[np.arange(F), p2] = 1.0                   # y[p2[i]] = x[i]
+    m.U[:] = U
+    m.U[1] = 2.0 * U                            # the second stream's FDM is its own
+    m.P["head.W"][:] = 0
+    m.P["head.W"][:F, :] = np.eye(F)
+    m.P["head.b"][:] = 0
+    ctx = np.array([[7, 200], [0, 255]])
+    z, _ = m.forward(ctx)
+    for s in range(2):
+        h0 = m.P["E"][ctx[s]].reshape(F)
+        y = np.zeros(F)
+        y[p2] = h0
+        assert np.allclose(z[s, :F], (1.0 + s) * y, atol=1e-12)
+
+
+def test_without_lte_parameter_gap_matches_table4():
+    """The oracle's two models differ by b (F^2 - F'^2) FDM entries less the LTE's
+    own 2 F F' + F' + F; Table 4 prints 2.93e8 vs 4.15e7 at batch 4096 (F = 256,
+    F' = 64 inferred)."""
+    g = json.load(open(os.path.join(GOLDEN, "paper_numbers.json")))["table4_params"]
+    b = g["batch"]
+    kw = dict(context=16, embed_dim=16, hidden=128, blocks=2)
+    count = lambda cfg: sum(int(np.prod(sh)) for _, sh, _ in param_layout(cfg)) + b * cfg.fdm_dim ** 2  # noqa: E731
+    gap = count(Config(latent=0, **kw)) - count(Config(latent=64, **kw))
+    assert gap == b * (256 * 256 - 64 * 64) - (2 * 256 * 64 + 64 + 256)
+    printed = g["without_lte"] - g["edpc"]
+    assert abs(gap - printed) / printed < 0.005
+
+
 def test_table4_parameter_gap_is_per_stream_fdm():
     g = json.load(open(os.path.join(GOLDEN, "paper_numbers.json")))["table4_params"]
     F, Fp, b = 256, 64, g["batch"]
@@ -194,7 +235,7 @@ def _fd_check(m, ctx, targets, rows, n_coords=25, h=1e-5, seed=0):
             worst = max(worst, err if abs(fd - gflat[i]) > 1e-9 else 0.0)
     for r_, s in enumerate(rows):
         for _ in range(8):
-            i, j = rng.integers(0, m.cfg.latent, size=2)
+            i, j = rng.integers(0, m.cfg.fdm_dim, size=2)
             old = m.U[s, i, j]
             m.U[s, i, j] = old + h
             lp = m.loss(ctx, targets, rows)
@@ -207,9 +248,10 @@ def _fd_check(m, ctx, targets, rows, n_coords=25, h=1e-5, seed=0):
     return worst
 
 
-@pytest.mark.parametrize("branches,blocks", [(2, 2), (3, 2), (2, 4), (1, 3)])
-def test_adjoint_matches_finite_differences(branches, blocks):
-    cfg = small_cfg(branches=branches, blocks=blocks)
+@pytest.mark.parametrize("branches,blocks,latent", [(2, 2, 6), (3, 2, 6), (2, 4, 6), (1, 3, 6), (2, 2, 0), (3, 3, 0)])
+def test_adjoint_matches_finite_differences(branches, blocks, latent):
+    # latent = 0: the "w/o LTE" variant (per-stream F x F FDM, no projections)
+    cfg = small_cfg(branches=branches, blocks=blocks, latent=latent)
     m = Model(cfg, 4)
     rng = np.random.default_rng(branches * 10 + blocks)
     # move away from the initial point so LN gamma/beta and Adam state are generic
