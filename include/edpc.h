@@ -81,7 +81,9 @@ extern "C" {
  *              equal probability (Algorithm 1, first line).
  *   embed_dim  D, the byte embedding width; F = K * D is the model width.
  *   latent     F' = F / r, the LTE latent width (Eq. 14); the FDM of each
- *              stream is F' x F' (Eq. 15).
+ *              stream is F' x F' (Eq. 15). 0 selects the ablation "w/o LTE"
+ *              of Table 4 and Sec. 4.4.3: no projections, and each stream's
+ *              FDM is F x F and acts on the block output itself (F <= 1024).
  *   hidden     H, the width of each MBRB branch (Eq. 10).
  *   blocks     n MBRBs: n/2 "Local" before the LTE and n - n/2 "Global"
  *              after it (Fig. 3 caption).
@@ -92,7 +94,8 @@ extern "C" {
  *   seed       seed of the initial parameters (SplitMix64 counter streams).
  *
  * Limits: 1 <= context <= 256; embed_dim a multiple of 8 in [8, 64];
- * latent and hidden multiples of 8; F <= 2048, F' <= 1024, H <= 2048;
+ * latent (0, or a multiple of 8) and hidden multiples of 8; F <= 2048,
+ * F' <= 1024, H <= 2048;
  * streams <= 65535; blocks <= 16.
  */
 typedef struct {

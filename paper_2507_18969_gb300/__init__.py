@@ -249,7 +249,8 @@ class Model:
         self.cfg = cfg
         self.b = streams
         self.np = param_count(cfg)
-        self.fdm = streams * cfg.latent * cfg.latent
+        fp = cfg.latent if cfg.latent else cfg.context * cfg.embed_dim  # latent 0: no LTE, F x F FDMs
+        self.fdm = streams * fp * fp
         h = C.c_void_p()
         check(load().edpc_model_create(C.byref(cfg), streams, C.byref(h)), "edpc_model_create")
         self._h = h

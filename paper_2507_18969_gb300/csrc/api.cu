@@ -70,8 +70,12 @@ static int check_cfg(const edpc_cfg* c, bool auto_streams = false) {
   if (c->embed_dim < 8 || c->embed_dim > 64 || c->embed_dim % 8)
     return fail(EDPC_EINVAL, "embed_dim must be a multiple of 8 in [8, 64]");
   if ((uint64_t)c->context * c->embed_dim > 2048) return fail(EDPC_EINVAL, "context * embed_dim must be <= 2048");
-  if (c->latent < 8 || c->latent > 1024 || c->latent % 8)
-    return fail(EDPC_EINVAL, "latent must be a multiple of 8 in [8, 1024]");
+  if (c->latent == 0) {  // "w/o LTE": the FDM is F x F
+    if ((uint64_t)c->context * c->embed_dim > 1024)
+      return fail(EDPC_EINVAL, "latent = 0 (no LTE) needs context * embed_dim <= 1024");
+  } else if (c->latent < 8 || c->latent > 1024 || c->latent % 8) {
+    return fail(EDPC_EINVAL, "latent must be 0 or a multiple of 8 in [8, 1024]");
+  }
   if (c->hidden < 8 || c->hidden > 2048 || c->hidden % 8)
     return fail(EDPC_EINVAL, "hidden must be a multiple of 8 in [8, 2048]");
   if (c->blocks < 1 || c->blocks > (uint32_t)kMaxBlocks) return fail(EDPC_EINVAL, "blocks must be in [1, 16]");

@@ -29,7 +29,8 @@ constexpr int kErrDecodeOverrun = 2;
 struct Dims {
   int b;      // rows = streams
   int K, D, F;
-  int Fp, H, n, nloc, k;
+  int Fp, H, n, nloc, k;  // Fp: side of each stream's FDM (F' with the LTE, F without)
+  bool lte;   // false: the "w/o LTE" ablation (cfg latent = 0), no W1, b1, W2, b2
   int ldT;    // leading dimension of transposed [feature][row] operands (b rounded up to 8)
 };
 

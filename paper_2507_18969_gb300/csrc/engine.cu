@@ -32,7 +32,8 @@ Dims make_dims(const edpc_cfg& c, int b) {
   d.K = (int)c.context;
   d.D = (int)c.embed_dim;
   d.F = d.K * d.D;
-  d.Fp = (int)c.latent;
+  d.lte = c.latent != 0;
+  d.Fp = d.lte ? (int)c.latent : d.F;
   d.H = (int)c.hidden;
   d.n = (int)c.blocks;
   d.nloc = d.n / 2;
@@ -58,10 +59,14 @@ ParamOff make_offsets(const Dims& d) {
     o.blk[j].Wo = take((size_t)d.F * d.H);
     o.blk[j].co = take(d.F);
   }
-  o.W1 = take((size_t)d.Fp * d.F);
-  o.b1 = take(d.Fp);
-  o.W2 = take((size_t)d.F * d.Fp);
-  o.b2 = take(d.F);
+  if (d.lte) {
+    o.W1 = take((size_t)d.Fp * d.F);
+    o.b1 = take(d.Fp);
+    o.W2 = take((size_t)d.F * d.Fp);
+    o.b2 = take(d.F);
+  } else {
+    o.W1 = o.b1 = o.W2 = o.b2 = off;  // none
+  }
   o.Wh = take((size_t)256 * d.F);
   o.bh = take(256);
   o.total = off;
@@ -163,8 +168,10 @@ int Model::init(const edpc_cfg& cfg, int streams) {
       mat(po.blk[j].W, kH, d.F);
       mat(po.blk[j].Wo, d.F, d.H);
     }
-    mat(po.W1, d.Fp, d.F);
-    mat(po.W2, d.F, d.Fp);
+    if (d.lte) {
+      mat(po.W1, d.Fp, d.F);
+      mat(po.W2, d.F, d.Fp);
+    }
     mat(po.Wh, 256, d.F);
   }
   ntiles = (int)th.size();
@@ -276,6 +283,26 @@ int Model::init(const edpc_cfg& cfg, int streams) {
       }
     }
   }
+  if (!d.lte) {
+    // "w/o LTE": the FDM reads the last Local block's output and writes the
+    // first Global block's input; in BF16 mode its adjoint reads that input's
+    // gradient and writes the last Local block's output gradient and its BF16
+    // copies (the FP32 adjoint sets dY and dXp per step).
+    Xp = S[d.nloc];
+    Y = S[d.nloc + 1];
+    Yb = YbT = nullptr;
+    if (bf16) {
+      dY = dLte;
+      if (d.nloc > 0) {
+        dXp = bb[d.nloc - 1].dOut;
+        dXpb = bb[d.nloc - 1].dOutb;
+        dXpbT = bb[d.nloc - 1].dOutbT;
+      } else {
+        dXp = dh0;
+        dXpb = dXpbT = nullptr;
+      }
+    }
+  }
   cudaStream_t st = 0;
   // zero everything once (transposed copies keep zero padding columns)
   EDPC_CUDA(cudaMemsetAsync(arena_, 0, arena_bytes_, st));
@@ -297,10 +324,12 @@ int Model::init(const edpc_cfg& cfg, int streams) {
     ts.push_back({b.Wo, (size_t)d.F * d.H, (float)(1.0 / std::sqrt(H)), 0.f});
     ts.push_back({b.co, (size_t)d.F, (float)(1.0 / std::sqrt(H)), 0.f});
   }
-  ts.push_back({po.W1, (size_t)d.Fp * d.F, (float)(1.0 / std::sqrt(F)), 0.f});
-  ts.push_back({po.b1, (size_t)d.Fp, (float)(1.0 / std::sqrt(F)), 0.f});
-  ts.push_back({po.W2, (size_t)d.F * d.Fp, (float)(1.0 / std::sqrt(Fp)), 0.f});
-  ts.push_back({po.b2, (size_t)d.F, (float)(1.0 / std::sqrt(Fp)), 0.f});
+  if (d.lte) {  // tensor ids follow the canonical order, which has no LTE tensors without it
+    ts.push_back({po.W1, (size_t)d.Fp * d.F, (float)(1.0 / std::sqrt(F)), 0.f});
+    ts.push_back({po.b1, (size_t)d.Fp, (float)(1.0 / std::sqrt(F)), 0.f});
+    ts.push_back({po.W2, (size_t)d.F * d.Fp, (float)(1.0 / std::sqrt(Fp)), 0.f});
+    ts.push_back({po.b2, (size_t)d.F, (float)(1.0 / std::sqrt(Fp)), 0.f});
+  }
   ts.push_back({po.Wh, (size_t)256 * d.F, (float)(1.0 / std::sqrt(F)), 0.f});
   ts.push_back({po.bh, (size_t)256, (float)(1.0 / std::sqrt(F)), 0.f});
   for (size_t tid = 0; tid < ts.size(); ++tid)
@@ -394,9 +423,9 @@ int Model::fdm_fwd_call(const StepIO& io, cudaStream_t st) {
 int Model::forward_f32(const StepIO& io, cudaStream_t st) {
   EDPC_CUDA(launch_embed(io.mode == 2 ? nullptr : io.data, io.sp, ctl, P + po.E, d.b, d.K, d.D, S[0], ctx, st));
   for (int j = 0; j < d.nloc; ++j) EDPC_TRY(block_fwd(j, S[j], S[j + 1], st));
-  EDPC_TRY(linear_fwd(S[d.nloc], d.b, d.F, po.W1, po.b1, d.Fp, nullptr, Xp, st));  // Eq. 14
-  EDPC_TRY(fdm_fwd_call(io, st));
-  EDPC_TRY(linear_fwd(Y, d.b, d.Fp, po.W2, po.b2, d.F, nullptr, S[d.nloc + 1], st));  // Eq. 16
+  if (d.lte) EDPC_TRY(linear_fwd(S[d.nloc], d.b, d.F, po.W1, po.b1, d.Fp, nullptr, Xp, st));  // Eq. 14
+  EDPC_TRY(fdm_fwd_call(io, st));  // Eq. 15 (w/o LTE: on S[nloc] into S[nloc + 1])
+  if (d.lte) EDPC_TRY(linear_fwd(Y, d.b, d.Fp, po.W2, po.b2, d.F, nullptr, S[d.nloc + 1], st));  // Eq. 16
   for (int j = d.nloc; j < d.n; ++j) EDPC_TRY(block_fwd(j, S[j + 1], S[j + 2], st));
   EDPC_TRY(linear_fwd(S[d.n + 1], d.b, d.F, po.Wh, po.bh, 256, nullptr, z, st));
   return EDPC_OK;
@@ -502,16 +531,24 @@ int Model::backward_f32(const StepIO& io, cudaStream_t st) {
     EDPC_TRY(block_bwd(j, cur, nxt, st));
     std::swap(cur, nxt);
   }
-  // LTE up (Eq. 16)
-  EDPC_TRY(linear_dw(cur, d.b, d.F, Y, d.Fp, po.W2, st));
-  EDPC_CUDA(launch_colsum(cur, nullptr, d.b, d.F, d.F, G + po.b2, st));
-  EDPC_TRY(linear_dx(cur, d.b, d.F, po.W2, d.Fp, dY, st));
-  // FDM (Eq. 15): adjoint fused with the FDM's Adam update
-  EDPC_TRY(fdm_bwd_call(io, st));
-  // LTE down (Eq. 14)
-  EDPC_TRY(linear_dw(dXp, d.b, d.Fp, S[d.nloc], d.F, po.W1, st));
-  EDPC_CUDA(launch_colsum(dXp, nullptr, d.b, d.Fp, d.Fp, G + po.b1, st));
-  EDPC_TRY(linear_dx(dXp, d.b, d.Fp, po.W1, d.F, cur, st));
+  if (d.lte) {
+    // LTE up (Eq. 16)
+    EDPC_TRY(linear_dw(cur, d.b, d.F, Y, d.Fp, po.W2, st));
+    EDPC_CUDA(launch_colsum(cur, nullptr, d.b, d.F, d.F, G + po.b2, st));
+    EDPC_TRY(linear_dx(cur, d.b, d.F, po.W2, d.Fp, dY, st));
+    // FDM (Eq. 15): adjoint fused with the FDM's Adam update
+    EDPC_TRY(fdm_bwd_call(io, st));
+    // LTE down (Eq. 14)
+    EDPC_TRY(linear_dw(dXp, d.b, d.Fp, S[d.nloc], d.F, po.W1, st));
+    EDPC_CUDA(launch_colsum(dXp, nullptr, d.b, d.Fp, d.Fp, G + po.b1, st));
+    EDPC_TRY(linear_dx(dXp, d.b, d.Fp, po.W1, d.F, cur, st));
+  } else {
+    // w/o LTE: the FDM's adjoint maps the gradient of S[nloc + 1] to that of S[nloc]
+    dY = cur;
+    dXp = nxt;
+    EDPC_TRY(fdm_bwd_call(io, st));
+    std::swap(cur, nxt);
+  }
   for (int j = d.nloc - 1; j >= 0; --j) {
     EDPC_TRY(block_bwd(j, cur, nxt, st));
     std::swap(cur, nxt);
@@ -750,7 +787,7 @@ int Model::build_tc_sites() {
       EDPC_TRY(split_site(id));
     }
   }
-  {  // Eq. 14
+  if (d.lte) {  // Eq. 14
     int bn = bn_rows(kSiteLteDownFwd, Fp);
     EDPC_TRY(site(kSiteLteDownFwd, b, Fp, F, Slte_b, b, F, F, Pb + po.W1, Fp, F, F, bn, bn));
     TcGemm& g = tcp.site[kSiteLteDownFwd];
@@ -758,7 +795,7 @@ int Model::build_tc_sites() {
     g.ldc = Fp;
     g.bias = P + po.b1;
   }
-  {  // Eq. 16
+  if (d.lte) {  // Eq. 16
     int bn = bn_rows(kSiteLteUpFwd, F);
     EDPC_TRY(site(kSiteLteUpFwd, b, F, Fp, Yb, b, Fp, Fp, Pb + po.W2, F, Fp, Fp, bn, bn));
     TcGemm& g = tcp.site[kSiteLteUpFwd];
@@ -794,14 +831,14 @@ int Model::build_tc_sites() {
     g.ldc = F;
     EDPC_TRY(split_site(kSiteHeadDw));
   }
-  {  // LTE up adjoint: dY = dX W2
+  if (d.lte) {  // LTE up adjoint: dY = dX W2
     int bn = bn_rows(kSiteLteUpDx, Fp);
     EDPC_TRY(site(kSiteLteUpDx, b, Fp, F, dLteb, b, F, F, PbT + po.W2, Fp, F, F, bn, bn));
     TcGemm& g = tcp.site[kSiteLteUpDx];
     g.C = dY;
     g.ldc = Fp;
   }
-  {  // dW2 = dX^T Y
+  if (d.lte) {  // dW2 = dX^T Y
     int bn = bn_site(kSiteLteUpDw, Fp);
     EDPC_TRY(site(kSiteLteUpDw, F, Fp, b, dLtebT, F, b, T, YbT, Fp, b, T, bn, bn));
     TcGemm& g = tcp.site[kSiteLteUpDw];
@@ -809,7 +846,7 @@ int Model::build_tc_sites() {
     g.ldc = Fp;
     EDPC_TRY(split_site(kSiteLteUpDw));
   }
-  {  // LTE down adjoint: dX = dX' W1 -> gradient of the last Local block's output
+  if (d.lte) {  // LTE down adjoint: dX = dX' W1 -> gradient of the last Local block's output
     int bn = bn_rows(kSiteLteDownDx, F);
     EDPC_TRY(site(kSiteLteDownDx, b, F, Fp, dXpb, b, Fp, Fp, PbT + po.W1, F, Fp, Fp, bn, bn));
     TcGemm& g = tcp.site[kSiteLteDownDx];
@@ -825,7 +862,7 @@ int Model::build_tc_sites() {
       g.C = dh0;
     }
   }
-  {  // dW1 = dX'^T X
+  if (d.lte) {  // dW1 = dX'^T X
     int bn = bn_site(kSiteLteDownDw, F);
     EDPC_TRY(site(kSiteLteDownDw, Fp, F, b, dXpbT, Fp, b, T, Slte_bT, F, b, T, bn, bn));
     TcGemm& g = tcp.site[kSiteLteDownDw];
@@ -844,7 +881,8 @@ void Model::tunable_sites(std::vector<int>* ids) const {
   ids->clear();
   for (int kind : {BR_FWD, OUT_FWD, OUT_DX, OUT_DW, BR_DX, BR_DW})
     for (int j = 0; j < d.n; ++j) ids->push_back(blk_site(kind, j));
-  for (int id = kSiteLteDownFwd; id <= kSiteLteDownDx; ++id) ids->push_back(id);
+  for (int id = kSiteLteDownFwd; id <= kSiteLteDownDx; ++id)
+    if (d.lte || id == kSiteHeadFwd || id == kSiteHeadDx || id == kSiteHeadDw) ids->push_back(id);
 }
 
 // Tile codes: 0 (size heuristic), or w + v with w in {1, 2, 4, 8} and v in
@@ -1027,9 +1065,9 @@ int Model::forward_bf16(const StepIO& io, cudaStream_t st) {
   if (d.nloc == 0) EDPC_CUDA(launch_to_bf16(S[0], d.b, d.F, d.F, Slte_b, d.F, Slte_bT, d.ldT, st));
   for (int jj = 0; jj < d.n; ++jj) {
     if (jj == d.nloc) {
-      EDPC_TRY(run_tc(kSiteLteDownFwd, st));  // Eq. 14
-      EDPC_TRY(fdm_fwd_call(io, st));             // Eq. 15
-      EDPC_TRY(run_tc(kSiteLteUpFwd, st));    // Eq. 16
+      if (d.lte) EDPC_TRY(run_tc(kSiteLteDownFwd, st));  // Eq. 14
+      EDPC_TRY(fdm_fwd_call(io, st));                      // Eq. 15 (w/o LTE: on S[nloc] into S[nloc + 1])
+      if (d.lte) EDPC_TRY(run_tc(kSiteLteUpFwd, st));    // Eq. 16
     }
     const BlockOff& o = po.blk[jj];
     const float* Xin = S[jj < d.nloc ? jj : jj + 1];
@@ -1040,6 +1078,18 @@ int Model::forward_bf16(const StepIO& io, cudaStream_t st) {
   }
   EDPC_TRY(run_tc(kSiteHeadFwd, st));
   return EDPC_OK;
+}
+
+int Model::fdm_bwd_joined(const StepIO& io, cudaStream_t st) {
+  if (d.b < 2048) return fdm_bwd_call(io, st);
+  // From 2048 streams on the FDM adjoint (milliseconds of HBM-bound
+  // streaming) runs faster alone than beside the side stream's pending
+  // weight gradients, so it waits for them (measured: 6.63 -> 5.81 ms per
+  // step at 4096 streams; at 512 streams the overlap wins).
+  EDPC_CUDA(cudaEventRecord(fdm_join_ev, side));
+  EDPC_CUDA(cudaStreamWaitEvent(st, fdm_join_ev, 0));
+  NoPdl scope;  // two incoming dependencies
+  return fdm_bwd_call(io, st);
 }
 
 int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
@@ -1061,7 +1111,8 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
   for (int j = d.n - 1; j >= 0; --j) {
     const BlockOff& o = po.blk[j];
     BlockBf16& q = bb[j];
-    if (j == d.nloc - 1) {
+    if (j == d.nloc - 1 && !d.lte) EDPC_TRY(fdm_bwd_joined(io, st));  // w/o LTE: the FDM alone
+    if (j == d.nloc - 1 && d.lte) {
       // LTE (Eqs. 14-16) between the Global and the Local blocks
       EDPC_TRY(fork_side(st));
       EDPC_TRY(run_tc(kSiteLteUpDw, side));
@@ -1070,18 +1121,7 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
       cj.n = 1;
       EDPC_TRY(colsums(cj, side));
       EDPC_TRY(run_tc(kSiteLteUpDx, st));
-      if (d.b >= 2048) {
-        // From 2048 streams on the FDM adjoint (milliseconds of HBM-bound
-        // streaming) runs faster alone than beside the side stream's pending
-        // weight gradients, so it waits for them (measured: 6.63 -> 5.81 ms
-        // per step at 4096 streams; at 512 streams the overlap wins).
-        EDPC_CUDA(cudaEventRecord(fdm_join_ev, side));
-        EDPC_CUDA(cudaStreamWaitEvent(st, fdm_join_ev, 0));
-        NoPdl scope;  // two incoming dependencies
-        EDPC_TRY(fdm_bwd_call(io, st));
-      } else {
-        EDPC_TRY(fdm_bwd_call(io, st));
-      }
+      EDPC_TRY(fdm_bwd_joined(io, st));
       EDPC_TRY(fork_side(st));
       EDPC_TRY(run_tc(kSiteLteDownDw, side));
       ColsumJobs cj2{};
@@ -1123,7 +1163,8 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
     EDPC_CUDA(launch_ln_bwd_bf16(q.dX0, ba[j].xhat, ba[j].rstd, P + o.ln_g, q.dOut, out, outb, outbT, d.b, d.F,
                                  d.ldT, st));
   }
-  if (d.nloc == 0) {
+  if (d.nloc == 0 && !d.lte) EDPC_TRY(fdm_bwd_joined(io, st));  // w/o LTE: writes dh0
+  if (d.nloc == 0 && d.lte) {
     // LTE before any Local block: its adjoint runs after the Global blocks.
     EDPC_TRY(fork_side(st));
     EDPC_TRY(run_tc(kSiteLteUpDw, side));

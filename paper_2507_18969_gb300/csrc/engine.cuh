@@ -187,6 +187,7 @@ class Model {
   int colsums(ColsumJobs cj, cudaStream_t st);  // column sums with the model's chunk scratch
   int fdm_fwd_call(const StepIO& io, cudaStream_t st);
   int fdm_bwd_call(const StepIO& io, cudaStream_t st);
+  int fdm_bwd_joined(const StepIO& io, cudaStream_t st);  // waits for the side stream from 2048 streams on
 };
 
 }  // namespace edpc
