@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle model steps for cpu_baseline (0 = auto)")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="also compress the whole workload in FP32, BF16 and FP8 e4m3 (bits/byte, MB/s)")
+    ap.add_argument("--ablation", action="store_true",
+                    help="also compress and decode the whole workload with 3 MBRB branches and without the LTE")
     return ap.parse_args()
 
 
@@ -412,6 +414,41 @@ def run_ours(args, d: Dist):
                 dec.close()
                 assert torch.equal(outd, xd), "FP8 round trip failed"
 
+    # ---- method variants over the whole workload (Table 4 / Table 5 trade-offs) -----------------
+    # The paper's ablations, re-run on the synthetic workload: the default model,
+    # three MBRB branches (Table 5) and no LTE, i.e. a per-stream F x F FDM on the
+    # block output (Table 4); BF16, the whole input compressed and decoded.
+    ablation = None
+    if args.ablation:
+        ablation = {}
+        F = WORKLOAD["context"] * WORKLOAD["embed_dim"]
+        for name, over in (("default", {}), ("mbrb_3_branches", {"branches": 3}), ("without_lte", {"latent": 0})):
+            w = dict(WORKLOAD, **over)
+            cfg = edpc.make_cfg(streams=w["streams"], context=w["context"], embed_dim=w["embed_dim"],
+                                latent=w["latent"], hidden=w["hidden"], blocks=w["blocks"], branches=w["branches"],
+                                lr=w["lr"], precision=edpc.EDPC_BF16, seed=w["seed"])
+            enc = edpc.Encoder(cfg, device_ptr=xd.data_ptr(), length=x.size, stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bits = enc.finish()
+            tt = time.perf_counter() - t0
+            enc.close()
+            _, n, be = edpc.peek(bits)
+            outd = torch.empty(x.size, dtype=torch.uint8, device="cuda")
+            dec = edpc.Decoder(bits, out_device_ptr=outd.data_ptr(), stream=stream.cuda_stream)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            dec.finish(to_host=False)
+            td = time.perf_counter() - t1
+            dec.close()
+            assert torch.equal(outd, xd), f"{name}: round trip failed"
+            del outd
+            fp = w["latent"] or F
+            ablation[name] = {"bits_per_byte": 8 * (len(bits) - (88 + 4 * be + 4)) / n,
+                              "compress_mbs": n / tt / 1e6, "decompress_mbs": n / td / 1e6,
+                              "shared_params": edpc.param_count(cfg), "fdm_params": b * fp * fp,
+                              "branches": w["branches"], "fdm": f"{fp} x {fp} per stream"}
+
     # ---- roofline of the dominant kernel ------------------------------------------------------
     # Per model step the FDM moves 24 B per element in its Adam update (read U,
     # m, v; write U, m, v) and 4 B in each of the forward and the dx' adjoint.
@@ -495,6 +532,8 @@ def run_ours(args, d: Dist):
         }
         if sweep:
             line["precision_sweep"] = sweep
+        if ablation:
+            line["ablation"] = ablation
         print(json.dumps(line), flush=True)
 
 
