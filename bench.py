@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=0, help="oracle model steps for cpu_baseline (0 = auto)")
     ap.add_argument("--precision-sweep", action="store_true",
                     help="also compress the whole workload in FP32, BF16 and FP8 e4m3 (bits/byte, MB/s)")
+    ap.add_argument("--independent", action="store_true",
+                    help="files1000: also compress and decode the sample as an archive of independent per-file models")
     ap.add_argument("--ablation", action="store_true",
                     help="also compress and decode the whole workload with 3 MBRB branches and without the LTE")
     return ap.parse_args()
@@ -598,7 +600,7 @@ def run_files(args, d: Dist):
     fdm_elems_active = int(np.sum(lens > Kc + W * CHUNK)) * w["latent"] ** 2
 
     # ---- e2e and decompress on a sample of the files (host buffers, public API) -------------
-    e2e = decomp = bpb = None
+    e2e = decomp = bpb = indep = None
     if not args.quick:
         sample = files[:w["sample_files"]]
         sb = int(sum(f.size for f in sample))
@@ -620,6 +622,26 @@ def run_files(args, d: Dist):
                "h2d_bytes_total": sb, "d2h_bytes_total": len(bits)}
         decomp = dec_v
         bpb = 8 * len(bits) / sb
+    if not args.quick and args.independent:
+        # the same files as an archive of independent per-file models (each decodes alone)
+        icfg = cfg(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ibits = edpc.compress_independent(sample, icfg, stream_len=int(plan.stream_len), concurrency=16)
+        t_ic = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        iback = edpc.decompress_independent(ibits, concurrency=16)
+        t_id = time.perf_counter() - t0
+        assert all(np.array_equal(a, b) for a, b in zip(sample, iback)), "independent archive round trip failed"
+        big = int(np.argmax([f.size for f in sample]))
+        t0 = time.perf_counter()
+        one = edpc.decompress_member(ibits, big)
+        t_one = time.perf_counter() - t0
+        assert np.array_equal(one, sample[big])
+        indep = {"compress_mbs": sb / t_ic / 1e6, "decompress_mbs": sb / t_id / 1e6, "bits_per_byte": 8 * len(ibits) / sb,
+                 "concurrency": 16, "stream_len": int(plan.stream_len),
+                 "largest_member_alone": {"bytes": int(sample[big].size), "seconds": t_one},
+                 "input": f"edpc_compress_independent of the same {len(sample)} files from host memory"}
 
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -643,6 +665,7 @@ def run_files(args, d: Dist):
                          "open_seconds_with_tile_tuning": t_open},
             "window_bytes": nbytes, "decompress_mbs": decomp, "bits_per_byte": bpb,
             "bits_per_byte_input": "the e2e sample files, whole", "e2e": e2e, "gpu_launches": launches,
+            "independent_models": indep,
             "roofline": {"kernel": "fdm_adam_kernel (FDM update)" if st.fdm_adam_ms else
                          "fdm_bwd_kernel (FDM adjoint + Adam)", "bound": "hbm", "achieved": ach,
                          "peak": peak, "unit": "GB/s", "frac": ach / peak if ach else None, "traffic": None,

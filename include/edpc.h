@@ -298,6 +298,44 @@ int edpc_archive_info(const uint8_t* bits, size_t bits_len, uint64_t* nfiles, ui
 int edpc_decompress_many(const uint8_t* bits, size_t bits_len, uint8_t*** outs, size_t** lens, size_t* nfiles);
 
 /* ------------------------------------------------------------------------ */
+/* Archives of independent per-file models.                                 */
+/* ------------------------------------------------------------------------ */
+/*
+ * A file set in which every file has its own model (the paper codes one
+ * input under one model, Algorithm 1 and Sec. 3.3; an archive whose files
+ * share one model, as edpc_compress_many makes, can only be decoded whole).
+ * File f is compressed exactly as edpc_compress would with cfg->streams =
+ * max(1, ceil(n_f / stream_len)), so each member is a single-input container
+ * and any file decodes alone. The files' sessions run `concurrency` at a time
+ * (0: 8), each on its own CUDA stream, so that the small models' dependent
+ * launches overlap on one GPU.
+ *
+ * Container: "EDPI", u32 format version, u64 file count, u64 stream_len,
+ * per file (u64 member offset, u64 member bytes, u64 file bytes), u32 CRC-32
+ * of the preceding bytes, then the members.
+ *
+ *   edpc_compress_independent  bufs/lens: host arrays of nfiles pointers and
+ *                              sizes (NULL allowed for size 0). out/out_len as
+ *                              for edpc_compress. cfg->streams is ignored.
+ *                              Errors: EINVAL (bad cfg, NULL, stream_len 0),
+ *                              ENOMEM, ECUDA, ETIMEOUT.
+ *   edpc_independent_info      file count and sizes (sizes may be NULL).
+ *                              Errors: ECORRUPT, EVERSION.
+ *   edpc_decompress_member     decodes file `index` alone into a
+ *                              library-allocated buffer (edpc_free).
+ *                              Errors: EINVAL (index), and as edpc_decompress.
+ *   edpc_decompress_independent  every file, `concurrency` at a time; outputs
+ *                              as for edpc_decompress_many.
+ */
+int edpc_compress_independent(const uint8_t* const* bufs, const size_t* lens, size_t nfiles, const edpc_cfg* cfg,
+                              uint64_t stream_len, uint32_t concurrency, uint8_t** out, size_t* out_len);
+int edpc_independent_info(const uint8_t* bits, size_t bits_len, uint64_t* nfiles, uint64_t* sizes);
+int edpc_decompress_member(const uint8_t* bits, size_t bits_len, uint64_t index, uint8_t** out, size_t* out_len);
+int edpc_decompress_independent(const uint8_t* bits, size_t bits_len, uint32_t concurrency, uint8_t*** outs,
+                                size_t** lens, size_t* nfiles);
+
+
+/* ------------------------------------------------------------------------ */
 /* Single kernels on device buffers, for tests and benchmarks.              */
 /* ------------------------------------------------------------------------ */
 

@@ -142,6 +142,64 @@ def decompress_many(bits) -> list[np.ndarray]:
         lib.edpc_free(lens)
 
 
+def compress_independent(files, cfg: Cfg, stream_len: int = 65536, concurrency: int = 8) -> bytes:
+    """Archive of independent per-file models: file f is compressed alone with
+    max(1, ceil(n_f / stream_len)) streams; the sessions run ``concurrency`` at a time."""
+    lib = load()
+    keep, ptrs, lens = _files(files)
+    out = C.c_void_p()
+    n = C.c_size_t()
+    check(lib.edpc_compress_independent(ptrs, lens, len(keep), C.byref(cfg), int(stream_len), int(concurrency),
+                                        C.byref(out), C.byref(n)), "edpc_compress_independent")
+    try:
+        return C.string_at(out, n.value)
+    finally:
+        lib.edpc_free(out)
+
+
+def independent_info(bits) -> list[int]:
+    """File sizes of an archive of independent models."""
+    lib = load()
+    a = _buf(bits)
+    nf = C.c_uint64()
+    check(lib.edpc_independent_info(_ptr(a), a.size, C.byref(nf), C.c_void_p(0)), "edpc_independent_info")
+    sizes = np.zeros(max(1, nf.value), np.uint64)
+    check(lib.edpc_independent_info(_ptr(a), a.size, C.byref(nf), _ptr(sizes)), "edpc_independent_info")
+    return [int(x) for x in sizes[:nf.value]]
+
+
+def decompress_member(bits, index: int) -> np.ndarray:
+    """File ``index`` of an archive of independent models, decoded alone."""
+    lib = load()
+    a = _buf(bits)
+    out = C.c_void_p()
+    n = C.c_size_t()
+    check(lib.edpc_decompress_member(_ptr(a), a.size, int(index), C.byref(out), C.byref(n)), "edpc_decompress_member")
+    try:
+        return np.frombuffer(C.string_at(out, n.value), np.uint8).copy() if n.value else np.zeros(0, np.uint8)
+    finally:
+        lib.edpc_free(out)
+
+
+def decompress_independent(bits, concurrency: int = 8) -> list[np.ndarray]:
+    """Every file of an archive of independent models."""
+    lib = load()
+    a = _buf(bits)
+    outs = C.c_void_p()
+    lens = C.c_void_p()
+    nf = C.c_size_t()
+    check(lib.edpc_decompress_independent(_ptr(a), a.size, int(concurrency), C.byref(outs), C.byref(lens),
+                                          C.byref(nf)), "edpc_decompress_independent")
+    try:
+        ptrs = C.cast(outs, C.POINTER(C.c_void_p))
+        ls = C.cast(lens, C.POINTER(C.c_size_t))
+        return [np.frombuffer(C.string_at(ptrs[i], ls[i]), np.uint8).copy() if ls[i] else np.zeros(0, np.uint8)
+                for i in range(nf.value)]
+    finally:
+        lib.edpc_free(outs)
+        lib.edpc_free(lens)
+
+
 class _Session:
     def __init__(self, handle, keep):
         self._h = handle

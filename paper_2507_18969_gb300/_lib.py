@@ -109,6 +109,12 @@ PROTOS = {
     "edpc_model_set_tiles": (C.c_int, [P, P, C.c_uint32]),
     "edpc_model_tune_tiles": (C.c_int, [P, P, C.c_uint32, C.POINTER(C.c_uint32)]),
     "edpc_model_time_gemms": (C.c_int, [P, C.c_uint32, P, P, P, C.c_uint32, C.POINTER(C.c_uint32)]),
+    "edpc_compress_independent": (C.c_int, [P, P, C.c_size_t, P, C.c_uint64, C.c_uint32, C.POINTER(C.c_void_p),
+                                            C.POINTER(C.c_size_t)]),
+    "edpc_independent_info": (C.c_int, [P, C.c_size_t, C.POINTER(C.c_uint64), P]),
+    "edpc_decompress_member": (C.c_int, [P, C.c_size_t, C.c_uint64, C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
+    "edpc_decompress_independent": (C.c_int, [P, C.c_size_t, C.c_uint32, C.POINTER(C.c_void_p),
+                                              C.POINTER(C.c_void_p), C.POINTER(C.c_size_t)]),
 }
 
 _LIB = None

@@ -1100,6 +1100,234 @@ extern "C" int edpc_decompress_many(const uint8_t* bits, size_t bits_len, uint8_
 }
 
 // ==========================================================================================
+// archives of independent per-file models
+// ==========================================================================================
+// Layout: "EDPI", u32 format version, u64 file count, u64 stream length L,
+// then per file (u64 member offset, u64 member bytes, u64 file bytes), a
+// CRC-32 of everything before it, then the members: member f is the
+// single-input container edpc_compress gives for file f with cfg.streams =
+// max(1, ceil(n_f / L)).
+namespace {
+
+constexpr uint32_t kIndepMagic = 0x49504445u;  // "EDPI"
+constexpr int kIndepChunk = 128;                // model steps queued per session and round
+
+struct IndepTable {
+  uint64_t nfiles = 0, L = 0;
+  std::vector<uint64_t> off, bytes, size;
+  size_t header_len = 0;
+};
+
+size_t indep_header_len(uint64_t nfiles) { return 24 + 24 * (size_t)nfiles + 4; }
+
+int read_indep(const uint8_t* p, size_t n, IndepTable* t) {
+  if (!p || n < 28) return fail(EDPC_ECORRUPT, "archive too short");
+  if (get<uint32_t>(p, 0) != kIndepMagic) return fail(EDPC_ECORRUPT, "not an archive of independent models");
+  if (get<uint32_t>(p, 4) != EDPC_FORMAT_VERSION) return fail(EDPC_EVERSION, "unsupported format version");
+  t->nfiles = get<uint64_t>(p, 8);
+  t->L = get<uint64_t>(p, 16);
+  if (t->nfiles > (n - 28) / 24) return fail(EDPC_ECORRUPT, "archive file table truncated");
+  t->header_len = indep_header_len(t->nfiles);
+  if (crc32_ieee(p, t->header_len - 4) != get<uint32_t>(p, t->header_len - 4))
+    return fail(EDPC_ECORRUPT, "archive header CRC mismatch");
+  t->off.resize(t->nfiles);
+  t->bytes.resize(t->nfiles);
+  t->size.resize(t->nfiles);
+  for (uint64_t f = 0; f < t->nfiles; ++f) {
+    t->off[f] = get<uint64_t>(p, 24 + 24 * f);
+    t->bytes[f] = get<uint64_t>(p, 32 + 24 * f);
+    t->size[f] = get<uint64_t>(p, 40 + 24 * f);
+    if (t->off[f] < t->header_len || t->off[f] > n || t->bytes[f] > n - t->off[f])
+      return fail(EDPC_ECORRUPT, "archive member out of range");
+  }
+  return EDPC_OK;
+}
+
+uint32_t indep_streams(uint64_t n, uint64_t L) {
+  const uint64_t b = (n + L - 1) / L;
+  return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(b, 1), kMaxStreams);
+}
+
+// Runs the sessions of `count` jobs, at most `conc` at a time, each on its
+// own CUDA stream: open(j, stream, &s) opens job j's session, done(j, s)
+// finishes it. Every round queues kIndepChunk model steps on each open
+// session; a session whose steps are all queued is finished (which waits for
+// its own stream only) and its slot reopened on the next job.
+template <class Open, class Done>
+int run_concurrent(size_t count, uint32_t conc, Open open, Done done) {
+  if (conc == 0) conc = 8;
+  conc = (uint32_t)std::min<size_t>(conc, std::max<size_t>(count, 1));
+  std::vector<cudaStream_t> sts(conc, nullptr);
+  std::vector<edpc_session*> ss(conc, nullptr);
+  std::vector<size_t> job(conc, 0);
+  int r = EDPC_OK;
+  for (auto& st : sts)
+    if (r == EDPC_OK && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+      r = fail(EDPC_ECUDA, "stream creation");
+  size_t next = 0, finished = 0;
+  while (r == EDPC_OK && finished < count) {
+    for (uint32_t k = 0; k < conc && r == EDPC_OK; ++k)
+      if (!ss[k] && next < count) {
+        job[k] = next++;
+        r = open(job[k], sts[k], &ss[k]);
+      }
+    for (uint32_t k = 0; k < conc && r == EDPC_OK; ++k) {
+      if (!ss[k]) continue;
+      uint64_t left = 0;
+      r = edpc_session_remaining(ss[k], &left);
+      if (r == EDPC_OK && left > 0) r = edpc_session_run(ss[k], kIndepChunk, 0, nullptr);
+    }
+    for (uint32_t k = 0; k < conc && r == EDPC_OK; ++k) {
+      if (!ss[k]) continue;
+      uint64_t left = 1;
+      r = edpc_session_remaining(ss[k], &left);
+      if (r == EDPC_OK && left == 0) {
+        r = done(job[k], ss[k]);
+        edpc_session_close(ss[k]);
+        ss[k] = nullptr;
+        ++finished;
+      }
+    }
+  }
+  for (uint32_t k = 0; k < conc; ++k) {
+    if (ss[k]) edpc_session_close(ss[k]);
+    if (sts[k]) cudaStreamDestroy(sts[k]);
+  }
+  return r;
+}
+
+}  // namespace
+
+extern "C" int edpc_compress_independent(const uint8_t* const* bufs, const size_t* lens, size_t nfiles,
+                                         const edpc_cfg* cfg, uint64_t stream_len, uint32_t concurrency,
+                                         uint8_t** out, size_t* out_len) {
+  if (!out || !out_len) return fail(EDPC_EINVAL, "NULL output pointer");
+  *out = nullptr;
+  *out_len = 0;
+  if ((!bufs || !lens) && nfiles) return fail(EDPC_EINVAL, "bufs or lens is NULL");
+  if (stream_len == 0) return fail(EDPC_EINVAL, "stream_len must be > 0");
+  edpc_cfg c0 = *cfg;
+  c0.streams = 1;
+  EDPC_TRY(check_cfg(&c0));
+  for (size_t f = 0; f < nfiles; ++f)
+    if (!bufs[f] && lens[f]) return fail(EDPC_EINVAL, "data is NULL");
+  EDPC_TRY(current_device_ok());
+  std::vector<std::vector<uint8_t>> members(nfiles);
+  auto open = [&](size_t f, cudaStream_t st, edpc_session** s) {
+    edpc_cfg c = *cfg;
+    c.streams = indep_streams(lens[f], stream_len);
+    return edpc_encoder_open(&c, bufs[f], lens[f], 0, st, s);
+  };
+  auto done = [&](size_t f, edpc_session* s) {
+    uint8_t* b = nullptr;
+    size_t n = 0;
+    EDPC_TRY(edpc_encoder_finish(s, &b, &n));
+    members[f].assign(b, b + n);
+    free(b);
+    return EDPC_OK;
+  };
+  EDPC_TRY(run_concurrent(nfiles, concurrency, open, done));
+  const size_t hl = indep_header_len(nfiles);
+  size_t total = hl;
+  for (auto& m : members) total += m.size();
+  std::vector<uint8_t> hdr(hl, 0);
+  put<uint32_t>(hdr, 0, kIndepMagic);
+  put<uint32_t>(hdr, 4, EDPC_FORMAT_VERSION);
+  put<uint64_t>(hdr, 8, (uint64_t)nfiles);
+  put<uint64_t>(hdr, 16, stream_len);
+  uint64_t o = hl;
+  for (size_t f = 0; f < nfiles; ++f) {
+    put<uint64_t>(hdr, 24 + 24 * f, o);
+    put<uint64_t>(hdr, 32 + 24 * f, (uint64_t)members[f].size());
+    put<uint64_t>(hdr, 40 + 24 * f, (uint64_t)lens[f]);
+    o += members[f].size();
+  }
+  put<uint32_t>(hdr, hl - 4, crc32_ieee(hdr.data(), hl - 4));
+  uint8_t* buf = static_cast<uint8_t*>(malloc(total));
+  if (!buf) return fail(EDPC_ENOMEM, "output buffer");
+  memcpy(buf, hdr.data(), hl);
+  o = hl;
+  for (auto& m : members) {
+    if (!m.empty()) memcpy(buf + o, m.data(), m.size());
+    o += m.size();
+  }
+  *out = buf;
+  *out_len = total;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_independent_info(const uint8_t* bits, size_t bits_len, uint64_t* nfiles, uint64_t* sizes) {
+  if (!nfiles) return fail(EDPC_EINVAL, "nfiles is NULL");
+  IndepTable t;
+  EDPC_TRY(read_indep(bits, bits_len, &t));
+  *nfiles = t.nfiles;
+  if (sizes && t.nfiles) memcpy(sizes, t.size.data(), 8 * (size_t)t.nfiles);
+  return EDPC_OK;
+}
+
+extern "C" int edpc_decompress_member(const uint8_t* bits, size_t bits_len, uint64_t index, uint8_t** out,
+                                      size_t* out_len) {
+  if (!out || !out_len) return fail(EDPC_EINVAL, "NULL output pointer");
+  IndepTable t;
+  EDPC_TRY(read_indep(bits, bits_len, &t));
+  if (index >= t.nfiles) return fail(EDPC_EINVAL, "member index out of range");
+  uint64_t n = 0;
+  EDPC_TRY(edpc_peek(bits + t.off[index], t.bytes[index], nullptr, &n, nullptr));
+  if (n != t.size[index]) return fail(EDPC_ECORRUPT, "member length does not match the file table");
+  return edpc_decompress(bits + t.off[index], t.bytes[index], out, out_len);
+}
+
+extern "C" int edpc_decompress_independent(const uint8_t* bits, size_t bits_len, uint32_t concurrency,
+                                           uint8_t*** outs, size_t** lens, size_t* nfiles) {
+  if (!outs || !lens || !nfiles) return fail(EDPC_EINVAL, "NULL output pointer");
+  *outs = nullptr;
+  *lens = nullptr;
+  *nfiles = 0;
+  IndepTable t;
+  EDPC_TRY(read_indep(bits, bits_len, &t));
+  for (uint64_t f = 0; f < t.nfiles; ++f) {
+    uint64_t n = 0;
+    EDPC_TRY(edpc_peek(bits + t.off[f], t.bytes[f], nullptr, &n, nullptr));
+    if (n != t.size[f]) return fail(EDPC_ECORRUPT, "member length does not match the file table");
+  }
+  uint64_t total = 0;
+  for (uint64_t v : t.size) total += v;
+  const size_t head = sizeof(uint8_t*) * (size_t)std::max<uint64_t>(t.nfiles, 1);
+  uint8_t* block = static_cast<uint8_t*>(malloc(head + std::max<uint64_t>(total, 1)));
+  size_t* ls = static_cast<size_t*>(malloc(sizeof(size_t) * (size_t)std::max<uint64_t>(t.nfiles, 1)));
+  if (!block || !ls) {
+    free(block);
+    free(ls);
+    return fail(EDPC_ENOMEM, "output buffers");
+  }
+  uint8_t** ptrs = reinterpret_cast<uint8_t**>(block);
+  uint64_t o = 0;
+  for (uint64_t f = 0; f < t.nfiles; ++f) {
+    ptrs[f] = block + head + o;
+    ls[f] = (size_t)t.size[f];
+    o += t.size[f];
+  }
+  int r = EDPC_OK;
+  if (t.nfiles) {
+    EDPC_TRY(current_device_ok());
+    auto open = [&](size_t f, cudaStream_t st, edpc_session** s) {
+      return edpc_decoder_open(bits + t.off[f], t.bytes[f], nullptr, st, s);
+    };
+    auto done = [&](size_t f, edpc_session* s) { return edpc_decoder_finish(s, ptrs[f]); };
+    r = run_concurrent((size_t)t.nfiles, concurrency, open, done);
+  }
+  if (r != EDPC_OK) {
+    free(block);
+    free(ls);
+    return r;
+  }
+  *outs = ptrs;
+  *lens = ls;
+  *nfiles = (size_t)t.nfiles;
+  return EDPC_OK;
+}
+
+// ==========================================================================================
 // single-kernel entry points
 // ==========================================================================================
 extern "C" int edpc_cdf_quantize(const float* p, uint32_t rows, uint32_t* freq, uint32_t* cum, void* stream) {
