@@ -103,3 +103,41 @@ def test_file_set_plan_rejects_too_many_streams(lib):
         pkg.archive_plan([1] * 70000, pkg.make_cfg(streams=65535))
     with pytest.raises(pkg.EdpcError):
         pkg.archive_plan([10, 20], pkg.make_cfg(streams=70000))
+
+
+def _indep(nfiles, members, L=65536, crc_ok=True, magic=0x49504445):
+    """An archive of independent models built by hand (table + members)."""
+    import struct
+    import zlib
+    hl = 24 + 24 * nfiles + 4
+    head = struct.pack("<IIQQ", magic, 1, nfiles, L)
+    o = hl
+    for m, size in members:
+        head += struct.pack("<QQQ", o, len(m), size)
+        o += len(m)
+    crc = zlib.crc32(head) & 0xFFFFFFFF
+    head += struct.pack("<I", crc if crc_ok else crc ^ 1)
+    return head + b"".join(m for m, _ in members)
+
+
+def test_independent_archive_table_is_checked(lib):
+    """The archive reader (host only) accepts a well-formed table and refuses a
+    bad magic, a bad CRC, a truncated table and members out of range."""
+    import paper_2507_18969_gb300 as edpc
+    assert edpc.independent_info(_indep(0, [])) == []
+    assert edpc.independent_info(_indep(2, [(b"ab", 7), (b"", 0)])) == [7, 0]
+    for bad in (_indep(0, [], magic=0x12345678), _indep(1, [(b"xy", 3)], crc_ok=False),
+                _indep(2, [(b"ab", 7), (b"", 0)])[:40]):
+        with pytest.raises(edpc.EdpcError) as e:
+            edpc.independent_info(bad)
+        assert e.value.code == 3  # EDPC_ECORRUPT
+    # a member that runs past the end of the archive
+    import struct
+    import zlib
+    head = struct.pack("<IIQQ", 0x49504445, 1, 1, 4096) + struct.pack("<QQQ", 52, 1000, 5)
+    head += struct.pack("<I", zlib.crc32(head) & 0xFFFFFFFF)
+    with pytest.raises(edpc.EdpcError):
+        edpc.independent_info(head + b"short")
+    with pytest.raises(edpc.EdpcError) as e:
+        edpc.decompress_member(_indep(1, [(b"xy", 3)]), 1)
+    assert e.value.code == 1  # EDPC_EINVAL: index out of range
