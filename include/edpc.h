@@ -474,6 +474,32 @@ int edpc_model_tune_tiles(edpc_model* m, uint8_t* codes, uint32_t cap, uint32_t*
 int edpc_model_time_gemms(edpc_model* m, uint32_t reps, double* ms, double* flop, double* bytes, uint32_t cap,
                           uint32_t* n);
 
+/*
+ * The residual-stream input and output of MBRB `block` (0 .. blocks-1) from
+ * the last edpc_model_forward: the skip S and the fused output S + X^(k) of
+ * Sec. 3.1.1 (Eq. 13: the block adds G W_o^T + c_o to its input). s_in and
+ * s_out are host arrays of streams * F floats (FP32, [stream][feature]).
+ * Errors: EINVAL (NULL, block out of range), ECUDA.
+ */
+int edpc_model_block_io(edpc_model* m, uint32_t block, float* s_in, float* s_out);
+
+/*
+ * Kraskov's k-nearest-neighbour estimate of the mutual information I(Z; Y)
+ * that Sec. 3.1.1 uses to compare branch counts (IFR_{k1->k2} =
+ * I^(k1) / I^(k2)). Z (N x dz) and Y (N x dy) are FP32 row-major device
+ * arrays of paired samples. For each sample i, eps(i) is the k-th smallest
+ * distance max(|z_i - z_j|_inf, |y_i - y_j|_inf) over j != i, and c_z(i),
+ * c_y(i) (written to the device arrays cz, cy of N counts) are the numbers of
+ * j != i strictly closer than eps(i) in z and in y alone; distances and counts
+ * are exact functions of the FP32 samples. *mi (host) receives
+ * psi(k) + psi(N) - mean_i(psi(c_z(i) + 1) + psi(c_y(i) + 1)) in nats, FP64.
+ * Runs on cuda_stream (NULL: the default stream) and waits for it.
+ * Limits: 2 <= N <= 8192, 1 <= k <= min(64, N - 1), dz + dy <= 8192.
+ * Errors: EINVAL, ECUDA.
+ */
+int edpc_ksg_mi(const float* Z, const float* Y, uint32_t N, uint32_t dz, uint32_t dy, uint32_t k, uint32_t* cz,
+                uint32_t* cy, double* mi, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -142,6 +142,16 @@ def decompress_many(bits) -> list[np.ndarray]:
         lib.edpc_free(lens)
 
 
+def ksg_mi(z_dev: int, y_dev: int, n: int, dz: int, dy: int, k: int, cz_dev: int, cy_dev: int,
+           stream: int = 0) -> float:
+    """Kraskov estimate of I(Z; Y) in nats from FP32 device arrays Z (n x dz) and Y (n x dy);
+    the per-sample counts c_z, c_y go to the device arrays cz_dev, cy_dev (n uint32 each)."""
+    mi = C.c_double()
+    check(load().edpc_ksg_mi(C.c_void_p(z_dev), C.c_void_p(y_dev), n, dz, dy, k, C.c_void_p(cz_dev),
+                             C.c_void_p(cy_dev), C.byref(mi), C.c_void_p(stream)), "edpc_ksg_mi")
+    return mi.value
+
+
 def compress_independent(files, cfg: Cfg, stream_len: int = 65536, concurrency: int = 8) -> bytes:
     """Archive of independent per-file models: file f is compressed alone with
     max(1, ceil(n_f / stream_len)) streams; the sessions run ``concurrency`` at a time."""
@@ -384,6 +394,14 @@ class Model:
               "edpc_model_time_gemms")
         k = n.value
         return ms[:k].copy(), fl[:k].copy(), by[:k].copy()
+
+    def block_io(self, block: int):
+        """(S, S + X^(k)) of MBRB ``block`` from the last forward: (streams, F) FP32 arrays."""
+        F = self.cfg.context * self.cfg.embed_dim
+        a = np.empty((self.b, F), np.float32)
+        o = np.empty((self.b, F), np.float32)
+        check(load().edpc_model_block_io(self._h, int(block), _ptr(a), _ptr(o)), "edpc_model_block_io")
+        return a, o
 
     def train_step(self, ctx, targets, active):
         ctx = np.ascontiguousarray(ctx, dtype=np.uint8)

@@ -9,6 +9,13 @@
       Every tcgen05 GEMM site of CASE's model with every tile code set to CODE,
       each launched alone (Model.time_gemms): ms, GFLOP and TFLOP/s per site.
 
+  python -m paper_2507_18969_gb300.cases ifr [STEPS]
+      Sec. 3.1.1's Information Flow Refinement on the 64 MiB mix: models with
+      1, 2 and 3 MBRB branches (c1's dims) each take STEPS online steps on
+      the first bytes of its 512 streams; then, on the next contexts, every
+      block's skip input S and fused output S + X^(k) give I^(k) (Kraskov,
+      3 neighbours, on the GPU), and IFR_{k1->k2} = I^(k1) / I^(k2).
+
 Cases: c1 (K=32, F'=256, 4 MBRBs of 256; 512 streams, the 64 MiB workload's
 model), c1_32k (the same model, 32768 streams), c4 (K=64, F'=512, 6 MBRBs of
 512; 4096 streams, the 1 GiB workload's model) and c4_gemm (c4's F, H and
@@ -66,7 +73,44 @@ def gemm(name: str, code: int) -> list[dict]:
     return [dict(site=int(i), gflop=fl[i] / 1e9, us=ms[i] * 1e3, tflops=fl[i] / ms[i] / 1e9) for i in np.nonzero(fl)[0]]
 
 
+def ifr(steps: int = 256) -> dict:
+    import torch
+    import paper_2507_18969_gb300 as edpc
+    import synth
+    c = CASES["c1"]
+    b, K = c["b"], c["K"]
+    x = synth.multimedia_mix(64 << 20, 20250719)
+    q = x.size // b
+    xs = x[: q * b].reshape(b, q)
+    res = {"steps": steps, "streams": b, "neighbours": 3, "mi_nats": {}, "ifr": {}}
+    for k in (1, 2, 3):
+        cfg = edpc.make_cfg(streams=b, context=K, embed_dim=16, latent=c["Fp"], hidden=c["H"], blocks=c["n"],
+                            branches=k, lr=1e-3, seed=1, precision=edpc.EDPC_BF16)
+        m = edpc.Model(cfg, b)
+        ones = np.ones(b, np.uint8)
+        for i in range(K, K + steps):
+            m.train_step(xs[:, i - K:i], xs[:, i], ones)
+        m.forward(np.ascontiguousarray(xs[:, steps + 1:steps + 1 + K]))
+        mis = []
+        for blk in range(c["n"]):
+            s, so = m.block_io(blk)
+            zs = torch.from_numpy(s).cuda()
+            ys = torch.from_numpy(so).cuda()
+            cz = torch.zeros(b, dtype=torch.int32, device="cuda")
+            cy = torch.zeros(b, dtype=torch.int32, device="cuda")
+            mis.append(edpc.ksg_mi(zs.data_ptr(), ys.data_ptr(), b, s.shape[1], so.shape[1], 3, cz.data_ptr(),
+                                   cy.data_ptr()))
+        m.close()
+        res["mi_nats"][str(k)] = mis
+    for k1, k2 in ((1, 2), (1, 3), (2, 3)):
+        res["ifr"][f"{k1}->{k2}"] = [a / bb for a, bb in zip(res["mi_nats"][str(k1)], res["mi_nats"][str(k2)])]
+    return res
+
+
 def main(argv) -> int:
+    if argv and argv[0] == "ifr":
+        print(json.dumps(ifr(int(argv[1]) if len(argv) > 1 else 256)), flush=True)
+        return 0
     if len(argv) < 2 or argv[0] not in ("steps", "gemm") or argv[1] not in CASES:
         print(__doc__)
         return 2

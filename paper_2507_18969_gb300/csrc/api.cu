@@ -1537,6 +1537,19 @@ extern "C" int edpc_model_time_gemms(edpc_model* mm, uint32_t reps, double* ms, 
   return EDPC_OK;
 }
 
+extern "C" int edpc_model_block_io(edpc_model* mm, uint32_t block, float* s_in, float* s_out) {
+  if (!mm || !s_in || !s_out) return fail(EDPC_EINVAL, "NULL argument");
+  Model& m = mm->m;
+  if (block >= (uint32_t)m.d.n) return fail(EDPC_EINVAL, "block out of range");
+  // residual-stream stages: blocks before the LTE read S[j], the others S[j + 1]
+  const int in = (int)block < m.d.nloc ? (int)block : (int)block + 1;
+  const size_t bytes = (size_t)m.d.b * m.d.F * sizeof(float);
+  EDPC_CUDA(cudaDeviceSynchronize());
+  EDPC_CUDA(cudaMemcpy(s_in, m.S[in], bytes, cudaMemcpyDeviceToHost));
+  EDPC_CUDA(cudaMemcpy(s_out, m.S[in + 1], bytes, cudaMemcpyDeviceToHost));
+  return EDPC_OK;
+}
+
 extern "C" int edpc_model_tune_tiles(edpc_model* mm, uint8_t* codes, uint32_t cap, uint32_t* n) {
   if (!mm) return fail(EDPC_EINVAL, "model is NULL");
   EDPC_TRY(mm->m.tune_tiles(0));
