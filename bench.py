@@ -218,12 +218,12 @@ def prefix_input(x: np.ndarray, per_stream: int, streams: int | None = None) -> 
     return np.ascontiguousarray(x[: q * b].reshape(b, q)[: streams or b, :per_stream]).reshape(-1)
 
 
-def make_cfg(prec):
+def make_cfg(prec, flags=0):
     import paper_2507_18969_gb300 as edpc
     w = WORKLOAD
     return edpc.make_cfg(streams=w["streams"], context=w["context"], embed_dim=w["embed_dim"], latent=w["latent"],
                          hidden=w["hidden"], blocks=w["blocks"], branches=w["branches"], lr=w["lr"],
-                         precision=prec, seed=w["seed"])
+                         precision=prec, seed=w["seed"], flags=flags)
 
 
 def traffic_from_profile(name: str):
@@ -351,7 +351,7 @@ def run_ours(args, d: Dist):
     launches = (st.launches_per_step * done + done // CHUNK) if st.launches_per_step else None
     out.update(value=value, t=t_max, done=done, clocks=ck, stats=st, launches=launches)
 
-    fp32_value = decomp_value = e2e = bpb = None
+    fp32_value = decomp_value = e2e = bpb = nopipe_value = None
     if not args.quick:
         # ---- plain FP32 path, same workload ----------------------------------------------
         enc = edpc.Encoder(make_cfg(edpc.EDPC_FP32), device_ptr=xd.data_ptr(), length=x.size,
@@ -359,6 +359,13 @@ def run_ours(args, d: Dist):
         t32, done32, _ = timed_session(enc, W, K, stream, d)
         enc.close()
         fp32_value, _ = aggregate(done32 * b, t32, d)
+
+        # ---- DPCA off: the coder stage inline on the model stream (Sec. 3.3; Table 4 "w/o pipeline")
+        enc = edpc.Encoder(make_cfg(edpc.EDPC_BF16, edpc.EDPC_FLAG_NO_PIPELINE), device_ptr=xd.data_ptr(),
+                           length=x.size, stream=stream.cuda_stream)
+        tnp, donenp, _ = timed_session(enc, W, K, stream, d)
+        enc.close()
+        nopipe_value, _ = aggregate(donenp * b, tnp, d)
 
         # ---- e2e through edpc_compress on pinned host memory (prefix input) --------------
         per = WORKLOAD["context"] + (W + K + 2) * CHUNK
@@ -527,6 +534,8 @@ def run_ours(args, d: Dist):
                        "parallelism": "replicas" if d.world > 1 else "single"},
             "decompress_mbs": decomp_value, "fp32_compress_mbs": fp32_value,
             "bf16_vs_fp32": (out["value"] / fp32_value) if fp32_value else None,
+            "dpca_off_compress_mbs": nopipe_value,
+            "dpca_speedup": (out["value"] / nopipe_value) if nopipe_value else None,
             "bits_per_byte": bpb,
             "bits_per_byte_input": "the e2e prefix input (early, still-learning part of each stream)",
             "e2e": e2e, "gpu_launches": out["launches"],
