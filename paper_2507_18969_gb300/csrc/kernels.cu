@@ -322,12 +322,9 @@ __global__ void __launch_bounds__(256) fdm_fwd_kernel(const float* __restrict__ 
   }
 }
 
-// Streamed version (F' in {128, 256, 512, 1024}): one CTA per stream pulls U_s
-// through a 3-deep ring of 16 KB TMA bulk copies (consecutive rows are
-// contiguous), so the copy engine keeps ~48 KB per CTA in flight with no
-// per-thread load instructions. Thread t owns columns t, t + NT, ... and sums
-// its rows in increasing i (deterministic, no cross-thread reduction). Every
-// mbarrier wait is bounded; all copies are waited for before the CTA exits.
+// Streamed FDM forward helpers (F' in {128, 256, 512, 1024}): TMA bulk copies
+// of 16 KB (consecutive rows of U_s are contiguous) into a ring of shared
+// memory slots, each with an mbarrier; every wait is bounded.
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -365,66 +362,12 @@ struct FdmRing {
   static constexpr size_t kSmem = (size_t)RING * 16384 + (size_t)FP * 4 + 64;
 };
 
-template <int FP>
-__global__ void __launch_bounds__(FdmRing<FP>::NT)
-    fdm_fwd_ring_kernel(const float* __restrict__ Xp, const float* __restrict__ U, float* __restrict__ Y,
-                        __nv_bfloat16* Yb, __nv_bfloat16* YbT, int ldT, int* err, FdmAct act) {
-  using R = FdmRing<FP>;
-  extern __shared__ __align__(128) float smf[];
-  float* buf = smf;                        // RING x 16 KB
-  float* xs = smf + (size_t)R::RING * 4096;  // FP
-  uint64_t* bars = reinterpret_cast<uint64_t*>(xs + FP);
-  const int s = blockIdx.x, t = threadIdx.x;
-  if (t == 0) {
-    for (int b = 0; b < R::RING; ++b) bar_init(&bars[b]);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  pdl_wait();
-  pdl_launch();
-  if (!fdm_row_active(act, s)) {  // CTA-uniform, before any copy is issued
-    fdm_zero_row(Y, Yb, YbT, ldT, s, FP);
-    return;
-  }
-  const float* Us = U + (size_t)s * FP * FP;
-  if (t == 0)
-    for (int b = 0; b < R::RING; ++b) bulk_load(buf + (size_t)b * 4096, Us + (size_t)b * 4096, 16384u, &bars[b]);
-  for (int i = t; i < FP; i += R::NT) xs[i] = Xp[(size_t)s * FP + i];
-  __syncthreads();
-  float acc[R::CPT];
-#pragma unroll
-  for (int j = 0; j < R::CPT; ++j) acc[j] = 0.f;
-  bool ok = true;
-  for (int st = 0; st < R::NST; ++st) {
-    const int b = st % R::RING;
-    ok = bar_wait(&bars[b], (uint32_t)(st / R::RING) & 1u) && ok;
-    const float* u = buf + (size_t)b * 4096;
-    const float* xv = xs + st * R::SROWS;
-#pragma unroll
-    for (int r = 0; r < R::SROWS; ++r) {
-      const float xr = xv[r];
-#pragma unroll
-      for (int j = 0; j < R::CPT; ++j) acc[j] += xr * u[r * FP + t + j * R::NT];
-    }
-    __syncthreads();  // stage b consumed by every thread
-    if (t == 0 && st + R::RING < R::NST)
-      bulk_load(buf + (size_t)b * 4096, Us + (size_t)(st + R::RING) * 4096, 16384u, &bars[b]);
-  }
-  if (!ok && t == 0 && err) atomicOr(err, 8);
-#pragma unroll
-  for (int j = 0; j < R::CPT; ++j) {
-    const int c = t + j * R::NT;
-    Y[(size_t)s * FP + c] = acc[j];
-    if (Yb) Yb[(size_t)s * FP + c] = __float2bfloat16_rn(acc[j]);
-    if (YbT) YbT[(size_t)c * ldT + s] = __float2bfloat16_rn(acc[j]);
-  }
-}
-
-// Persistent version: kFdmPersistPerSm CTAs per SM walk the streams s =
+// Persistent FDM forward: kFdmPersistPerSm CTAs per SM walk the streams s =
 // blockIdx.x, blockIdx.x + gridDim.x, ...; thread 0 keeps kFdmPersistRing
 // 16 KB copies in flight across stream boundaries (no drain between streams,
-// no partial last wave). Each thread still sums its columns' rows in
-// increasing i, so Y is bit-identical to the one-CTA-per-stream kernel.
+// no partial last wave). Thread t owns columns t, t + NT, ... of the stream's
+// y and sums its rows in increasing i (deterministic, no cross-thread
+// reduction).
 constexpr int kFdmPersistRing = 6;
 constexpr int kFdmPersistPerSm = 2;
 
@@ -524,19 +467,6 @@ cudaError_t launch_fdm_fwd_persist(const float* Xp, const float* U, float* Y, in
   const int g = b < grid ? b : grid;
   return launch_k(fdm_fwd_persist_kernel<FP>, dim3(g), dim3(FdmRing<FP>::NT), smem, st, Xp, U, Y, Yb, YbT, ldT, err,
                   act, b);
-}
-
-template <int FP>
-cudaError_t launch_fdm_fwd_ring(const float* Xp, const float* U, float* Y, int b, __nv_bfloat16* Yb,
-                                __nv_bfloat16* YbT, int ldT, int* err, const FdmAct& act, cudaStream_t st) {
-  const size_t smem = FdmRing<FP>::kSmem;
-  if (smem > 48 * 1024) {
-    cudaError_t e =
-        cudaFuncSetAttribute(fdm_fwd_ring_kernel<FP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  return launch_k(fdm_fwd_ring_kernel<FP>, dim3(b), dim3(FdmRing<FP>::NT), smem, st, Xp, U, Y, Yb, YbT, ldT, err,
-                  act);
 }
 
 cudaError_t launch_fdm_fwd(const float* Xp, const float* U, float* Y, int b, int Fp, cudaStream_t st,
