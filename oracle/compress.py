@@ -20,11 +20,25 @@ Readings:
   * A file set (archive) is cut file by file into streams of at most L
     bytes (``archive_split``); all its streams start together and share the
     model, exactly as the streams of one input do.
+  * Delayed update (``delayed=True``; a schedule outside Algorithm 1, which
+    updates before the next prediction): the gradient of step i is still
+    taken at the parameters theta_i that predicted step i, but it is
+    applied one step later, theta_{i+1} = Adam(theta_i, g_{i-1}), with
+    theta_{K+1} = theta_K (no gradient exists before the first step). The
+    shared parameters and every stream's FDM follow the same rule; the FDM
+    rows updated are those active at step i - 1. Adam's step counter counts
+    applied updates. Encoder and decoder run the same schedule, so the
+    result stays lossless; it lets the adjoint of step i run beside the
+    forward of step i + 1.
 
 Parity: the round trip is an invariant, checked here on every call that
 decodes. The code length is checked against the ideal plus truncation bound,
 and the bits/byte against the closed-form entropy of seeded sources
-(tests/test_oracle_compress.py).
+(tests/test_oracle_compress.py). The delayed schedule is pinned by its
+definition built from independent pieces: no update after the first step,
+the first update equal to Algorithm 1's first, and the second one taken
+from a fresh model's gradient at the stale parameters
+(tests/test_oracle_delayed.py).
 """
 from __future__ import annotations
 
@@ -96,8 +110,23 @@ def _contexts(buf, offsets, rows, i, K):
     return buf[idx]
 
 
+def _update(model: Model, g, dU, rows, pending, delayed: bool):
+    """The optimizer step after a model step; returns the new pending update.
+
+    Algorithm 1: Adam on this step's gradient now. Delayed: Adam on the
+    previous step's gradient (none after the first step), and this step's
+    gradient waits for the next step.
+    """
+    if not delayed:
+        model.adam(g, dU, rows)
+        return None
+    if pending is not None:
+        model.adam(*pending)
+    return (g, dU, rows)
+
+
 def oracle_compress(data, cfg: Config, streams: int, max_steps: int | None = None,
-                    model: Model | None = None, split=None):
+                    model: Model | None = None, split=None, delayed: bool = False):
     """Encodes ``data`` (uint8) with Algorithm 1 over ``streams`` streams.
 
     Returns a dict: ``streams`` (list of bytes), ``b``, ``lengths``,
@@ -107,6 +136,7 @@ def oracle_compress(data, cfg: Config, streams: int, max_steps: int | None = Non
     run, used for timing and for comparing bits/byte on a prefix).
     ``split`` = (b, offsets, lengths) replaces the contiguous split (for
     example ``archive_split`` of a file set; ``streams`` is then ignored).
+    ``delayed`` selects the delayed-update schedule (module header).
     """
     data = np.asarray(data, dtype=np.uint8)
     n = data.size
@@ -121,6 +151,7 @@ def oracle_compress(data, cfg: Config, streams: int, max_steps: int | None = Non
             encs[s].encode(256 * int(data[offsets[s] + i]), 256)
     L = int(lengths.max()) if b else 0
     steps = 0
+    pending = None
     for i in range(K, L):
         if max_steps is not None and steps >= max_steps:
             break
@@ -138,7 +169,7 @@ def oracle_compress(data, cfg: Config, streams: int, max_steps: int | None = Non
         dz[np.arange(len(rows)), x] -= 1.0
         dz /= len(rows)
         g, dU = model.backward(cache, dz)
-        model.adam(g, dU, rows)
+        pending = _update(model, g, dU, rows, pending, delayed)
         steps += 1
     out = [e.finish() for e in encs]
     return dict(streams=out, b=b, lengths=lengths, offsets=offsets,
@@ -147,7 +178,7 @@ def oracle_compress(data, cfg: Config, streams: int, max_steps: int | None = Non
                 model=model, steps=steps)
 
 
-def oracle_decompress(streams, n: int, cfg: Config, b_req: int, split=None) -> np.ndarray:
+def oracle_decompress(streams, n: int, cfg: Config, b_req: int, split=None, delayed: bool = False) -> np.ndarray:
     """Decodes the per-stream bitstreams of ``oracle_compress`` back to ``n`` bytes."""
     K = cfg.context
     b, offsets, lengths = split_streams(n, b_req, K) if split is None else split
@@ -159,6 +190,7 @@ def oracle_decompress(streams, n: int, cfg: Config, b_req: int, split=None) -> n
         for i in range(min(K, int(lengths[s]))):
             buf[offsets[s] + i] = decs[s].decode_uniform()
     L = int(lengths.max()) if b else 0
+    pending = None
     for i in range(K, L):
         rows = np.nonzero(lengths > i)[0]
         ctx = _contexts(buf, offsets, rows, i, K)
@@ -173,5 +205,5 @@ def oracle_decompress(streams, n: int, cfg: Config, b_req: int, split=None) -> n
         dz[np.arange(len(rows)), x] -= 1.0
         dz /= len(rows)
         g, dU = model.backward(cache, dz)
-        model.adam(g, dU, rows)
+        pending = _update(model, g, dU, rows, pending, delayed)
     return buf

@@ -5,8 +5,11 @@ transition row Dirichlet(0.1)); 4 streams; K = 16 context bytes, D = 16,
 LTE latent 128, 2 MBRB blocks of hidden 128; Adam lr 1e-3; T = 2^16;
 32-bit range coder.
 
+With --delayed the oracle runs the delayed-update schedule and writes
+oracle_c0_delayed.json.
+
 Every stored value comes from ``oracle/`` and ``synth/`` only. Run from the
-repository root:  python tests/golden/gen_oracle_c0.py
+repository root:  python tests/golden/gen_oracle_c0.py [--delayed]
 """
 import json
 import os
@@ -30,14 +33,14 @@ CFG = Config(context=16, embed_dim=16, latent=128, hidden=128, blocks=2, branche
              lr=1e-3, seed=MODEL_SEED)
 
 
-def main():
+def main(delayed=False):
     table = synth.markov_table(2, 0.1, DATA_SEED)
     x = synth.markov_bytes(N, 2, 0.1, DATA_SEED, table=table)
     H = synth.markov_entropy_rate(table, 2)
     t0 = time.time()
-    r = oracle_compress(x, CFG, STREAMS)
+    r = oracle_compress(x, CFG, STREAMS, delayed=delayed)
     t1 = time.time()
-    y = oracle_decompress(r["streams"], N, CFG, STREAMS)
+    y = oracle_decompress(r["streams"], N, CFG, STREAMS, delayed=delayed)
     assert np.array_equal(x, y), "oracle round trip failed"
     sizes = [len(s) for s in r["streams"]]
     out = dict(
@@ -54,11 +57,13 @@ def main():
         input_sha_prefix=bytes(x[:64]).hex(),
         oracle_seconds=round(t1 - t0, 1),
     )
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_c0.json")
+    if delayed:
+        out["schedule"] = "delayed update (gradient of step i applied after step i + 1)"
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_c0_delayed.json" if delayed else "oracle_c0.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps({k: out[k] for k in ("bits_per_byte", "entropy_rate_bits", "oracle_seconds")}))
 
 
 if __name__ == "__main__":
-    main()
+    main(delayed="--delayed" in sys.argv[1:])

@@ -9,8 +9,11 @@ input of 512 * 224 bytes whose balanced 512-stream split is exactly those
 prefixes. Model: K = 32, D = 16, F' = 256, 4 MBRBs of hidden 256, 2
 branches, Adam lr 1e-3, seed 1.
 
+With --delayed the oracle runs the delayed-update schedule and writes
+oracle_mix_prefix_delayed.json.
+
 Every stored value comes from ``oracle/`` and ``synth/`` only. Run from the
-repository root:  python tests/golden/gen_oracle_mix_prefix.py
+repository root:  python tests/golden/gen_oracle_mix_prefix.py [--delayed]
 """
 import json
 import os
@@ -40,10 +43,10 @@ def prefix_input():
     return np.ascontiguousarray(x[: q * STREAMS].reshape(STREAMS, q)[:, :per]).reshape(-1)
 
 
-def main():
+def main(delayed=False):
     xp = prefix_input()
     t0 = time.time()
-    r = oracle_compress(xp, CFG, STREAMS)
+    r = oracle_compress(xp, CFG, STREAMS, delayed=delayed)
     t1 = time.time()
     sizes = [len(s) for s in r["streams"]]
     out = dict(
@@ -57,11 +60,13 @@ def main():
         input_sha_prefix=bytes(xp[:64]).hex(),
         oracle_seconds=round(t1 - t0, 1),
     )
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_mix_prefix.json")
+    if delayed:
+        out["schedule"] = "delayed update (gradient of step i applied after step i + 1)"
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_mix_prefix_delayed.json" if delayed else "oracle_mix_prefix.json")
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     print(json.dumps({k: out[k] for k in ("bits_per_byte", "code_bytes", "oracle_seconds")}))
 
 
 if __name__ == "__main__":
-    main()
+    main(delayed="--delayed" in sys.argv[1:])
