@@ -351,7 +351,7 @@ def run_ours(args, d: Dist):
     launches = (st.launches_per_step * done + done // CHUNK) if st.launches_per_step else None
     out.update(value=value, t=t_max, done=done, clocks=ck, stats=st, launches=launches)
 
-    fp32_value = decomp_value = e2e = bpb = nopipe_value = None
+    fp32_value = decomp_value = e2e = bpb = nopipe_value = delayed_value = bpb_delayed = None
     if not args.quick:
         # ---- plain FP32 path, same workload ----------------------------------------------
         enc = edpc.Encoder(make_cfg(edpc.EDPC_FP32), device_ptr=xd.data_ptr(), length=x.size,
@@ -366,6 +366,13 @@ def run_ours(args, d: Dist):
         tnp, donenp, _ = timed_session(enc, W, K, stream, d)
         enc.close()
         nopipe_value, _ = aggregate(donenp * b, tnp, d)
+
+        # ---- delayed-update schedule: the adjoint of step i beside the forward of step i + 1
+        enc = edpc.Encoder(make_cfg(edpc.EDPC_BF16, edpc.EDPC_FLAG_DELAYED_UPDATE), device_ptr=xd.data_ptr(),
+                           length=x.size, stream=stream.cuda_stream)
+        tdl, donedl, _ = timed_session(enc, W, K, stream, d)
+        enc.close()
+        delayed_value, _ = aggregate(donedl * b, tdl, d)
 
         # ---- e2e through edpc_compress on pinned host memory (prefix input) --------------
         per = WORKLOAD["context"] + (W + K + 2) * CHUNK
@@ -392,6 +399,8 @@ def run_ours(args, d: Dist):
                "input": f"first {per} bytes of each of the {b} streams ({xp.size} bytes), host pinned"}
         _, n, be = edpc.peek(bits)
         bpb = 8 * (len(bits) - (88 + 4 * be + 4)) / n
+        bits_dl = edpc.compress(xp, make_cfg(edpc.EDPC_BF16, edpc.EDPC_FLAG_DELAYED_UPDATE))
+        bpb_delayed = 8 * (len(bits_dl) - (88 + 4 * be + 4)) / n
 
         # ---- decompress, device-resident output, same prefix input ------------------------
         outd = torch.empty(xp.size, dtype=torch.uint8, device="cuda")
@@ -536,6 +545,11 @@ def run_ours(args, d: Dist):
             "bf16_vs_fp32": (out["value"] / fp32_value) if fp32_value else None,
             "dpca_off_compress_mbs": nopipe_value,
             "dpca_speedup": (out["value"] / nopipe_value) if nopipe_value else None,
+            "delayed_update": ({"compress_mbs": delayed_value, "speedup": delayed_value / out["value"],
+                                "bits_per_byte": bpb_delayed,
+                                "schedule": "gradient of step i applied after step i + 1; its adjoint runs beside "
+                                            "the forward pass of step i + 1 on a second stream (not Algorithm 1)"}
+                               if delayed_value else None),
             "bits_per_byte": bpb,
             "bits_per_byte_input": "the e2e prefix input (early, still-learning part of each stream)",
             "e2e": e2e, "gpu_launches": out["launches"],

@@ -68,6 +68,19 @@ extern "C" {
                                      the step and the next step's first layers (same
                                      results; slower on GB300 at the measured sizes,
                                      kept for comparison) */
+#define EDPC_FLAG_DELAYED_UPDATE 16u
+                                  /* FP32/BF16: delayed-update schedule, a variant of
+                                     Algorithm 1 (which updates before the next
+                                     prediction): the gradient of step i, taken at the
+                                     parameters that predicted step i, is applied after
+                                     step i + 1, theta_{i+1} = Adam(theta_i, g_{i-1}), for
+                                     the shared parameters and the FDMs alike. The adjoint
+                                     of step i then runs beside the forward pass of step
+                                     i + 1 on a second CUDA stream, in the encoder and the
+                                     decoder. A different bitstream from the default
+                                     schedule, still lossless; recorded in the header.
+                                     Needs twice the parameter, FDM and activation memory.
+                                     Not with EDPC_FLAG_OVERLAP_FDM, FP8 or the model API. */
 
 /*
  * Model and coder configuration. Everything here that changes the bitstream

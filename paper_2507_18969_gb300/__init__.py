@@ -12,12 +12,12 @@ import ctypes as C
 
 import numpy as np
 
-from ._lib import (EDPC_BF16, EDPC_FP8E4M3, EDPC_FLAG_NO_GRAPH, EDPC_FLAG_OVERLAP_FDM, EDPC_FLAG_NO_PIPELINE, EDPC_FLAG_TUNE_TILES, EDPC_FP32, Cfg,
+from ._lib import (EDPC_BF16, EDPC_FP8E4M3, EDPC_FLAG_DELAYED_UPDATE, EDPC_FLAG_NO_GRAPH, EDPC_FLAG_OVERLAP_FDM, EDPC_FLAG_NO_PIPELINE, EDPC_FLAG_TUNE_TILES, EDPC_FP32, Cfg,
                    EdpcError, SplitPlan, Stats, check, load)
 
 __all__ = [
     "Cfg", "EdpcError", "EDPC_FP32", "EDPC_BF16", "EDPC_FP8E4M3", "EDPC_FLAG_NO_PIPELINE", "EDPC_FLAG_NO_GRAPH",
-    "EDPC_FLAG_TUNE_TILES", "EDPC_FLAG_OVERLAP_FDM", "make_cfg", "compress", "decompress", "peek", "param_count", "Encoder", "Decoder",
+    "EDPC_FLAG_TUNE_TILES", "EDPC_FLAG_OVERLAP_FDM", "EDPC_FLAG_DELAYED_UPDATE", "make_cfg", "compress", "decompress", "peek", "param_count", "Encoder", "Decoder",
     "Model", "archive_plan", "compress_many", "decompress_many", "archive_info", "SplitPlan",
     "cdf_quantize", "range_encode", "range_encode_noalloc", "NOALLOC_MAX_STREAMS", "load",
 ]

@@ -20,6 +20,7 @@ EDPC_FLAG_NO_PIPELINE = 1
 EDPC_FLAG_NO_GRAPH = 2
 EDPC_FLAG_TUNE_TILES = 4
 EDPC_FLAG_OVERLAP_FDM = 8
+EDPC_FLAG_DELAYED_UPDATE = 16
 
 STATUS = {0: "EDPC_OK", 1: "EDPC_EINVAL", 2: "EDPC_ENOMEM", 3: "EDPC_ECORRUPT", 4: "EDPC_EVERSION",
           5: "EDPC_ECUDA", 6: "EDPC_ETIMEOUT", 7: "EDPC_EARCH"}

@@ -83,6 +83,11 @@ static int check_cfg(const edpc_cfg* c, bool auto_streams = false) {
   if (!(c->lr > 0.f) || !std::isfinite(c->lr)) return fail(EDPC_EINVAL, "lr must be finite and > 0");
   if (c->precision != EDPC_FP32 && c->precision != EDPC_BF16 && c->precision != EDPC_FP8E4M3)
     return fail(EDPC_EINVAL, "unknown precision");
+  if (c->flags & EDPC_FLAG_DELAYED_UPDATE) {
+    if (c->precision == EDPC_FP8E4M3) return fail(EDPC_EINVAL, "the delayed update needs FP32 or BF16");
+    if (c->flags & EDPC_FLAG_OVERLAP_FDM)
+      return fail(EDPC_EINVAL, "the delayed update and EDPC_FLAG_OVERLAP_FDM exclude each other");
+  }
   return EDPC_OK;
 }
 
@@ -162,6 +167,7 @@ __global__ void gather_streams_kernel(const uint8_t* __restrict__ src, const uns
 // container header
 // ------------------------------------------------------------------------------------------
 constexpr uint32_t kMagic = 0x43504445u;  // "EDPC" little-endian
+constexpr uint32_t kSchedDelayed = 1u;     // header word 11: the delayed-update schedule
 constexpr size_t kFixedHeader = 88;
 
 // Variant 0: one input, balanced split, size-heuristic GEMM tiles.
@@ -211,7 +217,7 @@ std::vector<uint8_t> write_header(const Header& h) {
   put<uint32_t>(v, 32, h.cfg.blocks);
   put<uint32_t>(v, 36, h.cfg.branches);
   put<float>(v, 40, h.cfg.lr);
-  put<uint32_t>(v, 44, 0);
+  put<uint32_t>(v, 44, (h.cfg.flags & EDPC_FLAG_DELAYED_UPDATE) ? kSchedDelayed : 0u);  // update schedule
   put<uint64_t>(v, 48, h.cfg.seed);
   put<uint64_t>(v, 56, h.n);
   put<uint32_t>(v, 64, h.cfg.streams);
@@ -271,6 +277,9 @@ int read_header(const uint8_t* p, size_t n, Header* h) {
   h->cfg.blocks = get<uint32_t>(p, 32);
   h->cfg.branches = get<uint32_t>(p, 36);
   h->cfg.lr = get<float>(p, 40);
+  const uint32_t sched = get<uint32_t>(p, 44);
+  if (sched & ~kSchedDelayed) return fail(EDPC_EARCH, "unknown update schedule " + std::to_string(sched));
+  if (sched & kSchedDelayed) h->cfg.flags |= EDPC_FLAG_DELAYED_UPDATE;
   h->cfg.seed = get<uint64_t>(p, 48);
   h->n = get<uint64_t>(p, 56);
   h->cfg.streams = get<uint32_t>(p, 64);
@@ -500,6 +509,7 @@ int edpc_session::capture(int nsteps, int set0, cudaGraph_t* g) {
   int r = EDPC_OK;
   for (int k = 0; k < nsteps && r == EDPC_OK; ++k) {
     for (int q = 0; q < kEv; ++q) model.ev_fdm[q] = tev[set0 + k][q];
+    io.tick = k;  // graphs start at even steps
     r = model.step(io, st);
   }
   if (r == EDPC_OK) r = model.flush(st);
@@ -583,11 +593,12 @@ int edpc_session::launch_steps(uint64_t n) {
       const int p = (int)((j / chunk) % 2);
       if (profiling)
         for (int q = 0; q < chunk; ++q) EDPC_TRY(harvest(p * chunk + q));
+      EDPC_TRY(model.flush(st));  // an eager step's FDM update may still run on its own stream
       EDPC_CUDA(cudaGraphLaunch(x_chunk[p], st));
       if (profiling)
         for (int q = 0; q < chunk; ++q) tev_live[p * chunk + q] = true;
       adv = (uint64_t)chunk;
-    } else if (x_one) {
+    } else if (x_one && !model.delayed) {  // (the delayed update alternates parities: eager)
       const int set = 2 * kChunk;
       if (profiling) EDPC_TRY(harvest(set));
       EDPC_CUDA(cudaGraphLaunch(x_one, st));
@@ -599,6 +610,7 @@ int edpc_session::launch_steps(uint64_t n) {
         for (int q = 0; q < kEv; ++q) model.ev_fdm[q] = tev[set][q];
         model.timing = true;
       }
+      io.tick = (int)(j & 1);
       int r = model.step(io, st);
       model.timing = false;
       if (r != EDPC_OK) return r;
@@ -758,9 +770,11 @@ extern "C" int edpc_session_remaining(const edpc_session* s, uint64_t* left) {
 }
 
 static int check_device_errors(edpc_session* s) {
-  StepCtl c;
-  EDPC_CUDA(cudaMemcpyAsync(&c, s->model.ctl, sizeof(c), cudaMemcpyDeviceToHost, s->st));
+  StepCtl c, c2;
+  EDPC_CUDA(cudaMemcpyAsync(&c, s->model.ctl_of(0), sizeof(c), cudaMemcpyDeviceToHost, s->st));
+  EDPC_CUDA(cudaMemcpyAsync(&c2, s->model.ctl_of(1), sizeof(c2), cudaMemcpyDeviceToHost, s->st));
   EDPC_CUDA(cudaStreamSynchronize(s->st));
+  c.err |= c2.err;
   if (c.err & kErrTcTimeout) return fail(EDPC_ETIMEOUT, "a tensor-core GEMM wait expired");
   if (c.err) return fail(EDPC_ECUDA, "device error flags " + std::to_string(c.err));
   return EDPC_OK;
@@ -1402,6 +1416,8 @@ extern "C" int edpc_model_create(const edpc_cfg* cfg, uint32_t streams, edpc_mod
   *out = nullptr;
   EDPC_TRY(check_cfg(cfg));
   if (streams < 1 || streams > kMaxStreams) return fail(EDPC_EINVAL, "streams must be in [1, 65535]");
+  if (cfg->flags & EDPC_FLAG_DELAYED_UPDATE)
+    return fail(EDPC_EINVAL, "the model API runs Algorithm 1's schedule (no EDPC_FLAG_DELAYED_UPDATE)");
   EDPC_TRY(current_device_ok());
   edpc_model* m = new (std::nothrow) edpc_model();
   if (!m) return fail(EDPC_ENOMEM, "host allocation failed");

@@ -136,8 +136,11 @@ Model::~Model() {
   if (fdm_join_ev) cudaEventDestroy(fdm_join_ev);
   if (dx_ev) cudaEventDestroy(dx_ev);
   if (adam_ev) cudaEventDestroy(adam_ev);
+  if (tick_ev) cudaEventDestroy(tick_ev);
+  if (bwd_ev) cudaEventDestroy(bwd_ev);
   if (side) cudaStreamDestroy(side);
   if (side_fdm) cudaStreamDestroy(side_fdm);
+  if (bwd_st) cudaStreamDestroy(bwd_st);
   if (gU) cudaFree(gU);
   if (f8_arena) cudaFree(f8_arena);
   if (arena_) cudaFree(arena_);
@@ -176,16 +179,17 @@ int Model::init(const edpc_cfg& cfg, int streams) {
   }
   ntiles = (int)th.size();
 
-  for (int pass = 0; pass < 2; ++pass) {
-    Arena a;
-    a.base = static_cast<char*>(arena_);
+  delayed = (cfg.flags & EDPC_FLAG_DELAYED_UPDATE) != 0;
+  const int npar = delayed ? 2 : 1;
+  // The FDM update on its own stream (fdm_dx now, fdm_adam beside the next
+  // layers, from copies of x' and dy): optional for Algorithm 1's schedule,
+  // always for the delayed update, where it leaves the adjoint's critical path.
+  const bool split = overlap || delayed;
+  // what the forward pass and the head write, the parameters, the FDMs and the
+  // step control: one copy, or one per parity for the delayed update
+  auto take_parity = [&](Arena& a) {
     P = a.take<float>(nparam);
-    G = a.take<float>(nparam);
-    M = a.take<float>(nparam);
-    V = a.take<float>(nparam);
     U = a.take<float>(fdm);
-    Um = a.take<float>(fdm);
-    Uv = a.take<float>(fdm);
     ctl = a.take<StepCtl>(1);
     ctx = a.take<uint8_t>((size_t)d.b * d.K);
     for (int s = 0; s < d.n + 2; ++s) S[s] = a.take<float>(bF);
@@ -203,13 +207,45 @@ int Model::init(const edpc_cfg& cfg, int streams) {
     z = a.take<float>((size_t)d.b * 256);
     p = a.take<float>((size_t)d.b * 256);
     dz = a.take<float>((size_t)d.b * 256);
-    dY = a.take<float>(bFp);
-    dXp = a.take<float>(bFp);
-    if (overlap) {  // the FDM update runs on its own stream from these copies
+    if (split) {
       xp_pend = a.take<float>(bFp);
       dy_pend = a.take<float>(bFp);
       pend = a.take<FdmPend>(1);
     }
+    if (bf16) {
+      Pb = a.take<__nv_bfloat16>(nparam);
+      PbT = a.take<__nv_bfloat16>(nparam);
+      for (int j = 0; j < d.n; ++j) {
+        bb[j].X0b = a.take<__nv_bfloat16>(bF);
+        bb[j].X0bT = a.take<__nv_bfloat16>((size_t)d.F * T);
+        bb[j].Gb = a.take<__nv_bfloat16>(bH);
+        bb[j].GbT = a.take<__nv_bfloat16>((size_t)d.H * T);
+      }
+      Slte_b = a.take<__nv_bfloat16>(bF);
+      Slte_bT = a.take<__nv_bfloat16>((size_t)d.F * T);
+      Shead_b = a.take<__nv_bfloat16>(bF);
+      Shead_bT = a.take<__nv_bfloat16>((size_t)d.F * T);
+      Yb = a.take<__nv_bfloat16>(bFp);
+      YbT = a.take<__nv_bfloat16>((size_t)d.Fp * T);
+      dzb = a.take<__nv_bfloat16>((size_t)d.b * 256);
+      dzbT = a.take<__nv_bfloat16>((size_t)256 * T);
+    }
+  };
+
+  for (int pass = 0; pass < 2; ++pass) {
+    Arena a;
+    a.base = static_cast<char*>(arena_);
+    for (int q = 0; q < npar; ++q) {
+      take_parity(a);
+      save_parity(q);
+    }
+    G = a.take<float>(nparam);
+    M = a.take<float>(nparam);
+    V = a.take<float>(nparam);
+    Um = a.take<float>(fdm);
+    Uv = a.take<float>(fdm);
+    dY = a.take<float>(bFp);
+    dXp = a.take<float>(bFp);
     if (embed_bwd_chunks(d.b, d.K) > 1) {
       emb_part = a.take<float>((size_t)256 * embed_bwd_chunks(d.b, d.K) * d.D);
       emb_cnt = a.take<unsigned>(256);
@@ -242,15 +278,9 @@ int Model::init(const edpc_cfg& cfg, int streams) {
       dA = a.take<float>(bkH);
       dG = a.take<float>(bH);
     } else {
-      Pb = a.take<__nv_bfloat16>(nparam);
-      PbT = a.take<__nv_bfloat16>(nparam);
       tiles = a.take<TransposeTile>(std::max(1, ntiles));
       for (int j = 0; j < d.n; ++j) {
         BlockBf16& q = bb[j];
-        q.X0b = a.take<__nv_bfloat16>(bF);
-        q.X0bT = a.take<__nv_bfloat16>((size_t)d.F * T);
-        q.Gb = a.take<__nv_bfloat16>(bH);
-        q.GbT = a.take<__nv_bfloat16>((size_t)d.H * T);
         q.dOut = a.take<float>(bF);
         q.dOutb = a.take<__nv_bfloat16>(bF);
         q.dOutbT = a.take<__nv_bfloat16>((size_t)d.F * T);
@@ -259,14 +289,6 @@ int Model::init(const edpc_cfg& cfg, int streams) {
         q.dAbT = a.take<__nv_bfloat16>((size_t)kH * T);
         q.dX0 = a.take<float>(bF);
       }
-      Slte_b = a.take<__nv_bfloat16>(bF);
-      Slte_bT = a.take<__nv_bfloat16>((size_t)d.F * T);
-      Shead_b = a.take<__nv_bfloat16>(bF);
-      Shead_bT = a.take<__nv_bfloat16>((size_t)d.F * T);
-      Yb = a.take<__nv_bfloat16>(bFp);
-      YbT = a.take<__nv_bfloat16>((size_t)d.Fp * T);
-      dzb = a.take<__nv_bfloat16>((size_t)d.b * 256);
-      dzbT = a.take<__nv_bfloat16>((size_t)256 * T);
       dLte = a.take<float>(bF);
       dLteb = a.take<__nv_bfloat16>(bF);
       dLtebT = a.take<__nv_bfloat16>((size_t)d.F * T);
@@ -288,9 +310,14 @@ int Model::init(const edpc_cfg& cfg, int streams) {
     // first Global block's input; in BF16 mode its adjoint reads that input's
     // gradient and writes the last Local block's output gradient and its BF16
     // copies (the FP32 adjoint sets dY and dXp per step).
-    Xp = S[d.nloc];
-    Y = S[d.nloc + 1];
-    Yb = YbT = nullptr;
+    for (int q = 0; q < npar; ++q) {
+      par[q].Xp = par[q].S[d.nloc];
+      par[q].Y = par[q].S[d.nloc + 1];
+      par[q].Yb = par[q].YbT = nullptr;
+    }
+  }
+  select(0);
+  if (!d.lte) {
     if (bf16) {
       dY = dLte;
       if (d.nloc > 0) {
@@ -335,30 +362,123 @@ int Model::init(const edpc_cfg& cfg, int streams) {
   for (size_t tid = 0; tid < ts.size(); ++tid)
     EDPC_CUDA(launch_init_values(P + ts[tid].off, ts[tid].n, seed, (int)tid, ts[tid].bound, 0, ts[tid].fill, st));
   EDPC_CUDA(launch_init_values(U, fdm, seed, kFdmTid, (float)std::sqrt(3.0 / Fp), 0, 0.f, st));
+  // Stream priorities (the default is the least): with the delayed update the
+  // adjoint's streams go first and the FDM update last.
+  int prio_least = 0, prio_greatest = 0;
+  EDPC_CUDA(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest));
   if (bf16) {
     if (ntiles) EDPC_CUDA(cudaMemcpyAsync(tiles, th.data(), th.size() * sizeof(TransposeTile), cudaMemcpyHostToDevice, st));
     EDPC_TRY(refresh_bf16_weights(st));
     EDPC_TRY(build_tc_plan());
-    EDPC_CUDA(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking));
-    if (overlap) {
-      EDPC_CUDA(cudaStreamCreateWithFlags(&side_fdm, cudaStreamNonBlocking));
-      EDPC_CUDA(cudaEventCreateWithFlags(&dx_ev, cudaEventDisableTiming));
-      EDPC_CUDA(cudaEventCreateWithFlags(&adam_ev, cudaEventDisableTiming));
-    }
+    EDPC_CUDA(cudaStreamCreateWithPriority(&side, cudaStreamNonBlocking, delayed ? prio_greatest : prio_least));
     for (auto& e : fork) EDPC_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     EDPC_CUDA(cudaEventCreateWithFlags(&join_ev, cudaEventDisableTiming));
     EDPC_CUDA(cudaEventCreateWithFlags(&tr_ev, cudaEventDisableTiming));
     EDPC_CUDA(cudaEventCreateWithFlags(&fdm_join_ev, cudaEventDisableTiming));
   }
+  if (split) {
+    EDPC_CUDA(cudaStreamCreateWithPriority(&side_fdm, cudaStreamNonBlocking, prio_least));
+    EDPC_CUDA(cudaEventCreateWithFlags(&dx_ev, cudaEventDisableTiming));
+    EDPC_CUDA(cudaEventCreateWithFlags(&adam_ev, cudaEventDisableTiming));
+  }
+  if (delayed) {
+    // the adjoint (the longer of the two chains of a step) and its side stream first
+    EDPC_CUDA(cudaStreamCreateWithPriority(&bwd_st, cudaStreamNonBlocking, prio_greatest));
+    EDPC_CUDA(cudaEventCreateWithFlags(&tick_ev, cudaEventDisableTiming));
+    EDPC_CUDA(cudaEventCreateWithFlags(&bwd_ev, cudaEventDisableTiming));
+  }
   EDPC_CUDA(cudaStreamSynchronize(st));
   return EDPC_OK;
+}
+
+void Model::save_parity(int q) {
+  Parity& r = par[q];
+  r.P = P;
+  r.U = U;
+  r.Pb = Pb;
+  r.PbT = PbT;
+  r.ctl = ctl;
+  r.ctx = ctx;
+  for (int s = 0; s < kMaxBlocks + 2; ++s) r.S[s] = S[s];
+  for (int j = 0; j < kMaxBlocks; ++j) {
+    r.ba[j] = ba[j];
+    r.X0b[j] = bb[j].X0b;
+    r.X0bT[j] = bb[j].X0bT;
+    r.Gb[j] = bb[j].Gb;
+    r.GbT[j] = bb[j].GbT;
+  }
+  r.Slte_b = Slte_b;
+  r.Slte_bT = Slte_bT;
+  r.Shead_b = Shead_b;
+  r.Shead_bT = Shead_bT;
+  r.Yb = Yb;
+  r.YbT = YbT;
+  r.dzb = dzb;
+  r.dzbT = dzbT;
+  r.Xp = Xp;
+  r.Y = Y;
+  r.z = z;
+  r.p = p;
+  r.dz = dz;
+  r.xp_pend = xp_pend;
+  r.dy_pend = dy_pend;
+  r.pend = pend;
+}
+
+void Model::select(int q) {
+  const Parity& r = par[q];
+  P = r.P;
+  U = r.U;
+  Pb = r.Pb;
+  PbT = r.PbT;
+  ctl = r.ctl;
+  ctx = r.ctx;
+  for (int s = 0; s < kMaxBlocks + 2; ++s) S[s] = r.S[s];
+  for (int j = 0; j < kMaxBlocks; ++j) {
+    ba[j] = r.ba[j];
+    bb[j].X0b = r.X0b[j];
+    bb[j].X0bT = r.X0bT[j];
+    bb[j].Gb = r.Gb[j];
+    bb[j].GbT = r.GbT[j];
+  }
+  Slte_b = r.Slte_b;
+  Slte_bT = r.Slte_bT;
+  Shead_b = r.Shead_b;
+  Shead_bT = r.Shead_bT;
+  Yb = r.Yb;
+  YbT = r.YbT;
+  dzb = r.dzb;
+  dzbT = r.dzbT;
+  Xp = r.Xp;
+  Y = r.Y;
+  z = r.z;
+  p = r.p;
+  dz = r.dz;
+  xp_pend = r.xp_pend;
+  dy_pend = r.dy_pend;
+  pend = r.pend;
+  U_base = delayed ? par[q ^ 1].U : nullptr;
+  cur = q;
 }
 
 int Model::set_ctl_for_step(int i, int t, int bact, int ring_slots, cudaStream_t st) {
   int slot = ring_slots > 0 ? (int)(((long long)i - d.K) % ring_slots) : 0;
   if (slot < 0) slot = 0;
-  set_ctl_kernel<<<1, 1, 0, st>>>(ctl, i, t, bact, slot, lr);
-  EDPC_CUDA(cudaGetLastError());
+  if (!delayed) {
+    set_ctl_kernel<<<1, 1, 0, st>>>(ctl, i, t, bact, slot, lr);
+    EDPC_CUDA(cudaGetLastError());
+    return EDPC_OK;
+  }
+  // Delayed update: both parities start at the first step. The first step's
+  // adjoint runs on parity 1 with a zero head gradient (every gradient is then
+  // zero), so its updates copy parity 0's parameters and FDMs exactly.
+  for (int q = 0; q < 2; ++q) {
+    set_ctl_kernel<<<1, 1, 0, st>>>(par[q].ctl, i, t, bact, slot, lr);
+    EDPC_CUDA(cudaGetLastError());
+  }
+  EDPC_CUDA(cudaMemsetAsync(par[1].dz, 0, sizeof(float) * d.b * 256, st));
+  if (par[1].dzb) EDPC_CUDA(cudaMemsetAsync(par[1].dzb, 0, sizeof(__nv_bfloat16) * d.b * 256, st));
+  if (par[1].dzbT) EDPC_CUDA(cudaMemsetAsync(par[1].dzbT, 0, sizeof(__nv_bfloat16) * 256 * d.ldT, st));
   return EDPC_OK;
 }
 
@@ -482,6 +602,7 @@ int Model::fdm_bwd_call(const StepIO& io, cudaStream_t st) {
     sa.active = io.mode == 2 ? io.active : nullptr;
     sa.b = d.b;
     sa.Fp = d.Fp;
+    sa.Ub = U_base;  // delayed update: Adam from the next step's FDMs into this parity's
     if (timing && ev_fdm[2]) EDPC_CUDA(record_timing(ev_fdm[2], st));
     EDPC_CUDA(launch_fdm_dx(sa, st));
     if (timing && ev_fdm[3]) EDPC_CUDA(record_timing(ev_fdm[3], st));
@@ -490,7 +611,10 @@ int Model::fdm_bwd_call(const StepIO& io, cudaStream_t st) {
     {
       NoPdl scope;
       if (timing && ev_fdm[4]) EDPC_CUDA(record_timing(ev_fdm[4], side_fdm));
-      EDPC_CUDA(launch_fdm_adam(sa, side_fdm));
+      // delayed update: a CTA per 32 rows on a low-priority stream, so that
+      // the adjoint's and the forward pass's GEMM CTAs (up to 255 registers a
+      // thread, which leave no room beside a resident update CTA) go first
+      EDPC_CUDA(launch_fdm_adam(sa, side_fdm, !delayed));
       if (timing && ev_fdm[5]) EDPC_CUDA(record_timing(ev_fdm[5], side_fdm));
     }
     EDPC_CUDA(cudaEventRecord(adam_ev, side_fdm));
@@ -581,6 +705,19 @@ int Model::fp8_shadow(const void* src, int rows, int cols, int ld) {
 }
 
 int Model::build_tc_plan() {
+  if (!delayed) return build_tc_plan_one();
+  const int keep = cur;
+  int r = EDPC_OK;
+  for (int q = 0; q < 2 && r == EDPC_OK; ++q) {
+    select(q);
+    r = build_tc_plan_one();
+    if (r == EDPC_OK) par[q].tcp = tcp;
+  }
+  select(keep);
+  return r;
+}
+
+int Model::build_tc_plan_one() {
   if (precision == EDPC_FP8E4M3 && !f8_arena) {
     // first pass: collect the operand shadows; then allocate them
     f8.clear();
@@ -1014,10 +1151,10 @@ int Model::run_tc(int site, cudaStream_t st) {
   if (st == side) {
     NoPdl scope;
     if (precision == EDPC_FP8E4M3) EDPC_TRY(quantize_site(site, st));
-    EDPC_CUDA(launch_gemm_tc(tcp.site[site], st));
+    EDPC_CUDA(launch_gemm_tc(plan().site[site], st));
   } else {
     if (precision == EDPC_FP8E4M3) EDPC_TRY(quantize_site(site, st));
-    EDPC_CUDA(launch_gemm_tc(tcp.site[site], st));
+    EDPC_CUDA(launch_gemm_tc(plan().site[site], st));
   }
   return EDPC_OK;
 }
@@ -1094,7 +1231,9 @@ int Model::fdm_bwd_joined(const StepIO& io, cudaStream_t st) {
 
 int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
   const int kH = d.k * d.H;
-  EDPC_CUDA(cudaStreamWaitEvent(st, tr_ev, 0));  // PbT is read by the dX GEMMs below
+  // PbT is read by the dX GEMMs below (delayed update: this parity's copies
+  // were made during the previous step)
+  if (!delayed) EDPC_CUDA(cudaStreamWaitEvent(st, tr_ev, 0));
   // side: head weight gradients
   EDPC_TRY(fork_side(st));
   EDPC_TRY(run_tc(kSiteHeadDw, side));
@@ -1236,11 +1375,48 @@ int Model::adam(cudaStream_t st) {
 }
 
 int Model::step(const StepIO& io, cudaStream_t st) {
+  if (delayed) return step_delayed(io, st);
   EDPC_TRY(forward(io, st));
   EDPC_TRY(head(io, st));
   EDPC_TRY(backward(io, st));
   if (io.update) EDPC_TRY(adam(st));
   if (io.advance) EDPC_CUDA(launch_step_advance(ctl, io.sp, d.K, io.ring_slots, d.b, st));
+  return EDPC_OK;
+}
+
+// Step s of the delayed-update schedule (parity q = s % 2): the forward pass
+// and the head of step s on st with parity q; beside them, on bwd_st, the
+// adjoint of step s - 1 with parity q ^ 1 (its FDM adjoint writes the FDMs of
+// step s + 1, from those of step s, over parity q ^ 1's); then, after both,
+// Adam writes the parameters of step s + 1 into parity q ^ 1 from parity q's
+// and the gradient of step s - 1, with step s - 1's Adam counter.
+int Model::step_delayed(const StepIO& io, cudaStream_t st) {
+  const int q = io.tick & 1;
+  EDPC_CUDA(cudaEventRecord(tick_ev, st));  // after the previous step's Adam and step control
+  EDPC_CUDA(cudaStreamWaitEvent(bwd_st, tick_ev, 0));
+  select(q);
+  EDPC_TRY(forward(io, st));
+  EDPC_TRY(head(io, st));
+  select(q ^ 1);
+  if (precision == EDPC_FP32) {
+    NoPdl scope;  // the first launch on bwd_st follows a cross-stream wait
+    EDPC_TRY(backward(io, bwd_st));
+  } else {
+    EDPC_TRY(backward(io, bwd_st));  // its first launch on bwd_st is made without PDL
+  }
+  EDPC_CUDA(cudaEventRecord(bwd_ev, bwd_st));
+  EDPC_CUDA(cudaStreamWaitEvent(st, bwd_ev, 0));
+  const Parity& now = par[q];
+  const Parity& nxt = par[q ^ 1];
+  if (io.update) {
+    NoPdl scope;  // follows the join of bwd_st
+    if (precision != EDPC_FP32)
+      EDPC_CUDA(launch_adam_bf16(nxt.P, G, M, V, nxt.Pb, nparam, nxt.ctl, st, now.P));
+    else
+      EDPC_CUDA(launch_adam(nxt.P, G, M, V, nparam, nxt.ctl, st, now.P));
+  }
+  if (io.advance) EDPC_CUDA(launch_step_advance(now.ctl, io.sp, d.K, io.ring_slots, d.b, st, nxt.ctl));
+  select(q ^ 1);
   return EDPC_OK;
 }
 

@@ -96,6 +96,41 @@ class Model {
   cudaEvent_t ev_fdm[6] = {};
   bool timing = false;
 
+  // Delayed-update schedule (EDPC_FLAG_DELAYED_UPDATE): two copies ("parities")
+  // of the parameters, the FDMs, the step control and every buffer that the
+  // forward pass and the head write. Step s predicts with parity s % 2 while
+  // the adjoint of step s - 1 runs with parity (s - 1) % 2 (its parameters,
+  // activations and control) on bwd_st; Adam then writes the parameters of
+  // step s + 1 into parity (s + 1) % 2. The FDM adjoint's dx' reads parity
+  // (s - 1) % 2's FDMs, and its update (on side_fdm, off the adjoint's
+  // critical path) writes the FDMs of step s + 1 over them, from those of
+  // step s; the FDM forward of step s + 1 waits for it. Before the first
+  // step parity 1 is the zero state, whose adjoint is zero: its updates copy
+  // parity 0 exactly.
+  struct Parity {
+    float *P = nullptr, *U = nullptr;
+    __nv_bfloat16 *Pb = nullptr, *PbT = nullptr;
+    StepCtl* ctl = nullptr;
+    uint8_t* ctx = nullptr;
+    float* S[kMaxBlocks + 2] = {};
+    BlockAct ba[kMaxBlocks] = {};
+    __nv_bfloat16 *X0b[kMaxBlocks] = {}, *X0bT[kMaxBlocks] = {}, *Gb[kMaxBlocks] = {}, *GbT[kMaxBlocks] = {};
+    __nv_bfloat16 *Slte_b = nullptr, *Slte_bT = nullptr, *Shead_b = nullptr, *Shead_bT = nullptr;
+    __nv_bfloat16 *Yb = nullptr, *YbT = nullptr, *dzb = nullptr, *dzbT = nullptr;
+    float *Xp = nullptr, *Y = nullptr, *z = nullptr, *p = nullptr, *dz = nullptr;
+    float *xp_pend = nullptr, *dy_pend = nullptr;  // the FDM update's inputs
+    FdmPend* pend = nullptr;
+    TcPlan tcp;  // GEMM sites bound to this parity's buffers
+  };
+  bool delayed = false;
+  Parity par[2];
+  int cur = 0;                    // the parity the members above point into
+  float* U_base = nullptr;        // delayed: the other parity's U (Adam base of the FDM adjoint)
+  cudaStream_t bwd_st = nullptr;  // delayed: the adjoint of the previous step
+  cudaEvent_t tick_ev = nullptr, bwd_ev = nullptr;
+  void select(int q);             // points the members at parity q
+  StepCtl* ctl_of(int q) const { return delayed ? par[q].ctl : par[0].ctl; }
+
   ~Model();
   int init(const edpc_cfg& cfg, int streams);
   int set_ctl_for_step(int i, int t, int bact, int ring_slots, cudaStream_t st);
@@ -115,12 +150,14 @@ class Model {
     const uint8_t* active = nullptr;   // mode 2
     int update = 1;                    // 0: gradient only (FDM grad to gU, no Adam)
     bool advance = true;               // launch the step-control advance at the end
+    int tick = 0;                      // delayed update: the step's index (its parity is tick & 1)
   };
   int forward(const StepIO& io, cudaStream_t st);
   int head(const StepIO& io, cudaStream_t st);
   int backward(const StepIO& io, cudaStream_t st);
   int adam(cudaStream_t st);
   int step(const StepIO& io, cudaStream_t st);
+  int step_delayed(const StepIO& io, cudaStream_t st);
   // Makes `st` wait for a pending FDM update (call before reading U, and before
   // ending a graph capture).
   int flush(cudaStream_t st);
@@ -188,6 +225,9 @@ class Model {
   int fdm_fwd_call(const StepIO& io, cudaStream_t st);
   int fdm_bwd_call(const StepIO& io, cudaStream_t st);
   int fdm_bwd_joined(const StepIO& io, cudaStream_t st);  // waits for the side stream from 2048 streams on
+  int build_tc_plan_one();
+  void save_parity(int q);                                 // parity q <- the members
+  const TcPlan& plan() const { return delayed ? par[cur].tcp : tcp; }
 };
 
 }  // namespace edpc

@@ -663,12 +663,13 @@ __global__ void __launch_bounds__(256) fdm_adam_kernel(FdmSplitArgs a) {
     const float xi = a.xp_pend[(size_t)s * Fp + i];
     const size_t ro = ((size_t)s * Fp + i) * Fp;
     float4* U4 = reinterpret_cast<float4*>(a.U + ro);
+    const float4* B4 = reinterpret_cast<const float4*>((a.Ub ? a.Ub : a.U) + ro);
     float4* M4 = reinterpret_cast<float4*>(a.Um + ro);
     float4* V4 = reinterpret_cast<float4*>(a.Uv + ro);
     float4 u[NCH], m[NCH], v[NCH];
 #pragma unroll
     for (int q = 0; q < NCH; ++q) {
-      u[q] = __ldcs(U4 + lane + 32 * q);
+      u[q] = __ldcs(B4 + lane + 32 * q);
       m[q] = __ldcs(M4 + lane + 32 * q);
       v[q] = __ldcs(V4 + lane + 32 * q);
     }
@@ -703,6 +704,7 @@ __global__ void __maxnreg__(80) fdm_adam_persist_kernel(FdmSplitArgs a) {
   pdl_launch();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const FdmPend pd = *a.pend;
+  const float* src = a.Ub ? a.Ub : a.U;  // Adam base (the delayed update reads the other parity)
   const int units = a.b * FP * UPR;      // < 2^31: at most 65535 x 1024 x 4
   const int W = gridDim.x * kAdamWarps;
   for (int u0 = blockIdx.x * kAdamWarps + warp; u0 < units; u0 += 2 * W) {
@@ -727,7 +729,7 @@ __global__ void __maxnreg__(80) fdm_adam_persist_kernel(FdmSplitArgs a) {
       if (act[h]) {
 #pragma unroll
         for (int q = 0; q < NU; ++q) {
-          u[h][q] = __ldcs(reinterpret_cast<const float4*>(a.U + base[h]) + lane + 32 * q);
+          u[h][q] = __ldcs(reinterpret_cast<const float4*>(src + base[h]) + lane + 32 * q);
           m[h][q] = __ldcs(reinterpret_cast<const float4*>(a.Um + base[h]) + lane + 32 * q);
           v[h][q] = __ldcs(reinterpret_cast<const float4*>(a.Uv + base[h]) + lane + 32 * q);
         }
@@ -851,8 +853,9 @@ __global__ void __launch_bounds__(256) fdm_adam_generic_kernel(FdmSplitArgs a) {
     if (i >= Fp) break;
     const size_t ro = ((size_t)s * Fp + i) * Fp;
     const float xi = a.xp_pend[(size_t)s * Fp + i];
+    const float* src = a.Ub ? a.Ub : a.U;
     for (int j = lane; j < Fp; j += 32) {
-      float u = a.U[ro + j], m = a.Um[ro + j], v = a.Uv[ro + j];
+      float u = src[ro + j], m = a.Um[ro + j], v = a.Uv[ro + j];
       adam1(u, m, v, xi * a.dy_pend[(size_t)s * Fp + j], pd.lr, pd.bc1, pd.bc2);
       a.U[ro + j] = u;
       a.Um[ro + j] = m;
@@ -890,15 +893,15 @@ cudaError_t launch_adam_persist(const FdmSplitArgs& a, cudaStream_t st) {
   return launch_k(fdm_adam_persist_kernel<NCH>, dim3(sms), dim3(32 * kAdamWarps), 0, st, a);
 }
 
-cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st) {
-  switch (a.Fp) {
-    case 128: return launch_adam_persist<1>(a, st);
-    case 256: return launch_adam_persist<2>(a, st);
-    case 384: return launch_adam_persist<3>(a, st);
-    case 512: return launch_adam_persist<4>(a, st);
-    case 1024: return launch_adam_persist<8>(a, st);
-    default: break;
-  }
+cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st, bool persistent) {
+  if (persistent) switch (a.Fp) {
+      case 128: return launch_adam_persist<1>(a, st);
+      case 256: return launch_adam_persist<2>(a, st);
+      case 384: return launch_adam_persist<3>(a, st);
+      case 512: return launch_adam_persist<4>(a, st);
+      case 1024: return launch_adam_persist<8>(a, st);
+      default: break;
+    }
   dim3 grid(div_up(a.Fp, kFdmRowsPerCta), a.b);
   switch (a.Fp) {
     case 128: return launch_k(fdm_adam_kernel<1>, grid, dim3(256), 0, st, a);
@@ -1035,13 +1038,15 @@ cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, 
 // ============================================================================================
 // Adam on the shared parameters (Sec. 4.1: lr 1e-3; beta, eps as documented).
 // ============================================================================================
-__global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
+// P is read from Pin and written to P (Pin == P: in place; the delayed-update
+// schedule writes the next parameters beside the current ones).
+__global__ void adam_kernel(float* P, const float* Pin, const float* __restrict__ G, float* __restrict__ M,
                             float* __restrict__ V, size_t n, const StepCtl* __restrict__ ctl) {
   pdl_wait();
   pdl_launch();
   const StepCtl c = *ctl;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    float p = P[e], m = M[e], v = V[e];
+    float p = Pin[e], m = M[e], v = V[e];
     const float gr = G[e];
     adam1(p, m, v, gr, c.lr, c.bc1, c.bc2);
     P[e] = p;
@@ -1051,19 +1056,23 @@ __global__ void adam_kernel(float* __restrict__ P, const float* __restrict__ G, 
 }
 
 cudaError_t launch_adam(float* P, const float* G, float* M, float* V, size_t n, const StepCtl* ctl,
-                        cudaStream_t st) {
+                        cudaStream_t st, const float* Pin) {
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
-  return launch_k(adam_kernel, dim3(grid), dim3(256), 0, st, P, G, M, V, n, ctl);
+  return launch_k(adam_kernel, dim3(grid), dim3(256), 0, st, P, Pin ? Pin : P, G, M, V, n, ctl);
 }
 
 // ============================================================================================
 // Step control: advance to the next time index and derive its scalars.
 // ============================================================================================
-__global__ void step_advance_kernel(StepCtl* ctl, Split sp, int K, int ring_slots, int b) {
+// Reads the step control of the current step from `src` and writes the next
+// step's to `dst` (the same record, or the other of the delayed-update
+// schedule's two, whose sticky error bits are kept).
+__global__ void step_advance_kernel(const StepCtl* src, StepCtl* dst, Split sp, int K, int ring_slots, int b) {
   pdl_wait();
   pdl_launch();
-  StepCtl c = *ctl;
+  StepCtl c = *src;
+  c.err |= dst->err;
   c.i += 1;
   c.t += 1;
   long long i = c.i;
@@ -1080,11 +1089,13 @@ __global__ void step_advance_kernel(StepCtl* ctl, Split sp, int K, int ring_slot
   c.bc1 = 1.0f - powf(kB1, (float)c.t);
   c.bc2 = 1.0f - powf(kB2, (float)c.t);
   c.slot = (int)((i - K) % ring_slots);
-  *ctl = c;
+  *dst = c;
 }
 
-cudaError_t launch_step_advance(StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st) {
-  return launch_k(step_advance_kernel, dim3(1), dim3(1), 0, st, ctl, sp, K, ring_slots, b);
+cudaError_t launch_step_advance(StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st,
+                                StepCtl* dst) {
+  return launch_k(step_advance_kernel, dim3(1), dim3(1), 0, st, (const StepCtl*)ctl, dst ? dst : ctl, sp, K,
+                  ring_slots, b);
 }
 
 // ============================================================================================
@@ -1844,14 +1855,14 @@ cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st) {
 // Adam with the BF16 weight copy refreshed in the same pass; transposed copies
 // of every weight matrix in one launch (32 x 32 tiles through shared memory).
 // ============================================================================================
-__global__ void adam_bf16_kernel(float* __restrict__ P, const float* __restrict__ G, float* __restrict__ M,
+__global__ void adam_bf16_kernel(float* P, const float* Pin, const float* __restrict__ G, float* __restrict__ M,
                                  float* __restrict__ V, __nv_bfloat16* __restrict__ Pb, size_t n,
                                  const StepCtl* __restrict__ ctl) {
   pdl_wait();
   pdl_launch();
   const StepCtl c = *ctl;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < n; e += (size_t)gridDim.x * blockDim.x) {
-    float p = P[e], m = M[e], v = V[e];
+    float p = Pin[e], m = M[e], v = V[e];
     const float gr = G[e];
     adam1(p, m, v, gr, c.lr, c.bc1, c.bc2);
     P[e] = p;
@@ -1862,10 +1873,10 @@ __global__ void adam_bf16_kernel(float* __restrict__ P, const float* __restrict_
 }
 
 cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
-                             const StepCtl* ctl, cudaStream_t st) {
+                             const StepCtl* ctl, cudaStream_t st, const float* Pin) {
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
-  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, G, M, V, Pb, n, ctl);
+  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, Pin ? Pin : P, G, M, V, Pb, n, ctl);
 }
 
 __global__ void transpose_tiles_kernel(const __nv_bfloat16* __restrict__ Pb, __nv_bfloat16* __restrict__ PbT,

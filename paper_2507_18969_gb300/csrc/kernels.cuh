@@ -124,9 +124,14 @@ struct FdmSplitArgs {
   Split sp;
   const uint8_t* active;
   int b, Fp;
+  const float* Ub;  // fdm_adam: the Adam base (nullptr: U, in place); the delayed
+                    // update reads the next step's U there and writes U, whose
+                    // values fdm_dx has already consumed
 };
 cudaError_t launch_fdm_dx(const FdmSplitArgs& a, cudaStream_t st);
-cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st);
+// persistent: one resident CTA per SM (else a CTA per 32 FDM rows, which the
+// block scheduler interleaves with other streams' CTAs as they retire).
+cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st, bool persistent = true);
 // dE[c][d] = sum over positions with ctx == c of dX[s][k*D + d], fixed order
 // (CTAs per byte value c and chunk of kEmbChunkPos positions); D <= 64. With
 // more than one chunk, part (256 * chunks * D floats) and cnt (256 counters,
@@ -137,10 +142,13 @@ int embed_bwd_chunks(int b, int K);
 cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, float* part,
                              unsigned* cnt, cudaStream_t st);
 // Adam over the flat shared parameters; bf16 != nullptr also refreshes the BF16 copy.
+// Pin: the parameters read (nullptr: P itself, an in-place update).
 cudaError_t launch_adam(float* P, const float* G, float* M, float* V, size_t n, const StepCtl* ctl,
-                        cudaStream_t st);
+                        cudaStream_t st, const float* Pin = nullptr);
 // i += 1 and the derived per-step scalars.
-cudaError_t launch_step_advance(StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st);
+// dst: where the next step's control goes (nullptr: ctl itself).
+cudaError_t launch_step_advance(StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st,
+                                StepCtl* dst = nullptr);
 
 // ---- coder --------------------------------------------------------------------------------
 cudaError_t launch_prefix_encode(EncState* es, const uint8_t* data, Split sp, int K, int b,
@@ -219,7 +227,7 @@ constexpr int kColsumMaxChunks = 64;
 cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st);
 // Adam that also writes the BF16 copy Pb of every updated parameter (same flat layout).
 cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
-                             const StepCtl* ctl, cudaStream_t st);
+                             const StepCtl* ctl, cudaStream_t st, const float* Pin = nullptr);
 // Transposed BF16 copies of several matrices in one launch: PbT[off + c*rows + r] = Pb[off + r*cols + c].
 struct TransposeTile {
   unsigned long long off;
