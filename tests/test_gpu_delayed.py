@@ -11,7 +11,8 @@ stream beside the forward pass of step i + 1. Checks:
   * the code length within 0.5 % of the FP64 oracle's delayed schedule: the
     64 KiB order-2 Markov input (FP32), the 512-stream prefix of the 64 MiB
     mix (FP32 and BF16), and an uneven file set whose active streams drop
-    out step by step (FP32);
+    out step by step (FP32), 2048 streams (BF16) and the 1 GiB workload's
+    model dimensions (FP32);
   * the flag is recorded in the header and changes the bitstream;
   * rejected with FP8, with EDPC_FLAG_OVERLAP_FDM and by the model API.
 """
@@ -136,3 +137,25 @@ def test_delayed_rejected_combinations():
             edpc.compress(x, edpc.make_cfg(streams=4, context=8, precision=prec, flags=DL | extra, **SMALL))
     with pytest.raises(edpc.EdpcError):
         edpc.Model(edpc.make_cfg(streams=4, context=8, flags=DL, **SMALL), 4)
+
+
+@pytest.mark.parametrize("dims,b,steps,prec", [
+    (dict(context=16, embed_dim=8, latent=128, hidden=128, blocks=2), 2048, 48, edpc.EDPC_BF16),
+    (dict(context=64, embed_dim=16, latent=512, hidden=512, blocks=6), 8, 64, edpc.EDPC_FP32),
+], ids=["2048-streams-bf16", "1g-model-dims-fp32"])
+def test_delayed_against_oracle_at_large_batch_and_large_model(dims, b, steps, prec):
+    # From 2048 streams the BF16 FDM adjoint also waits for the side stream;
+    # the model of the 1 GiB workload (K = 64, F' = 512, 6 MBRBs of 512) takes
+    # the F' = 512 kernels. Both against the oracle's delayed schedule on
+    # prefix inputs (the oracle runs here, a minute or two of CPU).
+    cfg = dict(branches=2, lr=1e-3, seed=1, **dims)
+    x = synth.multimedia_mix(b * (dims["context"] + steps) * 4, 5)
+    q = x.size // b
+    xp = np.ascontiguousarray(x[: q * b].reshape(b, q)[:, : dims["context"] + steps]).reshape(-1)
+    ref = oracle_compress(xp, Config(**cfg), b, delayed=True)
+    o_bytes = sum(len(s) for s in ref["streams"])
+    bits = edpc.compress(xp, edpc.make_cfg(streams=b, precision=prec, flags=DL, **cfg))
+    assert np.array_equal(edpc.decompress(bits), xp)
+    code, _ = _payload(bits)
+    print("delayed %d: %d code bytes, oracle %d (%+.3f %%)" % (prec, code, o_bytes, 100 * (code / o_bytes - 1)))
+    assert abs(code - o_bytes) <= 0.005 * o_bytes, (code, o_bytes)
