@@ -2,6 +2,8 @@
 import ctypes as C
 import os
 import re
+import struct
+import zlib
 
 import numpy as np
 import pytest
@@ -141,3 +143,42 @@ def test_independent_archive_table_is_checked(lib):
     with pytest.raises(edpc.EdpcError) as e:
         edpc.decompress_member(_indep(1, [(b"xy", 3)]), 1)
     assert e.value.code == 1  # EDPC_EINVAL: index out of range
+
+
+def _header(sched, precision=1, n=100):
+    # variant-0 container of one empty stream: fixed header, one length word, CRC
+    b = 1
+    hl = 88 + 4 * b + 4
+    h = struct.pack("<IIIIIIIIIIf", 0x43504445, 1, hl, precision, 16, 16, 128, 128, 2, 2, 1e-3)
+    h += struct.pack("<IQQIIQII", sched, 1, n, 1, b, 0, 0, 0)
+    h += struct.pack("<I", 0)
+    assert len(h) == hl - 4
+    return h + struct.pack("<I", zlib.crc32(h) & 0xFFFFFFFF)
+
+
+def test_header_update_schedule_word(lib):
+    import paper_2507_18969_gb300 as pkg
+    c, n, b = pkg.peek(_header(0))
+    assert (n, b) == (100, 1) and not (c.flags & pkg.EDPC_FLAG_DELAYED_UPDATE)
+    c, _, _ = pkg.peek(_header(1))
+    assert c.flags & pkg.EDPC_FLAG_DELAYED_UPDATE
+    with pytest.raises(pkg.EdpcError) as e:
+        pkg.peek(_header(2))
+    assert e.value.code == 7  # EDPC_EARCH: a schedule this build lacks
+    with pytest.raises(pkg.EdpcError) as e:
+        pkg.peek(_header(1, precision=2))  # the delayed update with FP8 is not a valid configuration
+    assert e.value.code == 3
+
+
+def test_delayed_update_flag_combinations_are_checked(lib):
+    import paper_2507_18969_gb300 as pkg
+    D = pkg.EDPC_FLAG_DELAYED_UPDATE
+    assert pkg.param_count(pkg.make_cfg(precision=pkg.EDPC_BF16, flags=D)) > 0
+    assert pkg.param_count(pkg.make_cfg(precision=pkg.EDPC_FP32, flags=D)) > 0
+    for bad in (pkg.make_cfg(precision=pkg.EDPC_FP8E4M3, flags=D),
+                pkg.make_cfg(precision=pkg.EDPC_BF16, flags=D | pkg.EDPC_FLAG_OVERLAP_FDM)):
+        assert pkg.param_count(bad) == 0
+        out = C.c_void_p()
+        n = C.c_size_t()
+        assert lib.edpc_compress(None, 0, C.byref(bad), C.byref(out), C.byref(n)) == 1
+        assert b"delayed" in lib.edpc_last_error()
