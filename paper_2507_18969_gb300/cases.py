@@ -1,10 +1,11 @@
 """Named timing cases of the library (for step timing and kernel profiles).
 
-  python -m paper_2507_18969_gb300.cases steps CASE [CHUNKS]
+  python -m paper_2507_18969_gb300.cases steps CASE [CHUNKS [delayed]]
       An encoder session on CASE's model and stream count over random bytes
       already on the device (the kernels' work does not depend on the byte
       values): one warm-up chunk of 64 model steps, then CHUNKS timed chunks;
-      prints milliseconds per model step (CUDA events).
+      prints milliseconds per model step (CUDA events). "delayed" selects the
+      delayed-update schedule (EDPC_FLAG_DELAYED_UPDATE).
   python -m paper_2507_18969_gb300.cases gemm CASE CODE
       Every tcgen05 GEMM site of CASE's model with every tile code set to CODE,
       each launched alone (Model.time_gemms): ms, GFLOP and TFLOP/s per site.
@@ -41,7 +42,7 @@ def _cfg(c, edpc, **kw):
                          branches=2, lr=1e-3, seed=1, precision=edpc.EDPC_BF16, **kw)
 
 
-def steps(name: str, chunks: int = 2) -> dict:
+def steps(name: str, chunks: int = 2, delayed: bool = False) -> dict:
     import torch
     import paper_2507_18969_gb300 as edpc
     from paper_2507_18969_gb300 import Encoder
@@ -49,7 +50,8 @@ def steps(name: str, chunks: int = 2) -> dict:
     n = c["b"] * (c["K"] + (chunks + 2) * 64 + 8)
     x = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda")
     st = torch.cuda.current_stream()
-    enc = Encoder(_cfg(c, edpc), device_ptr=x.data_ptr(), length=n, stream=st.cuda_stream)
+    flags = edpc.EDPC_FLAG_DELAYED_UPDATE if delayed else 0
+    enc = Encoder(_cfg(c, edpc, flags=flags), device_ptr=x.data_ptr(), length=n, stream=st.cuda_stream)
     enc.run(64)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -60,7 +62,7 @@ def steps(name: str, chunks: int = 2) -> dict:
     torch.cuda.synchronize()
     enc.close()
     ms = e0.elapsed_time(e1) / done
-    return dict(case=name, streams=c["b"], ms_per_model_step=ms, mbs=c["b"] / ms / 1e3)
+    return dict(case=name, streams=c["b"], delayed=delayed, ms_per_model_step=ms, mbs=c["b"] / ms / 1e3)
 
 
 def gemm(name: str, code: int) -> list[dict]:
@@ -115,7 +117,8 @@ def main(argv) -> int:
         print(__doc__)
         return 2
     if argv[0] == "steps":
-        print(json.dumps(steps(argv[1], int(argv[2]) if len(argv) > 2 else 2)), flush=True)
+        print(json.dumps(steps(argv[1], int(argv[2]) if len(argv) > 2 else 2,
+                               len(argv) > 3 and argv[3] == "delayed")), flush=True)
     else:
         for r in gemm(argv[1], int(argv[2]) if len(argv) > 2 else 0):
             print(json.dumps(r), flush=True)
