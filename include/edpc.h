@@ -168,7 +168,9 @@ int edpc_compress(const uint8_t* buf, size_t len, const edpc_cfg* cfg,
 int edpc_decompress(const uint8_t* bits, size_t bits_len, uint8_t** out, size_t* out_len);
 
 /* Reads the configuration and original length stored in a container
- * header without decoding. Errors: ECORRUPT, EVERSION. */
+ * header without decoding (host only). cfg->flags carries
+ * EDPC_FLAG_DELAYED_UPDATE when the container was coded with that schedule.
+ * Errors: ECORRUPT, EVERSION, EARCH (an update schedule this build lacks). */
 int edpc_peek(const uint8_t* bits, size_t bits_len, edpc_cfg* cfg, uint64_t* orig_len,
               uint32_t* streams_eff);
 
