@@ -351,7 +351,7 @@ def run_ours(args, d: Dist):
     launches = (st.launches_per_step * done + done // CHUNK) if st.launches_per_step else None
     out.update(value=value, t=t_max, done=done, clocks=ck, stats=st, launches=launches)
 
-    fp32_value = decomp_value = e2e = bpb = nopipe_value = delayed_value = bpb_delayed = None
+    fp32_value = decomp_value = e2e = bpb = nopipe_value = delayed_value = bpb_delayed = st_dl = None
     if not args.quick:
         # ---- plain FP32 path, same workload ----------------------------------------------
         enc = edpc.Encoder(make_cfg(edpc.EDPC_FP32), device_ptr=xd.data_ptr(), length=x.size,
@@ -370,7 +370,8 @@ def run_ours(args, d: Dist):
         # ---- delayed-update schedule: the adjoint of step i beside the forward of step i + 1
         enc = edpc.Encoder(make_cfg(edpc.EDPC_BF16, edpc.EDPC_FLAG_DELAYED_UPDATE), device_ptr=xd.data_ptr(),
                            length=x.size, stream=stream.cuda_stream)
-        tdl, donedl, _ = timed_session(enc, W, K, stream, d)
+        tdl, donedl, _ = timed_session(enc, W, K, stream, d, profile=True)
+        st_dl = enc.stats()
         enc.close()
         delayed_value, _ = aggregate(donedl * b, tdl, d)
 
@@ -530,6 +531,23 @@ def run_ours(args, d: Dist):
                "sample": f"{n} model steps of {ns} of the {b} streams (the first {WORKLOAD['context'] + n} bytes of "
                          f"each), FP64 NumPy oracle, {tc:.1f} s"}
 
+    delayed = None
+    if delayed_value:
+        # the FDM update runs on its own low-priority stream beside the next
+        # layers: its CUDA-event span (queueing included) bounds its rate from below
+        upd = gbs(24 * fdm_elems, st_dl.fdm_adam_ms)
+        delayed = {
+            "compress_mbs": delayed_value, "speedup": delayed_value / out["value"], "bits_per_byte": bpb_delayed,
+            "schedule": "gradient of step i applied after step i + 1; its adjoint runs beside the forward pass of "
+                        "step i + 1 on a second stream (not Algorithm 1)",
+            "fdm_update": {"kernel": "fdm_adam_kernel (Adam on U, m, v from the other parity)", "bound": "hbm",
+                           "alg_bytes_per_launch": 24 * fdm_elems, "mean_ms": st_dl.fdm_adam_ms, "achieved": upd,
+                           "peak": peak, "unit": "GB/s", "frac": upd / peak if upd else None},
+            "fdm_dx": {"alg_bytes_per_launch": 4 * fdm_elems, "mean_ms": st_dl.fdm_bwd_ms,
+                       "achieved": gbs(4 * fdm_elems, st_dl.fdm_bwd_ms)},
+            "fdm_fwd": {"alg_bytes_per_launch": 4 * fdm_elems, "mean_ms": st_dl.fdm_fwd_ms,
+                        "achieved": gbs(4 * fdm_elems, st_dl.fdm_fwd_ms)},
+        }
     if d.rank == 0:
         ms_step = out["t"] / (out["done"] / CHUNK) * 1e3 if out["done"] else None
         line = {
@@ -545,11 +563,7 @@ def run_ours(args, d: Dist):
             "bf16_vs_fp32": (out["value"] / fp32_value) if fp32_value else None,
             "dpca_off_compress_mbs": nopipe_value,
             "dpca_speedup": (out["value"] / nopipe_value) if nopipe_value else None,
-            "delayed_update": ({"compress_mbs": delayed_value, "speedup": delayed_value / out["value"],
-                                "bits_per_byte": bpb_delayed,
-                                "schedule": "gradient of step i applied after step i + 1; its adjoint runs beside "
-                                            "the forward pass of step i + 1 on a second stream (not Algorithm 1)"}
-                               if delayed_value else None),
+            "delayed_update": delayed,
             "bits_per_byte": bpb,
             "bits_per_byte_input": "the e2e prefix input (early, still-learning part of each stream)",
             "e2e": e2e, "gpu_launches": out["launches"],
