@@ -13,6 +13,8 @@ stream beside the forward pass of step i + 1. Checks:
     mix (FP32 and BF16), and an uneven file set whose active streams drop
     out step by step (FP32), 2048 streams (BF16) and the 1 GiB workload's
     model dimensions (FP32);
+  * the method variants (no LTE, three branches, one block) and a BF16 file set
+    with tuned GEMM tiles stay lossless and deterministic;
   * the flag is recorded in the header and changes the bitstream;
   * rejected with FP8, with EDPC_FLAG_OVERLAP_FDM and by the model API.
 """
@@ -159,3 +161,35 @@ def test_delayed_against_oracle_at_large_batch_and_large_model(dims, b, steps, p
     code, _ = _payload(bits)
     print("delayed %d: %d code bytes, oracle %d (%+.3f %%)" % (prec, code, o_bytes, 100 * (code / o_bytes - 1)))
     assert abs(code - o_bytes) <= 0.005 * o_bytes, (code, o_bytes)
+
+
+@pytest.mark.parametrize("prec", [edpc.EDPC_FP32, edpc.EDPC_BF16], ids=["fp32", "bf16"])
+@pytest.mark.parametrize("variant", [dict(latent=0), dict(branches=3), dict(blocks=1)], ids=["no-lte", "k3", "one-block"])
+def test_delayed_with_method_variants(prec, variant):
+    # the variants of Table 4 / Table 5 under the delayed schedule: lossless and
+    # deterministic (two encoder runs give one bitstream)
+    dims = dict(context=8, embed_dim=8, latent=64, hidden=64, blocks=2, branches=2, seed=4)
+    dims.update(variant)
+    x = synth.markov_bytes(24000, 1, 0.05, 6)
+    c = edpc.make_cfg(streams=16, precision=prec, flags=DL, **dims)
+    a = edpc.compress(x, c)
+    assert a == edpc.compress(x, c)
+    assert np.array_equal(edpc.decompress(a), x)
+
+
+def test_delayed_tuned_file_set_round_trip_bf16():
+    # BF16 file sets time every GEMM's tile at open (on parity 1's plan, whose
+    # buffers stay zero); the decoder sets the recorded tiles without timing
+    rng = np.random.default_rng(8)
+    sizes = np.exp(rng.uniform(np.log(300), np.log(20000), size=9)).astype(np.int64)
+    sizes[3] = 0
+    x = synth.multimedia_mix(int(sizes.sum()), 8)
+    files, o = [], 0
+    for s in sizes:
+        files.append(x[o:o + s].copy())
+        o += s
+    cfg = edpc.make_cfg(streams=64, precision=edpc.EDPC_BF16, flags=DL, context=16, embed_dim=8, latent=128,
+                        hidden=128, blocks=2)
+    bits = edpc.compress_many(files, cfg)
+    for a, b in zip(files, edpc.decompress_many(bits)):
+        assert np.array_equal(a, b)
