@@ -411,7 +411,8 @@ int edpc_range_encode_noalloc(const uint32_t* sym, uint32_t nsym, uint32_t strea
 typedef struct edpc_model edpc_model;
 
 /* A model for `streams` rows with cfg's dims and precision, initialised
- * from cfg.seed exactly as the encoder initialises it. */
+ * from cfg.seed exactly as the encoder initialises it. Its steps follow
+ * Algorithm 1: cfg.flags with EDPC_FLAG_DELAYED_UPDATE gives EDPC_EINVAL. */
 int edpc_model_create(const edpc_cfg* cfg, uint32_t streams, edpc_model** out);
 void edpc_model_destroy(edpc_model* m);
 
