@@ -48,7 +48,8 @@ extern "C" {
 #define EDPC_EVERSION 4  /* bitstream format version not supported */
 #define EDPC_ECUDA 5     /* a CUDA runtime or driver call failed */
 #define EDPC_ETIMEOUT 6  /* a bounded device-side wait expired */
-#define EDPC_EARCH 7     /* bitstream was made by a GEMM/precision variant this build lacks */
+#define EDPC_EARCH 7     /* bitstream was made by a GEMM, precision or schedule variant this
+                            library version lacks */
 
 /* Arithmetic of the model's GEMMs. Softmax, CDF quantization, optimizer
  * state and the FDM stay FP32 in every mode. */
@@ -170,7 +171,7 @@ int edpc_decompress(const uint8_t* bits, size_t bits_len, uint8_t** out, size_t*
 /* Reads the configuration and original length stored in a container
  * header without decoding (host only). cfg->flags carries
  * EDPC_FLAG_DELAYED_UPDATE when the container was coded with that schedule.
- * Errors: ECORRUPT, EVERSION, EARCH (an update schedule this build lacks). */
+ * Errors: ECORRUPT, EVERSION, EARCH (an update schedule this library version lacks). */
 int edpc_peek(const uint8_t* bits, size_t bits_len, edpc_cfg* cfg, uint64_t* orig_len,
               uint32_t* streams_eff);
 

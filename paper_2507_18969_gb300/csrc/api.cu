@@ -35,7 +35,7 @@ extern "C" const char* edpc_strerror(int status) {
     case EDPC_EVERSION: return "unsupported bitstream version";
     case EDPC_ECUDA: return "CUDA error";
     case EDPC_ETIMEOUT: return "device wait timed out";
-    case EDPC_EARCH: return "bitstream variant not supported by this build";
+    case EDPC_EARCH: return "bitstream variant not supported by this library version";
     default: return "unknown status";
   }
 }

@@ -164,7 +164,7 @@ def test_header_update_schedule_word(lib):
     assert c.flags & pkg.EDPC_FLAG_DELAYED_UPDATE
     with pytest.raises(pkg.EdpcError) as e:
         pkg.peek(_header(2))
-    assert e.value.code == 7  # EDPC_EARCH: a schedule this build lacks
+    assert e.value.code == 7  # EDPC_EARCH: a schedule this library version lacks
     with pytest.raises(pkg.EdpcError) as e:
         pkg.peek(_header(1, precision=2))  # the delayed update with FP8 is not a valid configuration
     assert e.value.code == 3
