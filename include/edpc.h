@@ -517,6 +517,18 @@ int edpc_model_block_io(edpc_model* m, uint32_t block, float* s_in, float* s_out
 int edpc_ksg_mi(const float* Z, const float* Y, uint32_t N, uint32_t dz, uint32_t dy, uint32_t k, uint32_t* cz,
                 uint32_t* cy, double* mi, void* cuda_stream);
 
+/*
+ * Self-test of the bounded-wait error path (fault detection without a GPU
+ * fault). One CTA waits on a shared-memory mbarrier that nothing arrives on;
+ * the wait gives up after about 50 ms of SM clock (or 2^20 polls), records an
+ * error bit and returns, as every bounded wait of the library's kernels does.
+ * Runs on cuda_stream (NULL: the default stream) and waits for it, then runs
+ * a further copy on the stream to show the context still works.
+ * Returns EDPC_ETIMEOUT when the wait expired (the expected result), ECUDA if
+ * the wait completed or a CUDA call failed.
+ */
+int edpc_selftest_wait_timeout(void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

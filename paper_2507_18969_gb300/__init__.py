@@ -152,6 +152,12 @@ def ksg_mi(z_dev: int, y_dev: int, n: int, dz: int, dy: int, k: int, cz_dev: int
     return mi.value
 
 
+def selftest_wait_timeout(stream: int = 0) -> None:
+    """Runs the bounded-wait self-test; raises EdpcError with code 6
+    (EDPC_ETIMEOUT) when the wait expired as designed."""
+    check(load().edpc_selftest_wait_timeout(C.c_void_p(stream)), "edpc_selftest_wait_timeout")
+
+
 def compress_independent(files, cfg: Cfg, stream_len: int = 65536, concurrency: int = 8) -> bytes:
     """Archive of independent per-file models: file f is compressed alone with
     max(1, ceil(n_f / stream_len)) streams; the sessions run ``concurrency`` at a time."""

@@ -112,6 +112,7 @@ PROTOS = {
     "edpc_model_time_gemms": (C.c_int, [P, C.c_uint32, P, P, P, C.c_uint32, C.POINTER(C.c_uint32)]),
     "edpc_model_block_io": (C.c_int, [P, C.c_uint32, P, P]),
     "edpc_ksg_mi": (C.c_int, [P, P, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, P, P, C.POINTER(C.c_double), P]),
+    "edpc_selftest_wait_timeout": (C.c_int, [P]),
     "edpc_compress_independent": (C.c_int, [P, P, C.c_size_t, P, C.c_uint64, C.c_uint32, C.POINTER(C.c_void_p),
                                             C.POINTER(C.c_size_t)]),
     "edpc_independent_info": (C.c_int, [P, C.c_size_t, C.POINTER(C.c_uint64), P]),

@@ -22,6 +22,9 @@ static thread_local std::string g_last_error;
 void set_error(const std::string& msg) { g_last_error = msg; }
 int fail(int code, const std::string& msg) {
   g_last_error = msg;
+  // A failed allocation is not sticky, but the runtime keeps it as the
+  // thread's last error; clear it so that later launch checks do not see it.
+  if (code == EDPC_ENOMEM) (void)cudaGetLastError();
   return code;
 }
 }  // namespace edpc
