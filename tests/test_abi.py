@@ -182,3 +182,15 @@ def test_delayed_update_flag_combinations_are_checked(lib):
         n = C.c_size_t()
         assert lib.edpc_compress(None, 0, C.byref(bad), C.byref(out), C.byref(n)) == 1
         assert b"delayed" in lib.edpc_last_error()
+
+
+def test_host_allocation_failure_is_enomem(lib):
+    # A valid header whose original length (2^62 bytes) no host allocation can
+    # hold: edpc_decompress fails on its output buffer before any device work.
+    bits = _header(0, n=1 << 62)
+    out = C.c_void_p()
+    n = C.c_size_t()
+    buf = (C.c_uint8 * len(bits)).from_buffer_copy(bits)
+    assert lib.edpc_decompress(buf, len(bits), C.byref(out), C.byref(n)) == 2  # EDPC_ENOMEM
+    assert b"output buffer" in lib.edpc_last_error()
+    assert not out.value and n.value == 0
