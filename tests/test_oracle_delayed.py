@@ -5,8 +5,8 @@ theta_i, and the update after step i applies g_{i-1}:
 theta_{i+1} = Adam(theta_i, g_{i-1}), theta_{K+1} = theta_K. The pins build
 that trajectory from pieces the schedule does not share (Algorithm 1's own
 first step, and a fresh model's gradient at the stale parameters), so an
-update applied on time, a gradient taken at the updated parameters, or a
-wrong Adam counter fails one of them.
+update applied on time, a gradient taken at the updated parameters, a wrong
+Adam counter, or FDM rows taken from the wrong step fails one of them.
 """
 import numpy as np
 import pytest
@@ -140,3 +140,27 @@ def test_delayed_schedule_still_learns():
     bd = 8 * sum(len(s) for s in d["streams"]) / x.size
     assert ba < H + 0.25 and bd < H + 0.25, (H, ba, bd)
     assert abs(bd - ba) <= 0.01 * ba, (ba, bd)
+
+
+def test_delayed_update_uses_the_rows_active_at_the_gradients_step():
+    # Stream 0 (K + 2 bytes) is active at steps K and K + 1 only, stream 1
+    # (K + 6 bytes) throughout. The update after step K + 2 applies g_{K+1},
+    # so stream 0's FDM still moves then, with its own gradient of step K + 1.
+    from oracle.compress import archive_split
+    cfg = tiny(3)
+    K = cfg.context
+    sizes = [K + 2, K + 6]
+    sp = archive_split(sizes, 100)
+    x = data(sum(sizes), 13)
+    b, off, ln = sp
+    i = K + 1
+    rows = np.nonzero(ln > i)[0]
+    assert list(rows) == [0, 1]
+    _, g, dU, _ = Model(cfg, b).grad_step(_contexts(x, off, rows, i, K), x[off[rows] + i].astype(np.int64), rows)
+    want = oracle_compress(x, cfg, 0, split=sp, max_steps=1)["model"]
+    want.adam(g, dU, rows)
+    got = oracle_compress(x, cfg, 0, split=sp, max_steps=3, delayed=True)["model"]
+    assert same_state(got, want)
+    # stream 0's FDM did change in that update (it is inactive at step K + 2)
+    before = oracle_compress(x, cfg, 0, split=sp, max_steps=2, delayed=True)["model"]
+    assert not np.array_equal(got.U[0], before.U[0])
