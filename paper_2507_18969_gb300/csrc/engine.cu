@@ -1386,8 +1386,9 @@ int Model::step(const StepIO& io, cudaStream_t st) {
 
 // Step s of the delayed-update schedule (parity q = s % 2): the forward pass
 // and the head of step s on st with parity q; beside them, on bwd_st, the
-// adjoint of step s - 1 with parity q ^ 1 (its FDM adjoint writes the FDMs of
-// step s + 1, from those of step s, over parity q ^ 1's); then, after both,
+// adjoint of step s - 1 with parity q ^ 1 (its FDM update, launched on
+// side_fdm, writes the FDMs of step s + 1, from those of step s, over parity
+// q ^ 1's; the FDM forward of step s + 1 waits for it); then, after both,
 // Adam writes the parameters of step s + 1 into parity q ^ 1 from parity q's
 // and the gradient of step s - 1, with step s - 1's Adam counter.
 int Model::step_delayed(const StepIO& io, cudaStream_t st) {
