@@ -809,8 +809,6 @@ int Model::build_tc_sites() {
     g.K = K;
     g.bn = bn;
     g.persistent = (tile_code[id] & 16) != 0;
-    g.mcast = g.persistent ? 1 << ((tile_code[id] >> 5) & 3) : 1;
-    box_b /= g.mcast;  // each CTA of a multicast cluster loads 1/mcast of the B tile
     g.box_b = box_b;
     g.err = &ctl->err;
     if (precision == EDPC_FP8E4M3) {
@@ -1023,26 +1021,27 @@ void Model::tunable_sites(std::vector<int>* ids) const {
 }
 
 // Tile codes: 0 (size heuristic), or w + v with w in {1, 2, 4, 8} and v in
-// {0, 16, 48, 80}. The N tile (for the fused branch GEMM: the section of
-// hidden units per branch) is 32 * w, capped at the widest the site supports
-// (128 for the branch adjoint; k sections of at most 128 within 256 columns
-// for the branch GEMM). v selects the kernel: 0 one tile per CTA, 16
-// persistent, 48 / 80 persistent in clusters of 2 / 4 that multicast B (BF16
-// only). Every kernel gives the same results for the same tile.
+// {0, 16}. The N tile (for the fused branch GEMM: the section of hidden units
+// per branch) is 32 * w, capped at the widest the site supports (128 for the
+// branch adjoint; k sections of at most 128 within 256 columns for the branch
+// GEMM). v selects the kernel: 0 one tile per CTA, 16 persistent. Both kernels
+// give the same results for the same tile. (Codes with v = 48 or 80 named
+// kernels that are no longer built; containers that carry them are refused.)
 bool Model::tile_code_ok(int, uint8_t c) const {
   if (c == 0) return true;
   const int w = c & 15, v = c >> 4;
   if (w != 1 && w != 2 && w != 4 && w != 8) return false;
-  if (v == 0 || v == 1) return true;
-  return (v == 3 || v == 5) && precision == EDPC_BF16;
+  return v == 0 || v == 1;
 }
 
 int Model::set_tiles(const uint8_t* code, int n) {
   if (precision == EDPC_FP32) return EDPC_OK;
+  // validate every code before any is taken, so a refused set leaves the plan as it was
+  for (int i = 0; i < TcPlan::kMaxSites; ++i) {
+    const uint8_t c = (code && i < n) ? code[i] : 0;
+    if (!tile_code_ok(i, c)) return fail(EDPC_EARCH, "unknown GEMM tile code " + std::to_string(c));
+  }
   for (int i = 0; i < TcPlan::kMaxSites; ++i) tile_code[i] = (code && i < n) ? code[i] : 0;
-  for (int i = 0; i < TcPlan::kMaxSites; ++i)
-    if (!tile_code_ok(i, tile_code[i]))
-      return fail(EDPC_EARCH, "unknown GEMM tile code " + std::to_string(tile_code[i]));
   return build_tc_plan();
 }
 
@@ -1064,13 +1063,13 @@ int Model::tune_tiles(cudaStream_t st) {
     float best = 1e30f;
     uint8_t best_code = 1;
     int seen[16] = {}, nseen = 0;
-    static const uint8_t kCodes[] = {1, 2, 4, 8, 17, 18, 20, 24, 49, 50, 52, 56, 81, 82, 84, 88};
+    static const uint8_t kCodes[] = {1, 2, 4, 8, 17, 18, 20, 24};
     for (uint8_t code : kCodes) {
       if (!tile_code_ok(id, code)) continue;
       tile_code[id] = code;
       if ((r = build_tc_plan()) != EDPC_OK) break;
       // a capped code repeats a (tile, kernel) pair already timed
-      const int key = tcp.site[id].bn * 16 + (tcp.site[id].persistent ? 8 : 0) + tcp.site[id].mcast;
+      const int key = tcp.site[id].bn * 16 + (tcp.site[id].persistent ? 8 : 0);
       bool dup = false;
       for (int q = 0; q < nseen; ++q) dup |= seen[q] == key;
       if (dup) continue;

@@ -315,7 +315,6 @@ cudaError_t launch_gemm_tc_t(const TcGemm& g, cudaStream_t st) {
       return cudaErrorInvalidValue;
   }
   if (g.persistent) return launch_gemm_tcp(g, st);  // checks the tile against the box itself
-  if (g.mcast != 1) return cudaErrorInvalidValue;
   if (g.mode == TC_BRANCH) {
     // box_b = section width; bn = k sections
     if (g.bn != g.k * g.box_b) return cudaErrorInvalidValue;

@@ -43,10 +43,6 @@ struct TcGemm {
   // Same K order and epilogue arithmetic as the one-tile kernel, so the
   // results are identical for the same bn.
   bool persistent = false;
-  // Persistent kernel only: clusters of mcast (1, 2 or 4; BF16) CTAs along M
-  // share each B tile through TMA multicast; tb's box is then bn / mcast rows
-  // (TC_BRANCH: section / mcast). Same results as mcast = 1.
-  int mcast = 1;
   // Output tensor maps (FP32 C and BF16 Cb, boxes of 32 x 32, built by
   // tc_build_out_maps when the outputs are 16-byte aligned): whole 32 x 32
   // chunks are written by TMA stores from shared memory.
@@ -83,10 +79,8 @@ int make_tmap_bf16(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t co
 int make_tmap_u8(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
 
 cudaError_t launch_gemm_tc(const TcGemm& g, cudaStream_t st);
-// The persistent kernel (g.persistent), dispatched by launch_gemm_tc; its
-// multicast variants (g.mcast > 1).
+// The persistent kernel (g.persistent), dispatched by launch_gemm_tc.
 cudaError_t launch_gemm_tcp(const TcGemm& g, cudaStream_t st);
-cudaError_t launch_gemm_tcp_mc(const TcGemm& g, cudaStream_t st);
 
 // Builds g's output tensor maps (C over its logical columns: N for TC_PLAIN,
 // k * H for the branch modes; Cb likewise, H for TC_BRANCH). Returns 0 or an

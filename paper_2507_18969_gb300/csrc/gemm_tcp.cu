@@ -1,6 +1,5 @@
-// Persistent tcgen05 GEMM (gemm_tcp_kernel.cuh): launches without clusters,
-// BF16 and FP8, every epilogue mode; the multicast variants are built in
-// gemm_tcp_mc.cu.
+// Persistent tcgen05 GEMM (gemm_tcp_kernel.cuh): BF16 and FP8, every
+// epilogue mode.
 #include "gemm_tcp_kernel.cuh"
 
 namespace edpc {
@@ -21,8 +20,7 @@ int sm_count() {
 }  // namespace tcp
 
 cudaError_t launch_gemm_tcp(const TcGemm& g, cudaStream_t st) {
-  if (g.mcast > 1) return g.fp8 ? cudaErrorInvalidValue : launch_gemm_tcp_mc(g, st);
-  return g.fp8 ? tcp::launch_tcp_t<true, 1>(g, st) : tcp::launch_tcp_t<false, 1>(g, st);
+  return g.fp8 ? tcp::launch_tcp_t<true>(g, st) : tcp::launch_tcp_t<false>(g, st);
 }
 
 }  // namespace edpc

@@ -12,14 +12,8 @@
 //                      rows) with tcgen05.ld, runs the fused epilogue and
 //                      releases the accumulator (one arrival per warp), so
 //                      tile i's epilogue overlaps tile i+1's main loop.
-// With CM > 1 the CTAs run in clusters of CM along x. A cluster takes CM
-// consecutive M tiles of one N tile: each CTA loads its own A tile and 1/CM
-// of the shared B tile, multicast to the whole cluster, so the B operand is
-// read from L2 once per cluster instead of once per CTA. A stage is refilled
-// only after every CTA of the cluster has consumed it (each MMA warp's commit
-// arrives on the "empty" barrier of every CTA in the cluster).
-// Work unit u = cluster index, cluster index + cluster count, ... (N tile
-// fastest, then the group of CM M tiles, then the split-K index).
+// Work unit u = blockIdx.x, blockIdx.x + gridDim.x, ... (N tile fastest, then
+// the M tile, then the split-K index).
 // Each tile's MMAs run over K in the same order as in the one-tile kernel and
 // the epilogue is the same code, so every variant gives identical results for
 // the same N tile. Every wait is bounded; on expiry the kernel records
@@ -51,7 +45,7 @@ constexpr size_t psmem_bytes() {
 }
 static_assert(psmem_bytes<256>() <= 232448 && psmem_bytes<128>() <= 232448, "shared memory per CTA");
 
-template <int BN, int MODE, int KB, bool F8, int CM>
+template <int BN, int MODE, int KB, bool F8>
 __global__ void __launch_bounds__(192, 1)
     gemm_tcp_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
                     const __grid_constant__ CUtensorMap tmc, const __grid_constant__ CUtensorMap tmcb, const TcEpi e,
@@ -63,13 +57,9 @@ __global__ void __launch_bounds__(192, 1)
   constexpr int BK = bk_elems<F8>();
   constexpr int SECTIONS = (MODE == TC_BRANCH) ? KB : 1;
   constexpr int SW = BN / SECTIONS;   // rows of B per section (TC_BRANCH)
-  constexpr int SLICE = SW / CM;      // rows of each section one CTA loads (and multicasts)
   constexpr uint32_t ACC = (uint32_t)tmem_cols<BN>();  // columns of one accumulator
-  constexpr uint16_t MASK = (uint16_t)((1u << CM) - 1u);
   static_assert(SW % 32 == 0, "sections are whole 32-column TMEM chunks");
   static_assert(2 * ACC <= 512, "two accumulators must fit TMEM");
-  static_assert(CM == 1 || CM == 2 || CM == 4, "cluster of 1, 2 or 4");
-  static_assert(SLICE % 8 == 0, "a multicast slice is whole 1024-byte swizzle atoms");
   uint8_t* sA = smem;
   uint8_t* sB = sA + STAGES * A_BYTES;
   __nv_bfloat16* sT = reinterpret_cast<__nv_bfloat16*>(sB + STAGES * B_BYTES);
@@ -83,11 +73,8 @@ __global__ void __launch_bounds__(192, 1)
   volatile int* sk_flag = reinterpret_cast<volatile int*>(tmem_slot + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t rank = 0;
-  if (CM > 1) asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-  const int cid = blockIdx.x / CM, ncl = gridDim.x / CM;
-  const int ntg = (e.ntm + CM - 1) / CM;  // groups of CM M tiles
-  const int nunits = e.ntn * ntg * nsplit;
+  const int cid = blockIdx.x, ncl = gridDim.x;
+  const int nunits = e.ntn * e.ntm * nsplit;
   const int nk_all = (e.K + BK - 1) / BK;
   struct Tile {
     int m0, n0, z, lo, nk, ci;
@@ -95,9 +82,9 @@ __global__ void __launch_bounds__(192, 1)
   auto decode = [&](int u) {
     Tile q;
     const int tn = u % e.ntn, rest = u / e.ntn;
-    const int tm = (rest % ntg) * CM + (int)rank;
-    q.z = rest / ntg;
-    q.m0 = tm * BM;  // at or beyond M for the spare CTAs of a last, partial group
+    const int tm = rest % e.ntm;
+    q.z = rest / e.ntm;
+    q.m0 = tm * BM;
     q.n0 = (MODE == TC_BRANCH) ? tn * SW : tn * BN;
     q.lo = (int)(((long long)nk_all * q.z) / nsplit);
     q.nk = (int)(((long long)nk_all * (q.z + 1)) / nsplit) - q.lo;
@@ -108,7 +95,7 @@ __global__ void __launch_bounds__(192, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], CM);  // one MMA commit from every CTA of the cluster
+      mbar_init(&empty[s], 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(&tfull[a], 1);
@@ -126,7 +113,6 @@ __global__ void __launch_bounds__(192, 1)
   }
   tc_fence_before();
   __syncthreads();
-  if (CM > 1) cluster_sync_all();  // every CTA's barriers exist before any multicast reaches them
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   pdl_wait();
@@ -150,24 +136,10 @@ __global__ void __launch_bounds__(192, 1)
           const int kc = (q.lo + kb) * BK;
 #pragma unroll
           for (int i = 0; i < SECTIONS; ++i) {
-            const int brow = (MODE == TC_BRANCH ? i * e.H : 0) + q.n0 + (int)rank * SLICE;
-            uint8_t* dst = sB + s * B_BYTES + (i * SW + (int)rank * SLICE) * BKB;
-            if (CM > 1)
-              tma_load_2d_mc(dst, &tb, kc, brow, &full[s], MASK);
-            else
-              tma_load_2d(dst, &tb, kc, brow, &full[s]);
+            const int brow = (MODE == TC_BRANCH ? i * e.H : 0) + q.n0;
+            tma_load_2d(sB + s * B_BYTES + i * SW * BKB, &tb, kc, brow, &full[s]);
           }
           tma_load_2d(sA + s * A_BYTES, &ta, kc, q.m0, &full[s]);
-        }
-      }
-      if (CM > 1 && go) {
-        // Producer tail: wait until every CTA of the cluster has released the
-        // last use of each stage, so that no commit from a peer is still on
-        // its way to this CTA's barriers when it exits.
-        for (int s = 0; s < STAGES; ++s) {
-          if (it <= (uint32_t)s) continue;
-          const uint32_t uses = (it - (uint32_t)s + STAGES - 1) / STAGES;
-          if (!mbar_wait(&empty[s], (uses - 1) & 1u, abort_flag)) break;
         }
       }
     }
@@ -202,10 +174,7 @@ __global__ void __launch_bounds__(192, 1)
             else
               mma_bf16(dt, ad, bd, idesc, (kb > 0 || k > 0) ? 1u : 0u);
           }
-          if (CM > 1)
-            mma_commit_mc(&empty[s], MASK);
-          else
-            mma_commit(&empty[s]);
+          mma_commit(&empty[s]);
         }
         if (go) mma_commit(&tfull[a]);
       }
@@ -242,7 +211,6 @@ __global__ void __launch_bounds__(192, 1)
         if (mbar_try_wait(&full[s], 0) || mbar_try_wait(&full[s], 1)) break;
     }
   }
-  if (CM > 1) cluster_sync_all();  // no CTA leaves while a peer may still address it
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * ACC));
@@ -251,38 +219,20 @@ __global__ void __launch_bounds__(192, 1)
 
 int sm_count();
 
-template <int BN, int MODE, int KB, bool F8, int CM>
+template <int BN, int MODE, int KB, bool F8>
 cudaError_t launch_p(const TcGemm& g, cudaStream_t st) {
-  auto k = gemm_tcp_kernel<BN, MODE, KB, F8, CM>;
+  auto k = gemm_tcp_kernel<BN, MODE, KB, F8>;
   constexpr int SW = (MODE == TC_BRANCH) ? BN / KB : BN;
-  // the tensor map's box must be one CTA's slice of B
-  if (g.box_b * CM != SW) return cudaErrorInvalidValue;
+  // the tensor map's box must be one section of B
+  if (g.box_b != SW) return cudaErrorInvalidValue;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
-  static int max_clusters = 0;
+  static int max_ctas = 0;
   std::call_once(once, [&] {
     attr_err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem_bytes<BN>());
     if (attr_err == cudaSuccess)
       attr_err = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    max_clusters = sm_count() / CM;
-    if (attr_err == cudaSuccess && CM > 1) {
-      // clusters must fit inside a GPC: ask how many can be resident at once
-      cudaLaunchConfig_t cfg{};
-      cfg.gridDim = dim3(CM * max_clusters);
-      cfg.blockDim = dim3(192);
-      cfg.dynamicSmemBytes = psmem_bytes<BN>();
-      cudaLaunchAttribute at[1];
-      at[0].id = cudaLaunchAttributeClusterDimension;
-      at[0].val.clusterDim.x = CM;
-      at[0].val.clusterDim.y = 1;
-      at[0].val.clusterDim.z = 1;
-      cfg.attrs = at;
-      cfg.numAttrs = 1;
-      int n = 0;
-      attr_err = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
-      if (attr_err == cudaSuccess && n > 0 && n < max_clusters) max_clusters = n;
-      if (attr_err == cudaSuccess && n <= 0) attr_err = cudaErrorInvalidConfiguration;
-    }
+    max_ctas = sm_count();
   });
   if (attr_err != cudaSuccess) return attr_err;
   const int ntn = (MODE == TC_BRANCH) ? (g.H + SW - 1) / SW : (g.N + BN - 1) / BN;
@@ -290,51 +240,49 @@ cudaError_t launch_p(const TcGemm& g, cudaStream_t st) {
   const int S = g.splitk > 1 ? g.splitk : 1;
   TcEpi e{g.M, g.N, g.K, g.H, g.k, g.C, g.ldc, g.Cb, g.ldcb, g.CbT, g.ldct, g.bias, g.R, g.ldr, g.Aux, g.ldaux, g.err,
           g.inv_a, g.inv_b, 0, g.ws, g.cnt, ntn, ntm, g.has_tmc ? 1 : 0, g.has_tmcb ? 1 : 0};
-  const long long units = (long long)ntn * ((ntm + CM - 1) / CM) * S;
+  const long long units = (long long)ntn * ntm * S;
   if (units <= 0 || units > (1ll << 30)) return cudaErrorInvalidValue;
-  const int ncl = (int)(units < max_clusters ? units : max_clusters);
-  if (CM == 1) return launch_k(k, dim3(ncl), dim3(192), psmem_bytes<BN>(), st, g.ta, g.tb, g.tmc, g.tmcb, e, S);
-  return launch_kc(k, dim3(ncl * CM), dim3(192), psmem_bytes<BN>(), (unsigned)CM, st, g.ta, g.tb, g.tmc, g.tmcb, e,
-                   S);
+  const int nct = (int)(units < max_ctas ? units : max_ctas);
+  return launch_k(k, dim3(nct), dim3(192), psmem_bytes<BN>(), st, g.ta, g.tb, g.tmc, g.tmcb, e, S);
 }
 
-// Dispatch on (mode, k, tile) for one cluster size.
-template <bool F8, int CM>
+// Dispatch on (mode, k, tile).
+template <bool F8>
 cudaError_t launch_tcp_t(const TcGemm& g, cudaStream_t st) {
   if (g.mode == TC_BRANCH) {
-    if (g.bn != g.k * g.box_b * CM) return cudaErrorInvalidValue;
-    switch (g.k * 1000 + g.box_b * CM) {
-      case 1032: return launch_p<32, TC_BRANCH, 1, F8, CM>(g, st);
-      case 1064: return launch_p<64, TC_BRANCH, 1, F8, CM>(g, st);
-      case 1128: return launch_p<128, TC_BRANCH, 1, F8, CM>(g, st);
-      case 2032: return launch_p<64, TC_BRANCH, 2, F8, CM>(g, st);
-      case 2064: return launch_p<128, TC_BRANCH, 2, F8, CM>(g, st);
-      case 2128: return launch_p<256, TC_BRANCH, 2, F8, CM>(g, st);
-      case 3032: return launch_p<96, TC_BRANCH, 3, F8, CM>(g, st);
-      case 3064: return launch_p<192, TC_BRANCH, 3, F8, CM>(g, st);
+    if (g.bn != g.k * g.box_b) return cudaErrorInvalidValue;
+    switch (g.k * 1000 + g.box_b) {
+      case 1032: return launch_p<32, TC_BRANCH, 1, F8>(g, st);
+      case 1064: return launch_p<64, TC_BRANCH, 1, F8>(g, st);
+      case 1128: return launch_p<128, TC_BRANCH, 1, F8>(g, st);
+      case 2032: return launch_p<64, TC_BRANCH, 2, F8>(g, st);
+      case 2064: return launch_p<128, TC_BRANCH, 2, F8>(g, st);
+      case 2128: return launch_p<256, TC_BRANCH, 2, F8>(g, st);
+      case 3032: return launch_p<96, TC_BRANCH, 3, F8>(g, st);
+      case 3064: return launch_p<192, TC_BRANCH, 3, F8>(g, st);
       default: return cudaErrorInvalidValue;
     }
   }
-  if (g.box_b * CM != g.bn) return cudaErrorInvalidValue;
+  if (g.box_b != g.bn) return cudaErrorInvalidValue;
   if (g.mode == TC_BRANCH_BWD) {
     switch (g.k * 1000 + g.bn) {
-      case 1032: return launch_p<32, TC_BRANCH_BWD, 1, F8, CM>(g, st);
-      case 2032: return launch_p<32, TC_BRANCH_BWD, 2, F8, CM>(g, st);
-      case 3032: return launch_p<32, TC_BRANCH_BWD, 3, F8, CM>(g, st);
-      case 1064: return launch_p<64, TC_BRANCH_BWD, 1, F8, CM>(g, st);
-      case 2064: return launch_p<64, TC_BRANCH_BWD, 2, F8, CM>(g, st);
-      case 3064: return launch_p<64, TC_BRANCH_BWD, 3, F8, CM>(g, st);
-      case 1128: return launch_p<128, TC_BRANCH_BWD, 1, F8, CM>(g, st);
-      case 2128: return launch_p<128, TC_BRANCH_BWD, 2, F8, CM>(g, st);
-      case 3128: return launch_p<128, TC_BRANCH_BWD, 3, F8, CM>(g, st);
+      case 1032: return launch_p<32, TC_BRANCH_BWD, 1, F8>(g, st);
+      case 2032: return launch_p<32, TC_BRANCH_BWD, 2, F8>(g, st);
+      case 3032: return launch_p<32, TC_BRANCH_BWD, 3, F8>(g, st);
+      case 1064: return launch_p<64, TC_BRANCH_BWD, 1, F8>(g, st);
+      case 2064: return launch_p<64, TC_BRANCH_BWD, 2, F8>(g, st);
+      case 3064: return launch_p<64, TC_BRANCH_BWD, 3, F8>(g, st);
+      case 1128: return launch_p<128, TC_BRANCH_BWD, 1, F8>(g, st);
+      case 2128: return launch_p<128, TC_BRANCH_BWD, 2, F8>(g, st);
+      case 3128: return launch_p<128, TC_BRANCH_BWD, 3, F8>(g, st);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (g.bn) {
-    case 32: return launch_p<32, TC_PLAIN, 1, F8, CM>(g, st);
-    case 64: return launch_p<64, TC_PLAIN, 1, F8, CM>(g, st);
-    case 128: return launch_p<128, TC_PLAIN, 1, F8, CM>(g, st);
-    case 256: return launch_p<256, TC_PLAIN, 1, F8, CM>(g, st);
+    case 32: return launch_p<32, TC_PLAIN, 1, F8>(g, st);
+    case 64: return launch_p<64, TC_PLAIN, 1, F8>(g, st);
+    case 128: return launch_p<128, TC_PLAIN, 1, F8>(g, st);
+    case 256: return launch_p<256, TC_PLAIN, 1, F8>(g, st);
     default: return cudaErrorInvalidValue;
   }
 }
