@@ -396,7 +396,9 @@ int edpc_range_encode(const uint32_t* sym, uint32_t nsym, uint32_t streams, uint
  *     EDPC_EINVAL before any GPU work.
  *   - The first call on each device looks up the scratch's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture on the device.
+ *     before any stream capture on the device. The address is kept for the
+ *     life of the process, so after a cudaDeviceReset of a device this entry
+ *     point must not be called on that device again.
  *   - Every call on a device uses the same scratch and re-initialises it.
  *     Calls whose GPU work overlaps (different streams or threads, same
  *     device) race on it and must be serialised by the caller.

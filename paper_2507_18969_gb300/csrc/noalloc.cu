@@ -28,7 +28,11 @@ static __device__ __align__(256) unsigned char g_coder_scratch[kScratchBytes];
 
 // Device address of g_coder_scratch per device. In host code the symbol is
 // only a host-side stand-in, so the address must come from
-// cudaGetSymbolAddress with the device current.
+// cudaGetSymbolAddress with the device current. The address is looked up
+// once per device and kept for the life of the process: it stays valid as
+// long as the device's primary context does. A cudaDeviceReset destroys that
+// context (and the module image with the array), so a process that resets a
+// device must not call this entry point on it again.
 constexpr int kMaxDevices = 64;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
 std::mutex g_scratch_mu;

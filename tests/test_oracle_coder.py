@@ -26,6 +26,45 @@ def test_quantize_one_hot_closed_form():
     assert cum[-1] == T
 
 
+@pytest.mark.parametrize("idx,pmax,rest,fmax,frest,rem", [
+    # two symbols tie at the largest frequency; the other 254 share the rest
+    ((3, 7), 0.4, 0.2 / 254, 26113, 52, 102),
+    ((9, 200), 0.4, 0.2 / 254, 26113, 52, 102),
+    # a three-way tie that includes the first and the last symbol
+    ((0, 128, 255), 0.3, 0.1 / 253, 19585, 26, 203),
+])
+def test_quantize_tie_gives_the_remainder_to_the_lowest_index(idx, pmax, rest, fmax, frest, rem):
+    """Tied largest frequencies: the remainder T - sum(f) lands on the lowest
+    tied index only (the quantizer's tie rule). Hand arithmetic: fl32(0.4) *
+    65280 = 26112.0004 rounds to 26112.0 in FP32, so f = 26113;
+    fl32(0.2/254) * 65280 = 51.40, f = 52; 2 * 26113 + 254 * 52 = 65434, so
+    the remainder is 102. fl32(0.3) * 65280 = 19584.0008 -> 19584.0, f = 19585;
+    fl32(0.1/253) * 65280 = 25.80, f = 26; 3 * 19585 + 253 * 26 = 65333,
+    remainder 203."""
+    p = np.full(256, rest, dtype=np.float32)
+    p[list(idx)] = pmax
+    f, cum = quantize_cdf(p)
+    expect = np.full(256, frest, dtype=np.int64)
+    expect[list(idx)] = fmax
+    expect[min(idx)] += rem
+    assert np.array_equal(f, expect)
+    assert cum[-1] == T
+
+
+def test_quantize_strict_maximum_after_a_tie_takes_the_remainder():
+    """The remainder goes to the largest f even when a pair of smaller f tie
+    earlier: p[1] = p[2] = 0.2 and p[250] = 0.4; the rest share 0.2."""
+    p = np.full(256, 0.2 / 253, dtype=np.float32)
+    p[[1, 2]] = 0.2
+    p[250] = 0.4
+    f, _ = quantize_cdf(p)
+    # 1 + floor(fl32(0.2) * 65280) = 1 + 13056; 1 + floor(fl32(0.2/253) * 65280) = 1 + 51
+    assert f[1] == f[2] == 13057
+    base = 2 * 13057 + 26113 + 253 * 52
+    assert f[250] == 26113 + (T - base)
+    assert np.all(np.delete(f, [1, 2, 250]) == 52)
+
+
 @pytest.mark.parametrize("alpha", [0.01, 0.1, 1.0, 10.0])
 def test_quantize_invariants_and_error_bound(alpha):
     rng = np.random.default_rng(3)

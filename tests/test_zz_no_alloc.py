@@ -62,3 +62,43 @@ def test_noalloc_rejects_more_streams_than_its_scratch_holds():
         edpc.range_encode_noalloc(sym.data_ptr(), 1, n, out.data_ptr(), 16, ln.data_ptr())
     assert e.value.code == 1
     assert "EDPC_NOALLOC_MAX_STREAMS" in str(e.value)
+
+
+def _encode_status(fn, sym, streams, cap):
+    """Like _encode, but returns the error code (0 if none) with the outputs."""
+    nsym = sym.shape[0]
+    sd = torch.from_numpy(sym.view(np.int32)).cuda()
+    out = torch.full((streams * cap,), 0xAB, dtype=torch.uint8, device="cuda")
+    ln = torch.zeros(streams, dtype=torch.int32, device="cuda")
+    code = 0
+    try:
+        fn(sd.data_ptr(), nsym, streams, out.data_ptr(), cap, ln.data_ptr())
+    except edpc.EdpcError as e:
+        code = e.code
+    return code, out.cpu().numpy(), ln.cpu().numpy().view(np.uint32)
+
+
+def test_noalloc_overflow_matches_allocating_encoder():
+    """Streams that need more than cap bytes: both entry points report
+    EDPC_EINVAL, clamp those streams' lengths to cap, and write identical bytes
+    for every stream (the overflowing ones truncated at cap)."""
+    streams, nsym, cap = 301, 300, 300
+    sym = np.empty((nsym, streams), dtype=np.uint32)
+    sym[:, 0::2] = 0 | (65534 << 16)  # cum 0, f 65535: almost free
+    sym[:, 1::2] = 100                # cum 100, f 1: 16 bits per symbol, 600 bytes > cap
+    sym[::7, 2::3] = 0xFFFFFFFF       # some skipped steps
+    ref = _encode_status(edpc.range_encode, sym, streams, cap)
+    got = _encode_status(edpc.range_encode_noalloc, sym, streams, cap)
+    assert ref[0] == got[0] == 1  # EDPC_EINVAL
+    assert np.array_equal(got[2], ref[2])
+    over = sym[:, :] == 100
+    odd_full = np.array([over[:, s].sum() * 2 > cap for s in range(streams)])
+    assert np.all(ref[2][odd_full] == cap) and np.all(ref[2][~odd_full] < cap)
+    for s in range(streams):
+        n = int(ref[2][s])
+        assert bytes(got[1][s * cap:s * cap + n]) == bytes(ref[1][s * cap:s * cap + n]), s
+    # a clean call right after the failed one matches again (the shared flag was reset)
+    sym_ok = np.full((40, 5), 0 | (65534 << 16), dtype=np.uint32)
+    a = _encode_status(edpc.range_encode, sym_ok, 5, 64)
+    b = _encode_status(edpc.range_encode_noalloc, sym_ok, 5, 64)
+    assert a[0] == b[0] == 0 and np.array_equal(a[2], b[2])
