@@ -16,9 +16,13 @@ the launching stream, bracketed by a barrier and a device synchronize.
 value     compress MB/s (1e6 input bytes / s) with the input resident in HBM.
 e2e       the same metric through edpc_compress on a host (pinned) buffer:
           host->device input copy, every step, flush, device->host container.
-          Timed on the first P bytes of each stream (P = K + (W + K + 2) * 64).
-Also      decompress MB/s (device-resident, same prefix input, lossless check),
-          FP32 compress MB/s, bits/byte, the FDM kernels' roofline, clocks.
+          On the whole input for mix64m (about 50 s); on the first
+          P = K + (W + K + 2) * 64 bytes of each stream for the others unless
+          --whole is given.
+Also      decompress MB/s (device-resident output; the e2e container is then
+          decoded to its end and compared with the input), FP32 compress
+          MB/s, bits/byte of the e2e input, the FDM kernels' roofline, the
+          model step against its HBM floor, the GEMM sites, clocks.
 
 `--impl reference` times the CPU oracle (FP64 NumPy) on the same workload:
 each step is one model step of the workload's streams (a sample of 256 of
@@ -26,6 +30,31 @@ them for mix1g).
 
 With N GPUs (torchrun), each rank compresses its own replica (a different
 seed); the value is the total bytes of all ranks over the slowest rank's time.
+
+Timing cases (named models on device-resident random bytes; the ncu profiles
+under profiles/ are taken with these):
+
+  python bench.py case steps CASE [CHUNKS [delayed]]
+      An encoder session on CASE's model and stream count over random bytes
+      already on the device (the kernels' work does not depend on the byte
+      values): one warm-up chunk of 64 model steps, then CHUNKS timed chunks;
+      prints milliseconds per model step (CUDA events). "delayed" selects the
+      delayed-update schedule (EDPC_FLAG_DELAYED_UPDATE).
+  python bench.py case gemm CASE CODE
+      Every tcgen05 GEMM site of CASE's model with every tile code set to CODE
+      (0: the size heuristic), each launched alone (Model.time_gemms): ms,
+      GFLOP and TFLOP/s per site.
+  python bench.py case ifr [STEPS]
+      Sec. 3.1.1's Information Flow Refinement on the 64 MiB mix: models with
+      1, 2 and 3 MBRB branches (c1's dims) each take STEPS online steps on the
+      first bytes of its 512 streams; then, on the next contexts, every
+      block's skip input S and fused output S + X^(k) give I^(k) (Kraskov, 3
+      neighbours, on the GPU), and IFR_{k1->k2} = I^(k1) / I^(k2).
+
+  Cases: c1 (K=32, F'=256, 4 MBRBs of 256; 512 streams, the 64 MiB workload's
+  model), c1_32k (the same model, 32768 streams), c4 (K=64, F'=512, 6 MBRBs of
+  512; 4096 streams, the 1 GiB workload's model) and c4_gemm (c4's F, H and
+  stream count with F'=16 and 2 blocks: c4's GEMM shapes in well under 1 GB).
 """
 from __future__ import annotations
 
@@ -69,6 +98,104 @@ PROFILES = os.path.join(ROOT, "profiles")
 KERNEL_SRC = os.path.join(ROOT, "paper_2507_18969_gb300", "csrc", "kernels.cu")
 
 
+# --------------------------------------------------------------------------------------------
+# timing cases (python bench.py case ...)
+# --------------------------------------------------------------------------------------------
+CASES = {
+    "c1": dict(b=512, K=32, Fp=256, H=256, n=4),
+    "c1_32k": dict(b=32768, K=32, Fp=256, H=256, n=4),
+    "c4": dict(b=4096, K=64, Fp=512, H=512, n=6),
+    "c4_gemm": dict(b=4096, K=64, Fp=16, H=512, n=2),
+}
+
+
+def case_cfg(c, edpc, **kw):
+    return edpc.make_cfg(streams=c["b"], context=c["K"], embed_dim=16, latent=c["Fp"], hidden=c["H"], blocks=c["n"],
+                         branches=2, lr=1e-3, seed=1, precision=edpc.EDPC_BF16, **kw)
+
+
+def case_steps(name: str, chunks: int = 2, delayed: bool = False) -> dict:
+    import torch
+    import paper_2507_18969_gb300 as edpc
+    c = CASES[name]
+    n = c["b"] * (c["K"] + (chunks + 2) * 64 + 8)
+    x = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    flags = edpc.EDPC_FLAG_DELAYED_UPDATE if delayed else 0
+    enc = edpc.Encoder(case_cfg(c, edpc, flags=flags), device_ptr=x.data_ptr(), length=n, stream=st.cuda_stream)
+    enc.run(64)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    done = enc.run(64 * chunks)
+    e1.record(st)
+    torch.cuda.synchronize()
+    enc.close()
+    ms = e0.elapsed_time(e1) / done
+    return dict(case=name, streams=c["b"], delayed=delayed, ms_per_model_step=ms, mbs=c["b"] / ms / 1e3)
+
+
+def case_gemm(name: str, code: int) -> list[dict]:
+    import paper_2507_18969_gb300 as edpc
+    c = CASES[name]
+    m = edpc.Model(case_cfg(c, edpc), c["b"])
+    m.set_tiles(np.full(200, code, np.uint8))
+    ms, fl, _ = m.time_gemms(1)
+    m.close()
+    return [dict(site=int(i), gflop=fl[i] / 1e9, us=ms[i] * 1e3, tflops=fl[i] / ms[i] / 1e9) for i in np.nonzero(fl)[0]]
+
+
+def case_ifr(steps: int = 256) -> dict:
+    import torch
+    import paper_2507_18969_gb300 as edpc
+    import synth
+    c = CASES["c1"]
+    b, K = c["b"], c["K"]
+    x = synth.multimedia_mix(64 << 20, 20250719)
+    q = x.size // b
+    xs = x[: q * b].reshape(b, q)
+    res = {"steps": steps, "streams": b, "neighbours": 3, "mi_nats": {}, "ifr": {}}
+    for k in (1, 2, 3):
+        cfg = edpc.make_cfg(streams=b, context=K, embed_dim=16, latent=c["Fp"], hidden=c["H"], blocks=c["n"],
+                            branches=k, lr=1e-3, seed=1, precision=edpc.EDPC_BF16)
+        m = edpc.Model(cfg, b)
+        ones = np.ones(b, np.uint8)
+        for i in range(K, K + steps):
+            m.train_step(xs[:, i - K:i], xs[:, i], ones)
+        m.forward(np.ascontiguousarray(xs[:, steps + 1:steps + 1 + K]))
+        mis = []
+        for blk in range(c["n"]):
+            s, so = m.block_io(blk)
+            zs = torch.from_numpy(s).cuda()
+            ys = torch.from_numpy(so).cuda()
+            cz = torch.zeros(b, dtype=torch.int32, device="cuda")
+            cy = torch.zeros(b, dtype=torch.int32, device="cuda")
+            mis.append(edpc.ksg_mi(zs.data_ptr(), ys.data_ptr(), b, s.shape[1], so.shape[1], 3, cz.data_ptr(),
+                                   cy.data_ptr()))
+        m.close()
+        res["mi_nats"][str(k)] = mis
+    for k1, k2 in ((1, 2), (1, 3), (2, 3)):
+        res["ifr"][f"{k1}->{k2}"] = [a / bb for a, bb in zip(res["mi_nats"][str(k1)], res["mi_nats"][str(k2)])]
+    return res
+
+
+def run_case(argv) -> int:
+    if argv and argv[0] == "ifr":
+        print(json.dumps(case_ifr(int(argv[1]) if len(argv) > 1 else 256)), flush=True)
+        return 0
+    if len(argv) < 2 or argv[0] not in ("steps", "gemm") or argv[1] not in CASES:
+        print(__doc__)
+        return 2
+    if argv[0] == "steps":
+        print(json.dumps(case_steps(argv[1], int(argv[2]) if len(argv) > 2 else 2,
+                                    len(argv) > 3 and argv[3] == "delayed")), flush=True)
+    else:
+        for r in case_gemm(argv[1], int(argv[2]) if len(argv) > 2 else 0):
+            print(json.dumps(r), flush=True)
+    return 0
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -83,6 +210,9 @@ def parse():
                     help="also compress the whole workload in FP32, BF16 and FP8 e4m3 (bits/byte, MB/s)")
     ap.add_argument("--independent", action="store_true",
                     help="files1000: also compress and decode the sample as an archive of independent per-file models")
+    ap.add_argument("--whole", action="store_true",
+                    help="e2e leg on the whole input (the default for mix64m; about 25 min per direction for mix1g)")
+    ap.add_argument("--prefix-e2e", action="store_true", help="e2e leg on a prefix of each stream only")
     ap.add_argument("--ablation", action="store_true",
                     help="also compress and decode the whole workload with 3 MBRB branches and without the LTE")
     return ap.parse_args()
@@ -352,6 +482,7 @@ def run_ours(args, d: Dist):
     out.update(value=value, t=t_max, done=done, clocks=ck, stats=st, launches=launches)
 
     fp32_value = decomp_value = e2e = bpb = nopipe_value = delayed_value = bpb_delayed = st_dl = None
+    bpb_prefix = lossless = None
     if not args.quick:
         # ---- plain FP32 path, same workload ----------------------------------------------
         enc = edpc.Encoder(make_cfg(edpc.EDPC_FP32), device_ptr=xd.data_ptr(), length=x.size,
@@ -375,10 +506,14 @@ def run_ours(args, d: Dist):
         enc.close()
         delayed_value, _ = aggregate(donedl * b, tdl, d)
 
-        # ---- e2e through edpc_compress on pinned host memory (prefix input) --------------
+        # ---- e2e through edpc_compress on pinned host memory --------------------------------
+        # The whole input by default for the 64 MiB workload (and with --whole);
+        # else the first P bytes of each stream, P = K + (W + K + 2) * 64.
+        whole = (args.workload == "mix64m" or args.whole) and not args.prefix_e2e
         per = WORKLOAD["context"] + (W + K + 2) * CHUNK
         xp = prefix_input(x, per)
-        host = torch.from_numpy(xp).pin_memory()
+        xe = x if whole else xp
+        host = torch.from_numpy(xe).pin_memory()
         cfg = make_cfg(edpc.EDPC_BF16)
         import ctypes as C
         lib = edpc.load()
@@ -387,29 +522,39 @@ def run_ours(args, d: Dist):
         d.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = lib.edpc_compress(C.c_void_p(host.data_ptr()), xp.size, C.byref(cfg), C.byref(outp), C.byref(outn))
+        r = lib.edpc_compress(C.c_void_p(host.data_ptr()), xe.size, C.byref(cfg), C.byref(outp), C.byref(outn))
         t_e2e = time.perf_counter() - t0
         edpc._lib.check(r, "edpc_compress")
         bits = C.string_at(outp, outn.value)
         lib.edpc_free(outp)
         d.barrier()
-        e2e_value, _ = aggregate(xp.size, t_e2e, d)
-        n_chunks = (per - WORKLOAD["context"]) / CHUNK
-        e2e = {"value": e2e_value, "unit": "MB/s", "h2d_bytes_per_step": int(xp.size / n_chunks),
-               "d2h_bytes_per_step": int(len(bits) / n_chunks),
-               "input": f"first {per} bytes of each of the {b} streams ({xp.size} bytes), host pinned"}
+        e2e_value, _ = aggregate(xe.size, t_e2e, d)
+        n_chunks = (xe.size / b - WORKLOAD["context"]) / CHUNK
+        e2e = {"value": e2e_value, "unit": "MB/s", "h2d_bytes_per_step": int(xe.size / n_chunks),
+               "d2h_bytes_per_step": int(len(bits) / n_chunks), "seconds": t_e2e,
+               "input": (f"the whole input ({xe.size} bytes, {b} streams), host pinned" if whole else
+                         f"first {per} bytes of each of the {b} streams ({xe.size} bytes), host pinned")}
         _, n, be = edpc.peek(bits)
-        bpb = 8 * (len(bits) - (88 + 4 * be + 4)) / n
+        hdr = 88 + 4 * be + 4
+        bpb = {"value": 8 * (len(bits) - hdr) / n,
+               "input": "the whole input" if whole else f"the e2e prefix ({per} bytes of each stream)"}
+        bits_pre = edpc.compress(xp, make_cfg(edpc.EDPC_BF16)) if whole else bits
+        bpb_prefix = 8 * (len(bits_pre) - hdr) / xp.size
         bits_dl = edpc.compress(xp, make_cfg(edpc.EDPC_BF16, edpc.EDPC_FLAG_DELAYED_UPDATE))
-        bpb_delayed = 8 * (len(bits_dl) - (88 + 4 * be + 4)) / n
+        bpb_delayed = 8 * (len(bits_dl) - hdr) / xp.size
 
-        # ---- decompress, device-resident output, same prefix input ------------------------
-        outd = torch.empty(xp.size, dtype=torch.uint8, device="cuda")
+        # ---- decompress, device-resident output: the timed window, then the rest -----------
+        outd = torch.empty(xe.size, dtype=torch.uint8, device="cuda")
         dec = edpc.Decoder(bits, out_device_ptr=outd.data_ptr(), stream=stream.cuda_stream)
         tdec, donedec, _ = timed_session(dec, W, K, stream, d)
+        t1 = time.perf_counter()
         dec.finish(to_host=False)  # runs the tail and checks the data checksum
+        t_tail = time.perf_counter() - t1
         dec.close()
         assert torch.equal(outd.cpu(), host), "decompressed bytes differ from the input"
+        lossless = {"input_bytes": int(xe.size), "whole_input": whole, "identical": True,
+                    "decode_tail_seconds": t_tail}
+        del outd
         decomp_value, _ = aggregate(donedec * b, tdec, d)
 
     # ---- whole workload in each GEMM precision (bits/byte and throughput) ----------------------
@@ -520,6 +665,23 @@ def run_ours(args, d: Dist):
             "peak_source": "measured (burst, kernels timed alone)" if "bf16_tflops" in peaks else "fallback",
             "timing": "each site alone, CUDA events, mean of 8 launches after one warm-up"}
 
+    # ---- the model step against its bounds ----------------------------------------------------
+    # HBM floor: the FDM moves 28 B per element per model step (forward 4,
+    # adjoint + Adam 24); tensor floor: the step's GEMM FLOP at the sustained
+    # BF16 peak (the GEMMs run inside a long step). The step cannot be shorter
+    # than either; if nothing overlapped it could not be shorter than both.
+    step = None
+    if out["done"]:
+        step_ms = out["t"] / out["done"] * 1e3
+        hbm_ms = 28.0 * fdm_elems / (peak * 1e6)
+        tsus = peaks.get("bf16_tflops_sustained", 1700.0)
+        ten_ms = float(g_fl[used].sum()) / (tsus * 1e9)
+        step = {"model_step_ms": step_ms, "hbm_floor_ms": hbm_ms, "frac": hbm_ms / step_ms,
+                "alg_bytes_per_model_step": 28.0 * fdm_elems, "tensor_floor_ms": ten_ms,
+                "floor_ms_serial": hbm_ms + ten_ms, "frac_serial": (hbm_ms + ten_ms) / step_ms,
+                "bound": "hbm (FDM forward, adjoint and Adam: 28 B x b x F'^2 per model step)",
+                "peaks": f"HBM {peak:.0f} GB/s, BF16 {tsus:.0f} TFLOP/s sustained (measured)"}
+
     # ---- CPU oracle baseline ------------------------------------------------------------------
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.quick and not args.no_cpu_baseline:
@@ -537,7 +699,8 @@ def run_ours(args, d: Dist):
         # layers: its CUDA-event span (queueing included) bounds its rate from below
         upd = gbs(24 * fdm_elems, st_dl.fdm_adam_ms)
         delayed = {
-            "compress_mbs": delayed_value, "speedup": delayed_value / out["value"], "bits_per_byte": bpb_delayed,
+            "compress_mbs": delayed_value, "speedup": delayed_value / out["value"],
+            "bits_per_byte_prefix": bpb_delayed,
             "schedule": "gradient of step i applied after step i + 1; its adjoint runs beside the forward pass of "
                         "step i + 1 on a second stream (not Algorithm 1)",
             "fdm_update": {"kernel": "fdm_adam_kernel (Adam on U, m, v from the other parity)", "bound": "hbm",
@@ -564,10 +727,10 @@ def run_ours(args, d: Dist):
             "dpca_off_compress_mbs": nopipe_value,
             "dpca_speedup": (out["value"] / nopipe_value) if nopipe_value else None,
             "delayed_update": delayed,
-            "bits_per_byte": bpb,
-            "bits_per_byte_input": "the e2e prefix input (early, still-learning part of each stream)",
+            "bits_per_byte": bpb, "bits_per_byte_prefix": bpb_prefix, "lossless": lossless,
             "e2e": e2e, "gpu_launches": out["launches"],
-            "roofline": roof, "gemm_roofline": gemm, "cpu_baseline": cpu, "clocks": out["clocks"],
+            "roofline": roof, "step_roofline": step, "gemm_roofline": gemm, "cpu_baseline": cpu,
+            "clocks": out["clocks"],
         }
         if sweep:
             line["precision_sweep"] = sweep
@@ -715,6 +878,8 @@ def run_files(args, d: Dist):
 
 def main():
     global WORKLOAD
+    if len(sys.argv) > 1 and sys.argv[1] == "case":
+        sys.exit(run_case(sys.argv[2:]))
     args = parse()
     if args.workload == "files1000":
         if args.impl == "reference":
