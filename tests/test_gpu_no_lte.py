@@ -95,4 +95,4 @@ def test_roundtrip_and_bits_per_byte(prec):
         ref_bits = 8 * sum(len(s) for s in ref["streams"])
         _, n, be = edpc.peek(bits)
         got = 8 * (len(bits) - (88 + 4 * be + 4))
-        assert abs(got - ref_bits) <= 0.02 * ref_bits, (got, ref_bits)
+        assert abs(got - ref_bits) <= 0.005 * ref_bits, (got, ref_bits)

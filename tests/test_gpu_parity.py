@@ -155,9 +155,15 @@ def test_forward_and_gradient_parity(prec, dims, b):
         ref = o_flat[off:off + n]
         if np.linalg.norm(ref) > 1e-12:
             assert _rel(g[off:off + n], ref) <= tol, (name, _rel(g[off:off + n], ref))
+            if prec == edpc.EDPC_FP32:
+                # element by element: |dg| <= 1e-3 max|g_ref| (+ a floor far below FP32 noise of O(1) terms)
+                err = np.abs(g[off:off + n] - ref).max()
+                assert err <= 1e-3 * np.abs(ref).max() + 1e-9, (name, err, np.abs(ref).max())
         off += n
     gu = gu.reshape(b, o.latent, o.latent)
     assert _rel(gu[rows], dUo) <= tol
+    if prec == edpc.EDPC_FP32:
+        assert np.abs(gu[rows] - dUo).max() <= 1e-3 * np.abs(dUo).max() + 1e-9
     assert not gu[active == 0].any()
 
 
@@ -359,9 +365,21 @@ def test_large_config_dims_sampled_against_oracle():
         dz /= b
         go, dUo = om.backward(cache, dz)
         gf = OModel.flat_grads(om.layout, go)
-        assert _rel(g, gf) <= tg_
+        off = 0
+        for name, shape, _ in om.layout:  # tensor by tensor
+            n = int(np.prod(shape))
+            ref = gf[off:off + n]
+            if np.linalg.norm(ref) > 1e-12:
+                assert _rel(g[off:off + n], ref) <= tg_, (prec, name)
+                if prec == edpc.EDPC_FP32:
+                    err = np.abs(g[off:off + n] - ref).max()
+                    assert err <= 1e-3 * np.abs(ref).max() + 1e-9, (name, err)
+            off += n
         sample = rng.choice(b, size=16, replace=False)
         assert _rel(gu.reshape(b, 256, 256)[sample], dUo[sample]) <= tg_
+        if prec == edpc.EDPC_FP32:
+            d = gu.reshape(b, 256, 256)[sample] - dUo[sample]
+            assert np.abs(d).max() <= 1e-3 * np.abs(dUo[sample]).max() + 1e-9
         m.close()
 
 
