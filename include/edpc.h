@@ -318,13 +318,23 @@ int edpc_decompress_many(const uint8_t* bits, size_t bits_len, uint8_t*** outs, 
 /* ------------------------------------------------------------------------ */
 /*
  * A file set in which every file has its own model (the paper codes one
- * input under one model, Algorithm 1 and Sec. 3.3; an archive whose files
- * share one model, as edpc_compress_many makes, can only be decoded whole).
- * File f is compressed exactly as edpc_compress would with cfg->streams =
- * max(1, ceil(n_f / stream_len)), so each member is a single-input container
- * and any file decodes alone. The files' sessions run `concurrency` at a time
- * (0: 8), each on its own CUDA stream, so that the small models' dependent
- * launches overlap on one GPU.
+ * input under one model, Algorithm 1 and Sec. 3.3, over a batch of streams;
+ * an archive whose files share one model, as edpc_compress_many makes, can
+ * only be decoded whole). File f is split as edpc_compress would split it
+ * with cfg->streams = max(1, ceil(n_f / stream_len)), and each member is a
+ * single-input container, so any file decodes alone.
+ *   BF16 with Algorithm 1's schedule: all files' models run as one batch.
+ *     File f's streams take rows padded to a multiple of 64; every kernel of
+ *     the step indexes the parameters of the row's own file (the GEMMs run
+ *     one launch over all files: tile lists with per-file weights, and
+ *     weight gradients contracting each file's rows only), and the CE mean of
+ *     Eq. 2 is over the file's own active streams. Each member is a header
+ *     variant 2 container; edpc_decompress replays it with the same engine
+ *     and one file, and a member's bytes do not depend on the other files of
+ *     the batch. `concurrency` is unused.
+ *   Other precisions or schedules: member f is exactly edpc_compress's
+ *     container for file f; the files' sessions run `concurrency` at a time
+ *     (0: 8), each on its own CUDA stream.
  *
  * Container: "EDPI", u32 format version, u64 file count, u64 stream_len,
  * per file (u64 member offset, u64 member bytes, u64 file bytes), u32 CRC-32
@@ -333,15 +343,19 @@ int edpc_decompress_many(const uint8_t* bits, size_t bits_len, uint8_t*** outs, 
  *   edpc_compress_independent  bufs/lens: host arrays of nfiles pointers and
  *                              sizes (NULL allowed for size 0). out/out_len as
  *                              for edpc_compress. cfg->streams is ignored.
- *                              Errors: EINVAL (bad cfg, NULL, stream_len 0),
- *                              ENOMEM, ECUDA, ETIMEOUT.
+ *                              Errors: EINVAL (bad cfg, NULL, stream_len 0; a
+ *                              batch above 65535 padded rows), ENOMEM, ECUDA,
+ *                              ETIMEOUT.
  *   edpc_independent_info      file count and sizes (sizes may be NULL).
  *                              Errors: ECORRUPT, EVERSION.
  *   edpc_decompress_member     decodes file `index` alone into a
  *                              library-allocated buffer (edpc_free).
  *                              Errors: EINVAL (index), and as edpc_decompress.
- *   edpc_decompress_independent  every file, `concurrency` at a time; outputs
- *                              as for edpc_decompress_many.
+ *   edpc_decompress_independent  every file: members of the batched engine
+ *                              with one configuration in one batch (each
+ *                              member's checksum checked), others
+ *                              `concurrency` at a time; outputs as for
+ *                              edpc_decompress_many.
  */
 int edpc_compress_independent(const uint8_t* const* bufs, const size_t* lens, size_t nfiles, const edpc_cfg* cfg,
                               uint64_t stream_len, uint32_t concurrency, uint8_t** out, size_t* out_len);

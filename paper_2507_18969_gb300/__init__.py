@@ -159,8 +159,10 @@ def selftest_wait_timeout(stream: int = 0) -> None:
 
 
 def compress_independent(files, cfg: Cfg, stream_len: int = 65536, concurrency: int = 8) -> bytes:
-    """Archive of independent per-file models: file f is compressed alone with
-    max(1, ceil(n_f / stream_len)) streams; the sessions run ``concurrency`` at a time."""
+    """Archive of independent per-file models: file f gets its own model over
+    max(1, ceil(n_f / stream_len)) streams. BF16: all files' models run as one
+    batch (members are header variant 2 containers); otherwise one session per
+    file, ``concurrency`` at a time."""
     lib = load()
     keep, ptrs, lens = _files(files)
     out = C.c_void_p()

@@ -174,6 +174,9 @@ constexpr uint32_t kSchedDelayed = 1u;     // header word 11: the delayed-update
 constexpr size_t kFixedHeader = 88;
 
 // Variant 0: one input, balanced split, size-heuristic GEMM tiles.
+// Variant 2: as variant 0, coded by the engine of independent per-file models
+//   in one batch (the file's streams padded to a multiple of 64 rows with its
+//   own model; see GroupInfo): the decoder replays that engine with one group.
 // Variant 1: extended header after the fixed part:
 //   u64 nfiles, u64 L (stream length of the file-set split; 0 = one input
 //   with the balanced split), u32 ntile, u32 0, u64 size[nfiles],
@@ -267,7 +270,7 @@ int read_header(const uint8_t* p, size_t n, Header* h) {
     for (uint64_t f = 0; f < nf; ++f) h->sizes[f] = get<uint64_t>(p, kFixedHeader + 24 + 8 * f);
     h->tiles.assign(p + kFixedHeader + 24 + 8 * nf, p + kFixedHeader + 24 + 8 * nf + nt);
     ext = ext_bytes(*h);
-  } else if (h->variant != 0) {
+  } else if (h->variant != 0 && h->variant != 2) {
     return fail(EDPC_EARCH, "unknown header variant " + std::to_string(h->variant));
   }
   if (hl != kFixedHeader + ext + 4 * (size_t)b + 4) return fail(EDPC_ECORRUPT, "bad header length");
@@ -290,6 +293,8 @@ int read_header(const uint8_t* p, size_t n, Header* h) {
   h->checksum = get<uint64_t>(p, 72);
   int r = check_cfg(&h->cfg, h->variant == 1 && h->L > 0);
   if (r != EDPC_OK) return fail(EDPC_ECORRUPT, "header holds an invalid configuration: " + g_last_error);
+  if (h->variant == 2 && h->cfg.precision != EDPC_BF16)
+    return fail(EDPC_ECORRUPT, "an independent-model member must be BF16");
   h->len.resize(b);
   uint64_t total = 0;
   for (uint32_t s = 0; s < b; ++s) {
@@ -323,6 +328,56 @@ int effective_streams(const edpc_cfg& c, uint64_t n) {
   return (int)std::min<uint64_t>(c.streams, std::max<uint64_t>(1, n / c.context));
 }
 
+// Rows of independent per-file models in one batch: file f (n_f bytes at
+// offset off_f of the files' concatenation) gets its member's balanced split
+// into b_f streams (q or q + 1 bytes, the longer first), then padding rows of
+// no bytes up to a multiple of kGroupAlign rows; group f owns those rows.
+struct GroupPlan {
+  StreamLayout lay;
+  std::vector<GroupInfo> groups;
+  std::vector<uint64_t> n, off;
+  std::vector<uint32_t> b;
+};
+
+int grouped_plan(const uint64_t* sizes, const uint32_t* streams, size_t nfiles, GroupPlan* gp) {
+  gp->lay.off.clear();
+  gp->lay.len.clear();
+  gp->groups.clear();
+  gp->n.assign(sizes, sizes + nfiles);
+  gp->b.assign(streams, streams + nfiles);
+  gp->off.resize(nfiles);
+  uint64_t o = 0;
+  long long rows = 0;
+  for (size_t f = 0; f < nfiles; ++f) {
+    const uint64_t n = sizes[f];
+    const uint32_t b = streams[f];
+    if (b < 1) return fail(EDPC_EINVAL, "a member has no stream");
+    gp->off[f] = o;
+    GroupInfo g;
+    g.r0 = (int)rows;
+    g.s = (int)b;
+    g.q = (long long)(n / b);
+    g.rem = (int)(n % b);
+    for (uint32_t j = 0; j < b; ++j) {
+      gp->lay.off.push_back((long long)o + (long long)j * g.q + std::min<long long>(j, g.rem));
+      gp->lay.len.push_back(g.q + (j < (uint32_t)g.rem ? 1 : 0));
+    }
+    const long long padded = round_up(b, kGroupAlign);
+    for (long long j = b; j < padded; ++j) {
+      gp->lay.off.push_back((long long)(o + n));
+      gp->lay.len.push_back(0);
+    }
+    rows += padded;
+    if (rows > (long long)kMaxStreams)
+      return fail(EDPC_EINVAL, "independent models in one batch: more than 65535 rows (streams plus padding)");
+    g.r1 = (int)rows;
+    gp->groups.push_back(g);
+    o += n;
+  }
+  if (gp->groups.empty()) return fail(EDPC_EINVAL, "no files");
+  return EDPC_OK;
+}
+
 }  // namespace
 
 // ==========================================================================================
@@ -340,6 +395,8 @@ struct edpc_session {
   uint64_t arch_L = 0;                 // file-set stream length (variant 1)
   std::vector<uint64_t> file_sizes;    // file-set sizes (variant 1)
   std::vector<uint8_t> tiles;          // GEMM tile codes recorded in the header
+  GroupPlan gp;                        // independent per-file models in one batch (variant 2 members)
+  bool grouped = false;
   int b = 0;
   uint64_t n = 0;
   cudaStream_t st = nullptr;
@@ -397,7 +454,8 @@ struct edpc_session {
   Model::StepIO io;
 
   ~edpc_session();
-  int setup_common(const edpc_cfg& c, uint64_t n_, void* stream, const StreamLayout* explicit_lay = nullptr);
+  int setup_common(const edpc_cfg& c, uint64_t n_, void* stream, const StreamLayout* explicit_lay = nullptr,
+                   const std::vector<GroupInfo>* groups = nullptr);
   int capture_graph();
   int capture(int nsteps, int set0, cudaGraph_t* g);
   int launch_steps(uint64_t n);
@@ -441,7 +499,8 @@ edpc_session::~edpc_session() {
   if (own_stream && st) cudaStreamDestroy(st);
 }
 
-int edpc_session::setup_common(const edpc_cfg& c, uint64_t n_, void* stream, const StreamLayout* explicit_lay) {
+int edpc_session::setup_common(const edpc_cfg& c, uint64_t n_, void* stream, const StreamLayout* explicit_lay,
+                               const std::vector<GroupInfo>* groups) {
   cfg = c;
   n = n_;
   if (explicit_lay) {
@@ -496,7 +555,7 @@ int edpc_session::setup_common(const edpc_cfg& c, uint64_t n_, void* stream, con
     sp.cp = cp;
     sp.ncp = (int)pts.size();
   }
-  EDPC_TRY(model.init(c, b));
+  EDPC_TRY(model.init(c, b, groups));
   long long L = lay.max_len();
   steps_total = L > (long long)c.context ? (uint64_t)(L - c.context) : 0;
   chunk = 64;
@@ -664,9 +723,11 @@ static int session_prepare_events(edpc_session* s) {
 // device when data_on_device). A single device buffer is used in place.
 // lay: explicit stream layout (file sets), else the balanced split.
 // tune: time the GEMM tiles and record the chosen codes (header variant 1).
+// gp: independent per-file models in one batch (lay is then gp->lay).
 static int encoder_open_impl(const edpc_cfg* cfg, const uint8_t* const* parts, const uint64_t* part_len,
                              size_t nparts, int data_on_device, void* cuda_stream, const StreamLayout* lay,
-                             uint32_t variant, uint64_t arch_L, bool tune, edpc_session** out) {
+                             uint32_t variant, uint64_t arch_L, bool tune, edpc_session** out,
+                             const GroupPlan* gp = nullptr) {
   uint64_t len = 0;
   for (size_t f = 0; f < nparts; ++f) {
     if (!parts[f] && part_len[f]) return fail(EDPC_EINVAL, "data is NULL");
@@ -680,7 +741,12 @@ static int encoder_open_impl(const edpc_cfg* cfg, const uint8_t* const* parts, c
     return r;
   };
   s->encoder = true;
-  int r = s->setup_common(*cfg, len, cuda_stream, lay);
+  if (gp) {
+    s->gp = *gp;
+    s->grouped = true;
+  }
+  int r = gp ? s->setup_common(*cfg, len, cuda_stream, &gp->lay, &gp->groups)
+             : s->setup_common(*cfg, len, cuda_stream, lay);
   if (r != EDPC_OK) return bail(r);
   if ((r = session_prepare_events(s)) != EDPC_OK) return bail(r);
   cudaStream_t st = s->st;
@@ -783,11 +849,10 @@ static int check_device_errors(edpc_session* s) {
   return EDPC_OK;
 }
 
-extern "C" int edpc_encoder_finish(edpc_session* s, uint8_t** out, size_t* out_len) {
-  if (!s || !out || !out_len) return fail(EDPC_EINVAL, "NULL argument");
-  if (!s->encoder) return fail(EDPC_EINVAL, "not an encoder session");
-  *out = nullptr;
-  *out_len = 0;
+// Runs an encoder session to its end and flushes every coder; lens receives
+// the byte count of each row's substream, dst their offsets when packed.
+static int encoder_drain(edpc_session* s, std::vector<uint32_t>* lens, std::vector<unsigned long long>* dst,
+                         uint64_t* total) {
   uint64_t done = 0;
   EDPC_TRY(edpc_session_run(s, UINT64_MAX, 0, &done));
   EDPC_TRY(s->code_pending());
@@ -795,49 +860,102 @@ extern "C" int edpc_encoder_finish(edpc_session* s, uint8_t** out, size_t* out_l
   const int b = s->b;
   cudaStream_t st = s->st;
   EDPC_CUDA(launch_encode_flush(s->es, b, s->out, s->out_off, s->out_cap, s->out_len, st));
-  std::vector<uint32_t> len(b);
-  EDPC_CUDA(cudaMemcpyAsync(len.data(), s->out_len, 4 * (size_t)b, cudaMemcpyDeviceToHost, st));
+  lens->resize(b);
+  EDPC_CUDA(cudaMemcpyAsync(lens->data(), s->out_len, 4 * (size_t)b, cudaMemcpyDeviceToHost, st));
   EDPC_CUDA(cudaStreamSynchronize(st));
   EDPC_TRY(check_device_errors(s));
-  uint64_t total = 0;
-  std::vector<unsigned long long> dst(b);
+  *total = 0;
+  dst->resize(b);
   for (int i = 0; i < b; ++i) {
-    if (len[i] == 0xFFFFFFFFu) return fail(EDPC_ECUDA, "coder output buffer overflow");
-    dst[i] = total;
-    total += len[i];
+    if ((*lens)[i] == 0xFFFFFFFFu) return fail(EDPC_ECUDA, "coder output buffer overflow");
+    (*dst)[i] = *total;
+    *total += (*lens)[i];
   }
+  return EDPC_OK;
+}
+
+// Packs every row's substream (in row order) into host memory.
+static int gather_payload(edpc_session* s, const std::vector<unsigned long long>& dst, uint64_t total, uint8_t* host) {
+  if (!total) return EDPC_OK;
+  const int b = s->b;
+  cudaStream_t st = s->st;
+  uint8_t* packed = nullptr;
+  unsigned long long* dst_dev = nullptr;
+  if (cudaMalloc(&packed, total) != cudaSuccess || cudaMalloc(&dst_dev, 8 * (size_t)b) != cudaSuccess) {
+    cudaFree(packed);
+    return fail(EDPC_ENOMEM, "packing buffer");
+  }
+  cudaMemcpyAsync(dst_dev, dst.data(), 8 * (size_t)b, cudaMemcpyHostToDevice, st);
+  gather_streams_kernel<<<b, 256, 0, st>>>(s->out, s->out_off, s->out_len, dst_dev, packed);
+  cudaError_t e = cudaMemcpyAsync(host, packed, total, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(packed);
+  cudaFree(dst_dev);
+  if (e != cudaSuccess) return fail(EDPC_ECUDA, std::string("stream gather: ") + cudaGetErrorString(e));
+  return EDPC_OK;
+}
+
+// Independent per-file models in one batch: one variant-2 container per file
+// (the file's own streams, cfg.streams = its stream count, its bytes' checksum).
+static int grouped_encoder_finish(edpc_session* s, std::vector<std::vector<uint8_t>>* members) {
+  std::vector<uint32_t> len;
+  std::vector<unsigned long long> dst;
+  uint64_t total = 0;
+  EDPC_TRY(encoder_drain(s, &len, &dst, &total));
+  std::vector<uint8_t> payload(std::max<uint64_t>(total, 1));
+  EDPC_TRY(gather_payload(s, dst, total, payload.data()));
+  const GroupPlan& gp = s->gp;
+  members->assign(gp.groups.size(), {});
+  for (size_t f = 0; f < gp.groups.size(); ++f) {
+    const GroupInfo& g = gp.groups[f];
+    Header h;
+    h.cfg = s->cfg;
+    h.cfg.streams = gp.b[f];
+    h.n = gp.n[f];
+    h.b = gp.b[f];
+    h.len.assign(len.begin() + g.r0, len.begin() + g.r0 + g.s);
+    h.variant = 2;
+    EDPC_TRY(device_checksum(s->data + gp.off[f], gp.n[f], s->scratch, s->st, &h.checksum));
+    std::vector<uint8_t> hdr = write_header(h);
+    uint64_t bytes = 0;
+    for (uint32_t v : h.len) bytes += v;
+    std::vector<uint8_t>& m = (*members)[f];
+    m.resize(hdr.size() + bytes);
+    memcpy(m.data(), hdr.data(), hdr.size());
+    if (bytes) memcpy(m.data() + hdr.size(), payload.data() + dst[g.r0], bytes);
+  }
+  s->finished = true;
+  return EDPC_OK;
+}
+
+extern "C" int edpc_encoder_finish(edpc_session* s, uint8_t** out, size_t* out_len) {
+  if (!s || !out || !out_len) return fail(EDPC_EINVAL, "NULL argument");
+  if (!s->encoder) return fail(EDPC_EINVAL, "not an encoder session");
+  if (s->grouped) return fail(EDPC_EINVAL, "a batch of independent models finishes into an archive");
+  *out = nullptr;
+  *out_len = 0;
+  std::vector<uint32_t> len;
+  std::vector<unsigned long long> dst;
+  uint64_t total = 0;
+  EDPC_TRY(encoder_drain(s, &len, &dst, &total));
   Header h;
   h.cfg = s->cfg;
   h.n = s->n;
-  h.b = (uint32_t)b;
+  h.b = (uint32_t)s->b;
   h.len = len;
   h.variant = s->variant;
   h.L = s->arch_L;
   h.sizes = s->file_sizes;
   h.tiles = s->tiles;
-  EDPC_TRY(device_checksum(s->data, s->n, s->scratch, st, &h.checksum));
+  EDPC_TRY(device_checksum(s->data, s->n, s->scratch, s->st, &h.checksum));
   std::vector<uint8_t> hdr = write_header(h);
   uint8_t* buf = static_cast<uint8_t*>(malloc(hdr.size() + total + 1));
   if (!buf) return fail(EDPC_ENOMEM, "output buffer");
   memcpy(buf, hdr.data(), hdr.size());
-  if (total) {
-    uint8_t* packed = nullptr;
-    unsigned long long* dst_dev = nullptr;
-    if (cudaMalloc(&packed, total) != cudaSuccess || cudaMalloc(&dst_dev, 8 * (size_t)b) != cudaSuccess) {
-      cudaFree(packed);
-      free(buf);
-      return fail(EDPC_ENOMEM, "packing buffer");
-    }
-    cudaMemcpyAsync(dst_dev, dst.data(), 8 * (size_t)b, cudaMemcpyHostToDevice, st);
-    gather_streams_kernel<<<b, 256, 0, st>>>(s->out, s->out_off, s->out_len, dst_dev, packed);
-    cudaError_t e = cudaMemcpyAsync(buf + hdr.size(), packed, total, cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(packed);
-    cudaFree(dst_dev);
-    if (e != cudaSuccess) {
-      free(buf);
-      return fail(EDPC_ECUDA, std::string("stream gather: ") + cudaGetErrorString(e));
-    }
+  int r = gather_payload(s, dst, total, buf + hdr.size());
+  if (r != EDPC_OK) {
+    free(buf);
+    return r;
   }
   s->finished = true;
   *out = buf;
@@ -855,12 +973,13 @@ extern "C" int edpc_peek(const uint8_t* bits, size_t bits_len, edpc_cfg* cfg, ui
   return EDPC_OK;
 }
 
-extern "C" int edpc_decoder_open(const uint8_t* bits, size_t bits_len, void* out_device, void* cuda_stream,
-                                 edpc_session** out) {
-  if (!out) return fail(EDPC_EINVAL, "out is NULL");
-  *out = nullptr;
-  Header h;
-  EDPC_TRY(read_header(bits, bits_len, &h));
+// Opens a decoder over `payload` (every row's substream, in row order; row r
+// has row_len[r] bytes). lay: explicit layout (file sets), gp: independent
+// models in one batch (rows and layout from gp), neither: the balanced split.
+static int decoder_open_impl(const edpc_cfg& cfg, uint64_t n, const StreamLayout* lay, const GroupPlan* gp,
+                             const uint8_t* payload, size_t payload_len, const std::vector<uint32_t>& row_len,
+                             uint64_t checksum, const std::vector<uint8_t>& tiles, void* out_device,
+                             void* cuda_stream, edpc_session** out) {
   EDPC_TRY(current_device_ok());
   edpc_session* s = new (std::nothrow) edpc_session();
   if (!s) return fail(EDPC_ENOMEM, "host allocation failed");
@@ -869,44 +988,46 @@ extern "C" int edpc_decoder_open(const uint8_t* bits, size_t bits_len, void* out
     return r;
   };
   s->encoder = false;
-  StreamLayout lay;
-  const bool file_set = h.variant == 1 && h.L > 0;
-  if (file_set) archive_split(h.sizes.data(), h.sizes.size(), h.L, &lay);
-  int r = s->setup_common(h.cfg, h.n, cuda_stream, file_set ? &lay : nullptr);
+  if (gp) {
+    s->gp = *gp;
+    s->grouped = true;
+  }
+  int r = gp ? s->setup_common(cfg, n, cuda_stream, &gp->lay, &gp->groups) : s->setup_common(cfg, n, cuda_stream, lay);
   if (r != EDPC_OK) return bail(r);
   if ((r = session_prepare_events(s)) != EDPC_OK) return bail(r);
   cudaStream_t st = s->st;
   const int b = s->b;
-  s->checksum_expected = h.checksum;
+  if ((int)row_len.size() != b) return bail(fail(EDPC_ECORRUPT, "stream table does not match the layout"));
+  s->checksum_expected = checksum;
   // the encoder's GEMM tiles (they fix the accumulation layout of the replay)
-  if (!h.tiles.empty() && (r = s->model.set_tiles(h.tiles.data(), (int)h.tiles.size())) != EDPC_OK) return bail(r);
+  if (!tiles.empty() && (r = s->model.set_tiles(tiles.data(), (int)tiles.size())) != EDPC_OK) return bail(r);
   if (out_device) {
     s->data = static_cast<uint8_t*>(out_device);
   } else {
-    if (cudaMalloc(&s->data, std::max<uint64_t>(h.n, 1)) != cudaSuccess) return bail(fail(EDPC_ENOMEM, "output"));
+    if (cudaMalloc(&s->data, std::max<uint64_t>(n, 1)) != cudaSuccess) return bail(fail(EDPC_ENOMEM, "output"));
     s->own_data = true;
   }
-  const size_t payload = bits_len - h.header_len;
   std::vector<unsigned long long> off(b);
   unsigned long long o = 0;
   for (int i = 0; i < b; ++i) {
     off[i] = o;
-    o += h.len[i];
+    o += row_len[i];
   }
-  if (cudaMalloc(&s->bits, std::max<size_t>(payload, 1)) != cudaSuccess ||
+  if (o != payload_len) return bail(fail(EDPC_ECORRUPT, "stream lengths do not match the payload"));
+  if (cudaMalloc(&s->bits, std::max<size_t>(payload_len, 1)) != cudaSuccess ||
       cudaMalloc(&s->bits_off, 8 * (size_t)b) != cudaSuccess || cudaMalloc(&s->bits_len, 4 * (size_t)b) != cudaSuccess ||
       cudaMalloc(&s->ds, sizeof(DecState) * b) != cudaSuccess)
     return bail(fail(EDPC_ENOMEM, "decoder buffers"));
-  if ((payload && cudaMemcpyAsync(s->bits, bits + h.header_len, payload, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
+  if ((payload_len && cudaMemcpyAsync(s->bits, payload, payload_len, cudaMemcpyHostToDevice, st) != cudaSuccess) ||
       cudaMemcpyAsync(s->bits_off, off.data(), 8 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(s->bits_len, h.len.data(), 4 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      cudaMemcpyAsync(s->bits_len, row_len.data(), 4 * (size_t)b, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return bail(fail(EDPC_ECUDA, "decoder input copies"));
   if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(EDPC_ECUDA, "decoder input sync"));
   if (launch_dec_init(s->ds, s->bits, s->bits_off, s->bits_len, b, st) != cudaSuccess ||
-      launch_prefix_decode(s->ds, s->bits, s->bits_off, s->bits_len, s->sp, (int)h.cfg.context, b, s->data, st) !=
+      launch_prefix_decode(s->ds, s->bits, s->bits_off, s->bits_len, s->sp, (int)cfg.context, b, s->data, st) !=
           cudaSuccess)
     return bail(fail(EDPC_ECUDA, "decoder prefix launch"));
-  long long i0 = h.cfg.context;
+  long long i0 = cfg.context;
   if ((r = s->model.set_ctl_for_step((int)i0, 1, s->lay.active_at(i0), s->ring_slots, st)) != EDPC_OK) return bail(r);
   s->io.mode = 1;
   s->io.data = s->data;
@@ -920,6 +1041,61 @@ extern "C" int edpc_decoder_open(const uint8_t* bits, size_t bits_len, void* out
   if (cudaStreamSynchronize(st) != cudaSuccess) return bail(fail(EDPC_ECUDA, "decoder open sync"));
   *out = s;
   return EDPC_OK;
+}
+
+// Rows of a batch of variant-2 members (each member's streams, then padding
+// rows of no bytes) and their concatenated payload.
+static int grouped_members_plan(const std::vector<Header>& hs, const std::vector<const uint8_t*>& payloads,
+                                GroupPlan* gp, std::vector<uint8_t>* payload, std::vector<uint32_t>* row_len,
+                                uint64_t* total_n) {
+  std::vector<uint64_t> n(hs.size());
+  std::vector<uint32_t> b(hs.size());
+  *total_n = 0;
+  size_t bytes = 0;
+  for (size_t f = 0; f < hs.size(); ++f) {
+    n[f] = hs[f].n;
+    b[f] = hs[f].b;
+    *total_n += hs[f].n;
+    for (uint32_t v : hs[f].len) bytes += v;
+  }
+  EDPC_TRY(grouped_plan(n.data(), b.data(), hs.size(), gp));
+  payload->resize(bytes);
+  row_len->assign(gp->lay.streams(), 0);
+  size_t o = 0;
+  for (size_t f = 0; f < hs.size(); ++f) {
+    size_t mb = 0;
+    for (uint32_t s = 0; s < hs[f].b; ++s) {
+      (*row_len)[gp->groups[f].r0 + s] = hs[f].len[s];
+      mb += hs[f].len[s];
+    }
+    if (mb) memcpy(payload->data() + o, payloads[f], mb);
+    o += mb;
+  }
+  return EDPC_OK;
+}
+
+extern "C" int edpc_decoder_open(const uint8_t* bits, size_t bits_len, void* out_device, void* cuda_stream,
+                                 edpc_session** out) {
+  if (!out) return fail(EDPC_EINVAL, "out is NULL");
+  *out = nullptr;
+  Header h;
+  EDPC_TRY(read_header(bits, bits_len, &h));
+  if (h.variant == 2) {
+    // one file of an archive of independent models: its own model, replayed
+    // by the batched engine with one group
+    GroupPlan gp;
+    std::vector<uint8_t> payload;
+    std::vector<uint32_t> row_len;
+    uint64_t n = 0;
+    EDPC_TRY(grouped_members_plan({h}, {bits + h.header_len}, &gp, &payload, &row_len, &n));
+    return decoder_open_impl(h.cfg, h.n, nullptr, &gp, payload.data(), payload.size(), row_len, h.checksum, {},
+                             out_device, cuda_stream, out);
+  }
+  StreamLayout lay;
+  const bool file_set = h.variant == 1 && h.L > 0;
+  if (file_set) archive_split(h.sizes.data(), h.sizes.size(), h.L, &lay);
+  return decoder_open_impl(h.cfg, h.n, file_set ? &lay : nullptr, nullptr, bits + h.header_len,
+                           bits_len - h.header_len, h.len, h.checksum, h.tiles, out_device, cuda_stream, out);
 }
 
 extern "C" int edpc_decoder_finish(edpc_session* s, uint8_t* out_host) {
@@ -1165,6 +1341,13 @@ uint32_t indep_streams(uint64_t n, uint64_t L) {
   return (uint32_t)std::min<uint64_t>(std::max<uint64_t>(b, 1), kMaxStreams);
 }
 
+// Independent models run as one batch (the grouped engine) in BF16 with
+// Algorithm 1's schedule; other precisions and schedules run one session per
+// file, several at a time.
+bool batched_independent(const edpc_cfg& c) {
+  return c.precision == EDPC_BF16 && !(c.flags & (EDPC_FLAG_DELAYED_UPDATE | EDPC_FLAG_OVERLAP_FDM));
+}
+
 // Runs the sessions of `count` jobs, at most `conc` at a time, each on its
 // own CUDA stream: open(j, stream, &s) opens job j's session, done(j, s)
 // finishes it. Every round queues kIndepChunk model steps on each open
@@ -1230,20 +1413,38 @@ extern "C" int edpc_compress_independent(const uint8_t* const* bufs, const size_
     if (!bufs[f] && lens[f]) return fail(EDPC_EINVAL, "data is NULL");
   EDPC_TRY(current_device_ok());
   std::vector<std::vector<uint8_t>> members(nfiles);
-  auto open = [&](size_t f, cudaStream_t st, edpc_session** s) {
-    edpc_cfg c = *cfg;
-    c.streams = indep_streams(lens[f], stream_len);
-    return edpc_encoder_open(&c, bufs[f], lens[f], 0, st, s);
-  };
-  auto done = [&](size_t f, edpc_session* s) {
-    uint8_t* b = nullptr;
-    size_t n = 0;
-    EDPC_TRY(edpc_encoder_finish(s, &b, &n));
-    members[f].assign(b, b + n);
-    free(b);
-    return EDPC_OK;
-  };
-  EDPC_TRY(run_concurrent(nfiles, concurrency, open, done));
+  if (batched_independent(*cfg) && nfiles) {
+    // BF16: every file's model in one batch (grouped engine), one session
+    std::vector<uint64_t> sz(lens, lens + nfiles);
+    std::vector<uint32_t> bs(nfiles);
+    for (size_t f = 0; f < nfiles; ++f) {
+      edpc_cfg c = *cfg;
+      c.streams = indep_streams(lens[f], stream_len);
+      bs[f] = (uint32_t)effective_streams(c, lens[f]);
+    }
+    GroupPlan gp;
+    EDPC_TRY(grouped_plan(sz.data(), bs.data(), nfiles, &gp));
+    edpc_session* s = nullptr;
+    EDPC_TRY(encoder_open_impl(&c0, bufs, sz.data(), nfiles, 0, nullptr, nullptr, 2, 0, false, &s, &gp));
+    int r = grouped_encoder_finish(s, &members);
+    edpc_session_close(s);
+    EDPC_TRY(r);
+  } else {
+    auto open = [&](size_t f, cudaStream_t st, edpc_session** s) {
+      edpc_cfg c = *cfg;
+      c.streams = indep_streams(lens[f], stream_len);
+      return edpc_encoder_open(&c, bufs[f], lens[f], 0, st, s);
+    };
+    auto done = [&](size_t f, edpc_session* s) {
+      uint8_t* b = nullptr;
+      size_t n = 0;
+      EDPC_TRY(edpc_encoder_finish(s, &b, &n));
+      members[f].assign(b, b + n);
+      free(b);
+      return EDPC_OK;
+    };
+    EDPC_TRY(run_concurrent(nfiles, concurrency, open, done));
+  }
   const size_t hl = indep_header_len(nfiles);
   size_t total = hl;
   for (auto& m : members) total += m.size();
@@ -1294,6 +1495,36 @@ extern "C" int edpc_decompress_member(const uint8_t* bits, size_t bits_len, uint
   return edpc_decompress(bits + t.off[index], t.bytes[index], out, out_len);
 }
 
+// Decodes every variant-2 member of an archive in one batched session and
+// checks each member's data checksum.
+static int grouped_decode_all(const std::vector<Header>& hs, const uint8_t* bits, const IndepTable& t,
+                              uint8_t** outs) {
+  std::vector<const uint8_t*> pl(hs.size());
+  for (size_t f = 0; f < hs.size(); ++f) pl[f] = bits + t.off[f] + hs[f].header_len;
+  GroupPlan gp;
+  std::vector<uint8_t> payload;
+  std::vector<uint32_t> row_len;
+  uint64_t n = 0;
+  EDPC_TRY(grouped_members_plan(hs, pl, &gp, &payload, &row_len, &n));
+  edpc_session* s = nullptr;
+  EDPC_TRY(decoder_open_impl(hs[0].cfg, n, nullptr, &gp, payload.data(), payload.size(), row_len, 0, {}, nullptr,
+                             nullptr, &s));
+  uint64_t done = 0;
+  int r = edpc_session_run(s, UINT64_MAX, 1, &done);
+  if (r == EDPC_OK) r = check_device_errors(s);
+  for (size_t f = 0; f < hs.size() && r == EDPC_OK; ++f) {
+    uint64_t h = 0;
+    r = device_checksum(s->data + gp.off[f], gp.n[f], s->scratch, s->st, &h);
+    if (r == EDPC_OK && h != hs[f].checksum) r = fail(EDPC_ECORRUPT, "checksum of a decoded member does not match");
+    if (r == EDPC_OK && gp.n[f] && cudaMemcpy(outs[f], s->data + gp.off[f], gp.n[f], cudaMemcpyDeviceToHost) !=
+                                       cudaSuccess)
+      r = fail(EDPC_ECUDA, "member copy");
+  }
+  if (r == EDPC_OK) s->finished = true;
+  edpc_session_close(s);
+  return r;
+}
+
 extern "C" int edpc_decompress_independent(const uint8_t* bits, size_t bits_len, uint32_t concurrency,
                                            uint8_t*** outs, size_t** lens, size_t* nfiles) {
   if (!outs || !lens || !nfiles) return fail(EDPC_EINVAL, "NULL output pointer");
@@ -1325,13 +1556,26 @@ extern "C" int edpc_decompress_independent(const uint8_t* bits, size_t bits_len,
     o += t.size[f];
   }
   int r = EDPC_OK;
-  if (t.nfiles) {
-    EDPC_TRY(current_device_ok());
+  // members of the batched engine with one configuration decode as one batch
+  std::vector<Header> hs(t.nfiles);
+  bool batch = t.nfiles > 0;
+  for (uint64_t f = 0; f < t.nfiles && r == EDPC_OK; ++f) {
+    r = read_header(bits + t.off[f], t.bytes[f], &hs[f]);
+    const edpc_cfg& a = hs[f].cfg;
+    const edpc_cfg& z = hs[0].cfg;
+    batch = batch && hs[f].variant == 2 && a.context == z.context && a.embed_dim == z.embed_dim &&
+            a.latent == z.latent && a.hidden == z.hidden && a.blocks == z.blocks && a.branches == z.branches &&
+            a.lr == z.lr && a.seed == z.seed && a.precision == z.precision && a.flags == z.flags;
+  }
+  if (r == EDPC_OK && batch) {
+    r = grouped_decode_all(hs, bits, t, ptrs);
+  } else if (r == EDPC_OK && t.nfiles) {
+    r = current_device_ok();
     auto open = [&](size_t f, cudaStream_t st, edpc_session** s) {
       return edpc_decoder_open(bits + t.off[f], t.bytes[f], nullptr, st, s);
     };
     auto done = [&](size_t f, edpc_session* s) { return edpc_decoder_finish(s, ptrs[f]); };
-    r = run_concurrent((size_t)t.nfiles, concurrency, open, done);
+    if (r == EDPC_OK) r = run_concurrent((size_t)t.nfiles, concurrency, open, done);
   }
   if (r != EDPC_OK) {
     free(block);

@@ -59,7 +59,8 @@ struct StepCtl {
   float lr;
   int err;        // sticky error bits
   int cpi;        // next entry of the active-count table (uneven splits)
-  int pad[6];
+  unsigned arrive;  // CTAs of the Adam launch that also advances the step, done so far (0 between steps)
+  int pad[5];
 };
 
 // Change point of the active-stream count: from time index i on, bact
@@ -90,6 +91,22 @@ struct Split {
     return seg ? (long long)(seg[s + 1] - seg[s]) : q + (s < rem ? 1 : 0);
   }
 };
+
+// Independent per-file models in one batch ("grouped" mode): group g owns
+// rows [r0, r1) (r0, r1 multiples of 64): its file's s streams, the first rem
+// of q + 1 bytes and the others of q bytes (the balanced split of the file),
+// then r1 - r0 - s padding rows that never hold a byte. Each group has its own
+// parameters, `gstride` floats after the previous group's.
+struct GroupInfo {
+  int r0, r1, s, rem;
+  long long q;
+};
+// Streams of a group active at time index i (K <= i): the mean of Eq. 2 over
+// the group's own active streams.
+__host__ __device__ inline int group_active(const GroupInfo& g, long long i) {
+  return i < g.q ? g.s : (i < g.q + 1 ? g.rem : 0);
+}
+constexpr int kGroupAlign = 64;  // rows per group are padded to a multiple of this
 
 // Range coder states (one per stream), kept in device memory between launches.
 struct EncState {

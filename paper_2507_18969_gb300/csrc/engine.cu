@@ -146,13 +146,33 @@ Model::~Model() {
   if (arena_) cudaFree(arena_);
 }
 
-int Model::init(const edpc_cfg& cfg, int streams) {
+int Model::init(const edpc_cfg& cfg, int streams, const std::vector<GroupInfo>* groups) {
   d = make_dims(cfg, streams);
   po = make_offsets(d);
   precision = cfg.precision;
   seed = cfg.seed;
   lr = cfg.lr;
   nparam = po.total;
+  np_all = nparam;
+  if (groups) {
+    // grouped mode: BF16, Algorithm 1's schedule, groups tiling the rows in
+    // order with boundaries on multiples of kGroupAlign
+    if (precision != EDPC_BF16 || (cfg.flags & (EDPC_FLAG_DELAYED_UPDATE | EDPC_FLAG_OVERLAP_FDM)))
+      return fail(EDPC_EINVAL, "independent per-file models in one batch need BF16 and Algorithm 1's schedule");
+    if (groups->empty() || groups->size() > 65535) return fail(EDPC_EINVAL, "group count out of range");
+    int r = 0;
+    for (const GroupInfo& g : *groups) {
+      if (g.r0 != r || g.r1 <= g.r0 || g.r0 % kGroupAlign || g.r1 % kGroupAlign || g.s < 1 || g.s > g.r1 - g.r0 ||
+          g.rem < 0 || g.rem >= g.s || g.q < 0 || (long long)(g.r1 - g.r0) * d.K > (1ll << 30))
+        return fail(EDPC_EINVAL, "malformed group table");
+      r = g.r1;
+    }
+    if (r != streams) return fail(EDPC_EINVAL, "groups do not cover the rows");
+    groups_h = *groups;
+    ngroups = (int)groups->size();
+    gstride = (size_t)round_up((long long)nparam, 64);
+    np_all = gstride * (size_t)ngroups;
+  }
   const size_t bF = (size_t)d.b * d.F, bFp = (size_t)d.b * d.Fp, bH = (size_t)d.b * d.H;
   const int kH = d.k * d.H;
   const size_t bkH = (size_t)d.b * kH, fdm = (size_t)d.b * d.Fp * d.Fp;
@@ -176,8 +196,26 @@ int Model::init(const edpc_cfg& cfg, int streams) {
       mat(po.W2, d.F, d.Fp);
     }
     mat(po.Wh, 256, d.F);
+    if (ngroups > 1) {  // every group's matrices
+      const size_t n1 = th.size();
+      for (int g = 1; g < ngroups; ++g)
+        for (size_t t = 0; t < n1; ++t) {
+          TransposeTile x = th[t];
+          x.off += (unsigned long long)g * gstride;
+          th.push_back(x);
+        }
+    }
   }
   ntiles = (int)th.size();
+  // grouped mode: tile list of the forward / dX GEMMs and K ranges of the weight gradients
+  std::vector<int4> mt_h, gk_h;
+  for (int g = 0; g < ngroups; ++g) {
+    const GroupInfo& gi = groups_h[g];
+    for (int m0 = gi.r0; m0 < gi.r1; m0 += 128) mt_h.push_back(make_int4(m0, std::min(m0 + 128, gi.r1), g, 0));
+    gk_h.push_back(make_int4(gi.r0, (gi.r1 - gi.r0) / 64, 0, 0));
+  }
+  ngtiles = (int)mt_h.size();
+  if (ngtiles > 65535) return fail(EDPC_EINVAL, "too many row tiles for independent models in one batch");
 
   delayed = (cfg.flags & EDPC_FLAG_DELAYED_UPDATE) != 0;
   const int npar = delayed ? 2 : 1;
@@ -188,7 +226,7 @@ int Model::init(const edpc_cfg& cfg, int streams) {
   // what the forward pass and the head write, the parameters, the FDMs and the
   // step control: one copy, or one per parity for the delayed update
   auto take_parity = [&](Arena& a) {
-    P = a.take<float>(nparam);
+    P = a.take<float>(np_all);
     U = a.take<float>(fdm);
     ctl = a.take<StepCtl>(1);
     ctx = a.take<uint8_t>((size_t)d.b * d.K);
@@ -213,8 +251,8 @@ int Model::init(const edpc_cfg& cfg, int streams) {
       pend = a.take<FdmPend>(1);
     }
     if (bf16) {
-      Pb = a.take<__nv_bfloat16>(nparam);
-      PbT = a.take<__nv_bfloat16>(nparam);
+      Pb = a.take<__nv_bfloat16>(np_all);
+      PbT = a.take<__nv_bfloat16>(np_all);
       for (int j = 0; j < d.n; ++j) {
         bb[j].X0b = a.take<__nv_bfloat16>(bF);
         bb[j].X0bT = a.take<__nv_bfloat16>((size_t)d.F * T);
@@ -239,9 +277,15 @@ int Model::init(const edpc_cfg& cfg, int streams) {
       take_parity(a);
       save_parity(q);
     }
-    G = a.take<float>(nparam);
-    M = a.take<float>(nparam);
-    V = a.take<float>(nparam);
+    G = a.take<float>(np_all);
+    M = a.take<float>(np_all);
+    V = a.take<float>(np_all);
+    if (ngroups) {
+      row_grp = a.take<int>(d.b);
+      ginfo = a.take<GroupInfo>(ngroups);
+      gtiles = a.take<int4>(ngtiles);
+      gkr = a.take<int4>(ngroups);
+    }
     Um = a.take<float>(fdm);
     Uv = a.take<float>(fdm);
     dY = a.take<float>(bFp);
@@ -361,6 +405,19 @@ int Model::init(const edpc_cfg& cfg, int streams) {
   ts.push_back({po.bh, (size_t)256, (float)(1.0 / std::sqrt(F)), 0.f});
   for (size_t tid = 0; tid < ts.size(); ++tid)
     EDPC_CUDA(launch_init_values(P + ts[tid].off, ts[tid].n, seed, (int)tid, ts[tid].bound, 0, ts[tid].fill, st));
+  if (ngroups) {
+    // every group starts from the same initial values (those of a single-file model)
+    for (int g = 1; g < ngroups; ++g)
+      EDPC_CUDA(cudaMemcpyAsync(P + (size_t)g * gstride, P, nparam * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    std::vector<int> rg(d.b);
+    for (int g = 0; g < ngroups; ++g)
+      for (int r = groups_h[g].r0; r < groups_h[g].r1; ++r) rg[r] = g;
+    EDPC_CUDA(cudaMemcpyAsync(row_grp, rg.data(), sizeof(int) * d.b, cudaMemcpyHostToDevice, st));
+    EDPC_CUDA(cudaMemcpyAsync(ginfo, groups_h.data(), sizeof(GroupInfo) * ngroups, cudaMemcpyHostToDevice, st));
+    EDPC_CUDA(cudaMemcpyAsync(gtiles, mt_h.data(), sizeof(int4) * ngtiles, cudaMemcpyHostToDevice, st));
+    EDPC_CUDA(cudaMemcpyAsync(gkr, gk_h.data(), sizeof(int4) * ngroups, cudaMemcpyHostToDevice, st));
+    EDPC_CUDA(cudaStreamSynchronize(st));  // the host tables above are locals
+  }
   EDPC_CUDA(launch_init_values(U, fdm, seed, kFdmTid, (float)std::sqrt(3.0 / Fp), 0, 0.f, st));
   // Stream priorities (the default is the least): with the delayed update the
   // adjoint's streams go first and the FDM update last.
@@ -483,7 +540,8 @@ int Model::set_ctl_for_step(int i, int t, int bact, int ring_slots, cudaStream_t
 }
 
 int Model::refresh_bf16_weights(cudaStream_t st) {
-  EDPC_CUDA(launch_to_bf16(P, 1, (int)nparam, (int)nparam, Pb, (int)nparam, nullptr, 0, st));
+  if (np_all > (size_t)INT32_MAX) return fail(EDPC_EINVAL, "parameter count exceeds 2^31 - 1");
+  EDPC_CUDA(launch_to_bf16(P, 1, (int)np_all, (int)np_all, Pb, (int)np_all, nullptr, 0, st));
   EDPC_CUDA(launch_transpose_tiles(Pb, PbT, tiles, ntiles, st));
   return EDPC_OK;
 }
@@ -789,7 +847,7 @@ int Model::build_tc_sites() {
   // dW GEMMs (K = streams): split K when the output has too few tiles for the GPU
   auto split_site = [&](int id) -> int {
     TcGemm& g = tcp.site[id];
-    g.splitk = tc_splitk(g.M, g.N, g.K, g.bn);
+    g.splitk = ngroups ? 1 : tc_splitk(g.M, g.N, g.K, g.bn);  // grouped: each group's own K range
     if (g.splitk > 1) {
       if (!sk_ws || (size_t)g.splitk * g.M * g.N > sk_ws_floats || tc_tiles(g.M, g.N, g.bn) > kSplitCounters)
         return fail(EDPC_EINVAL, "split-K GEMM exceeds its scratch");
@@ -827,6 +885,24 @@ int Model::build_tc_sites() {
     }
     EDPC_TRY(make_tmap_bf16(&g.ta, a, a_rows, a_cols, a_ld, 128));
     EDPC_TRY(make_tmap_bf16(&g.tb, b, b_rows, b_cols, b_ld, box_b));
+    g.mt = nullptr;
+    g.gk = nullptr;
+    if (ngroups) {
+      // grouped mode: a weight operand is one matrix per group (3-D map, tile
+      // list over the groups' rows); otherwise B holds activations and the
+      // GEMM is a weight gradient contracting each group's own rows
+      const auto* pb = static_cast<const __nv_bfloat16*>(b);
+      const bool weight = (pb >= Pb && pb < Pb + np_all) || (pb >= PbT && pb < PbT + np_all);
+      g.gs = gstride;
+      if (weight) {
+        EDPC_TRY(make_tmap_bf16_groups(&g.tb, b, b_rows, b_cols, b_ld, ngroups, gstride, box_b));
+        g.mt = gtiles;
+        g.nmt = ngtiles;
+      } else {
+        g.gk = gkr;
+        g.ngk = ngroups;
+      }
+    }
     return EDPC_OK;
   };
   const int b = d.b, F = d.F, H = d.H, Fp = d.Fp;
@@ -1036,6 +1112,7 @@ bool Model::tile_code_ok(int, uint8_t c) const {
 
 int Model::set_tiles(const uint8_t* code, int n) {
   if (precision == EDPC_FP32) return EDPC_OK;
+  if (ngroups) return fail(EDPC_EINVAL, "independent models in one batch use the size-heuristic tiles");
   // validate every code before any is taken, so a refused set leaves the plan as it was
   for (int i = 0; i < TcPlan::kMaxSites; ++i) {
     const uint8_t c = (code && i < n) ? code[i] : 0;
@@ -1051,7 +1128,7 @@ int Model::set_tiles(const uint8_t* code, int n) {
 // model's own buffers, and keeps the fastest. Runs before the first step: the
 // GEMMs only overwrite per-step outputs (activations, BF16 copies, gradients).
 int Model::tune_tiles(cudaStream_t st) {
-  if (precision == EDPC_FP32) return EDPC_OK;
+  if (precision == EDPC_FP32 || ngroups) return EDPC_OK;
   std::vector<int> ids;
   tunable_sites(&ids);
   cudaEvent_t e0, e1;
@@ -1160,6 +1237,10 @@ int Model::run_tc(int site, cudaStream_t st) {
 
 int Model::colsums(ColsumJobs cj, cudaStream_t st) {
   NoPdl scope;
+  if (ngroups) {  // each group's own rows into its own gradient
+    EDPC_CUDA(launch_colsum_groups(cj, ginfo, ngroups, gstride, st));
+    return EDPC_OK;
+  }
   cj.chunk_rows = colsum_chunk_rows(d.b, colsum_tiles(cj));
   if (cj.chunk_rows > 0) {
     const int tw = colsum_vec(cj) ? 128 : 32;
@@ -1197,7 +1278,17 @@ int Model::forward_bf16(const StepIO& io, cudaStream_t st) {
   }
   EDPC_CUDA(cudaEventRecord(tr_ev, side));
   if (f8m) EDPC_TRY(quantize_weights(false, st));
-  EDPC_CUDA(launch_embed(io.mode == 2 ? nullptr : io.data, io.sp, ctl, P + po.E, d.b, d.K, d.D, S[0], ctx, st));
+  // the embedding, fused with the first block's LayerNorm when a Local block follows it
+  const bool fuse0 = d.nloc > 0 && (d.F == 128 || d.F == 256 || d.F == 512 || d.F == 1024);
+  if (fuse0) {
+    const BlockOff& o = po.blk[0];
+    EDPC_CUDA(launch_embed_ln_bf16(io.mode == 2 ? nullptr : io.data, io.sp, ctl, P + po.E, d.b, d.K, d.D, S[0], ctx,
+                                   P + o.ln_g, P + o.ln_b, ba[0].xhat, ba[0].rstd, bb[0].X0b, bb[0].X0bT, d.ldT, st,
+                                   row_grp, gstride));  // Eq. 9 of block 0
+  } else {
+    EDPC_CUDA(launch_embed(io.mode == 2 ? nullptr : io.data, io.sp, ctl, P + po.E, d.b, d.K, d.D, S[0], ctx, st,
+                           row_grp, gstride));
+  }
   if (d.nloc == 0) EDPC_CUDA(launch_to_bf16(S[0], d.b, d.F, d.F, Slte_b, d.F, Slte_bT, d.ldT, st));
   for (int jj = 0; jj < d.n; ++jj) {
     if (jj == d.nloc) {
@@ -1207,8 +1298,9 @@ int Model::forward_bf16(const StepIO& io, cudaStream_t st) {
     }
     const BlockOff& o = po.blk[jj];
     const float* Xin = S[jj < d.nloc ? jj : jj + 1];
-    EDPC_CUDA(launch_ln_fwd_bf16(Xin, P + o.ln_g, P + o.ln_b, ba[jj].xhat, ba[jj].rstd, bb[jj].X0b, bb[jj].X0bT,
-                                 d.b, d.F, d.ldT, st));  // Eq. 9
+    if (!(jj == 0 && fuse0))
+      EDPC_CUDA(launch_ln_fwd_bf16(Xin, P + o.ln_g, P + o.ln_b, ba[jj].xhat, ba[jj].rstd, bb[jj].X0b, bb[jj].X0bT,
+                                   d.b, d.F, d.ldT, st, row_grp, gstride));  // Eq. 9
     EDPC_TRY(run_tc(blk_site(BR_FWD, jj), st));         // Eqs. 10-12
     EDPC_TRY(run_tc(blk_site(OUT_FWD, jj), st));        // Eq. 13
   }
@@ -1299,7 +1391,7 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
       outbT = bb[j - 1].dOutbT;
     }
     EDPC_CUDA(launch_ln_bwd_bf16(q.dX0, ba[j].xhat, ba[j].rstd, P + o.ln_g, q.dOut, out, outb, outbT, d.b, d.F,
-                                 d.ldT, st));
+                                 d.ldT, st, row_grp, gstride));
   }
   if (d.nloc == 0 && !d.lte) EDPC_TRY(fdm_bwd_joined(io, st));  // w/o LTE: writes dh0
   if (d.nloc == 0 && d.lte) {
@@ -1320,7 +1412,10 @@ int Model::backward_bf16(const StepIO& io, cudaStream_t st) {
     EDPC_TRY(colsums(cj2, side));
     EDPC_TRY(run_tc(kSiteLteDownDx, st));  // writes dh0
   }
-  EDPC_CUDA(launch_embed_bwd(ctx, dh0, d.b, d.K, d.D, G + po.E, emb_part, emb_cnt, st));
+  if (ngroups)
+    EDPC_CUDA(launch_embed_bwd_groups(ctx, dh0, d.K, d.D, G + po.E, ginfo, ngroups, gstride, st));
+  else
+    EDPC_CUDA(launch_embed_bwd(ctx, dh0, d.b, d.K, d.D, G + po.E, emb_part, emb_cnt, st));
   // join the side stream
   EDPC_CUDA(cudaEventRecord(join_ev, side));
   EDPC_CUDA(cudaStreamWaitEvent(st, join_ev, 0));
@@ -1355,6 +1450,8 @@ int Model::head(const StepIO& io, cudaStream_t st) {
   h.dzbT = dzbT;
   h.ldT = d.ldT;
   h.err = &ctl->err;
+  h.rg = row_grp;
+  h.gi = ginfo;
   EDPC_CUDA(launch_head(h, st));
   return EDPC_OK;
 }
@@ -1366,7 +1463,7 @@ int Model::backward(const StepIO& io, cudaStream_t st) {
 int Model::adam(cudaStream_t st) {
   if (precision != EDPC_FP32) {
     NoPdl scope;  // follows the join of the side stream
-    EDPC_CUDA(launch_adam_bf16(P, G, M, V, Pb, nparam, ctl, st));
+    EDPC_CUDA(launch_adam_bf16(P, G, M, V, Pb, np_all, ctl, st));
   } else {
     EDPC_CUDA(launch_adam(P, G, M, V, nparam, ctl, st));
   }
@@ -1378,6 +1475,12 @@ int Model::step(const StepIO& io, cudaStream_t st) {
   EDPC_TRY(forward(io, st));
   EDPC_TRY(head(io, st));
   EDPC_TRY(backward(io, st));
+  if (io.update && io.advance && precision != EDPC_FP32) {
+    // Adam with the step advance in its last CTA
+    NoPdl scope;  // follows the join of the side stream
+    EDPC_CUDA(launch_adam_bf16_advance(P, G, M, V, Pb, np_all, ctl, io.sp, d.K, io.ring_slots, d.b, st));
+    return EDPC_OK;
+  }
   if (io.update) EDPC_TRY(adam(st));
   if (io.advance) EDPC_CUDA(launch_step_advance(ctl, io.sp, d.K, io.ring_slots, d.b, st));
   return EDPC_OK;
@@ -1422,11 +1525,11 @@ int Model::step_delayed(const StepIO& io, cudaStream_t st) {
 
 int Model::launches_per_step() const {
   if (precision != EDPC_FP32) {
-    // forward: embed + 3 per block + LTE (2 GEMMs + FDM) + head GEMM + head
-    int n = 1 + 3 * d.n + 3 + 1 + 1;
+    // forward: embed (with block 0's LN) + 3 per block (2 for block 0) + LTE (2 GEMMs + FDM) + head GEMM + head
+    int n = 1 + 3 * d.n - (d.nloc > 0 ? 1 : 0) + 3 + 1 + 1;
     // backward: head dW/colsum/dX, per block 3 main + 3 side, LTE 3 + 2 side ... + embed
     n += 3 + 6 * d.n + 3 + 4 + 1;
-    return n + 3;  // adam, transpose, advance
+    return n + 2;  // adam (with the step advance), transpose
   }
   int n = 1 + 4 * d.n + 3 + 1 + 1;
   n += 3 + 10 * d.n + 3 + 1 + 3 + 1;

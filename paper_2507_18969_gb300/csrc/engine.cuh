@@ -131,8 +131,23 @@ class Model {
   void select(int q);             // points the members at parity q
   StepCtl* ctl_of(int q) const { return delayed ? par[q].ctl : par[0].ctl; }
 
+  // Grouped mode: independent per-file models in one batch (BF16, Algorithm
+  // 1's schedule). Group g owns rows [r0, r1) and its own parameters, Adam
+  // moments and BF16 copies at offset g * gstride of every parameter buffer;
+  // every GEMM runs over all groups in one launch (tile lists with the
+  // group's weights, or the group's own K range for weight gradients).
+  int ngroups = 0;
+  size_t gstride = 0;               // floats between consecutive groups' parameters
+  size_t np_all = 0;                // parameter floats of all groups (nparam when not grouped)
+  int* row_grp = nullptr;           // device, b: group of each row
+  GroupInfo* ginfo = nullptr;       // device, ngroups
+  int4* gtiles = nullptr;           // device: M tiles {m0, m_end, group, 0} of forward / dX GEMMs
+  int ngtiles = 0;
+  int4* gkr = nullptr;              // device, ngroups: {k0, K blocks of 64, 0, 0} of weight gradients
+  std::vector<GroupInfo> groups_h;
+
   ~Model();
-  int init(const edpc_cfg& cfg, int streams);
+  int init(const edpc_cfg& cfg, int streams, const std::vector<GroupInfo>* groups = nullptr);
   int set_ctl_for_step(int i, int t, int bact, int ring_slots, cudaStream_t st);
 
   // One model step. mode: 0 encode, 1 decode, 2 model API.

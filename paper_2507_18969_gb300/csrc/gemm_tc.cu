@@ -18,6 +18,8 @@
 // stops waiting, frees its TMEM and returns.
 #include <cudaTypedefs.h>
 
+#include <climits>
+
 #include <mutex>
 
 #include "gemm_tc.cuh"
@@ -66,14 +68,31 @@ __global__ void __launch_bounds__(128, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);  // tmem_slot + 2: split-K flag
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM;
+  // Rows [m0, mend) of the tile are stored; grouped mode reads the tile (and
+  // its group) from the tile list, or the group's K range (weight gradients).
+  int m0 = blockIdx.y * BM, mend = e.M, grp = 0;
+  if (e.mt) {
+    const int4 t = e.mt[blockIdx.y];
+    m0 = t.x;
+    mend = t.y;
+    grp = t.z;
+  }
   // N offset of the tile: in TC_BRANCH mode a tile covers hidden units
   // [SW*bx, SW*bx + SW) of every branch.
   const int n0 = (MODE == TC_BRANCH) ? blockIdx.x * SW : blockIdx.x * BN;
-  // K blocks of this CTA: all of them, or split z of gridDim.z (split-K)
-  const int nk_all = (e.K + BK - 1) / BK;
-  const int kb_lo = (int)(((long long)nk_all * blockIdx.z) / gridDim.z);
-  const int nk = (int)(((long long)nk_all * (blockIdx.z + 1)) / gridDim.z) - kb_lo;
+  // K blocks of this CTA: all of them, split z of gridDim.z (split-K), or the
+  // group's own range (grouped weight gradients; k0 is a multiple of 64)
+  int kel0 = 0, kb_lo = 0, nk = 0;
+  if (e.gk) {
+    grp = blockIdx.z;
+    const int4 t = e.gk[grp];
+    kel0 = t.x;
+    nk = t.y;
+  } else {
+    const int nk_all = (e.K + BK - 1) / BK;
+    kb_lo = (int)(((long long)nk_all * blockIdx.z) / gridDim.z);
+    nk = (int)(((long long)nk_all * (blockIdx.z + 1)) / gridDim.z) - kb_lo;
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -100,12 +119,14 @@ __global__ void __launch_bounds__(128, 1)
   // two kernels earlier (b_early), its first tiles are fetched before the
   // programmatic-dependent-launch wait; A comes from the previous kernel.
   auto load_b = [&](int kb, int s) {
-    if (MODE == TC_BRANCH) {
+    const int kc = kel0 + (kb_lo + kb) * BK;
 #pragma unroll
-      for (int i = 0; i < SECTIONS; ++i)
-        tma_load_2d(sB + s * B_BYTES + i * (SW * BKB), &tb, (kb_lo + kb) * BK, i * e.H + n0, &full[s]);
-    } else {
-      tma_load_2d(sB + s * B_BYTES, &tb, (kb_lo + kb) * BK, n0, &full[s]);
+    for (int i = 0; i < SECTIONS; ++i) {
+      const int brow = (MODE == TC_BRANCH ? i * e.H : 0) + n0;
+      if (e.mt)
+        tma_load_3d(sB + s * B_BYTES + i * (SW * BKB), &tb, kc, brow, grp, &full[s]);
+      else
+        tma_load_2d(sB + s * B_BYTES + i * (SW * BKB), &tb, kc, brow, &full[s]);
     }
   };
   const int npre = e.b_early ? (nk < STAGES ? nk : STAGES) : 0;
@@ -128,7 +149,7 @@ __global__ void __launch_bounds__(128, 1)
         mbar_expect_tx(&full[s], A_BYTES + B_BYTES);
         load_b(kb, s);
       }
-      tma_load_2d(sA + s * A_BYTES, &ta, (kb_lo + kb) * BK, m0, &full[s]);
+      tma_load_2d(sA + s * A_BYTES, &ta, kel0 + (kb_lo + kb) * BK, m0, &full[s]);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
@@ -162,9 +183,21 @@ __global__ void __launch_bounds__(128, 1)
   static_assert(STAGES * A_BYTES >= 8192 + kStageOut, "A stages hold the epilogue staging");
   if (ok) {
     const EpiOut o{&tmc, &tmcb, sA + 8192 + warp * kStageOutWarp, m0 + warp * 32, lane};
-    tc_epilogue<BN, MODE, KB, F8>(e, tmem + ((uint32_t)(warp * 32) << 16), m0, n0, blockIdx.z, gridDim.z,
-                                  blockIdx.y * gridDim.x + blockIdx.x, reinterpret_cast<__nv_bfloat16*>(sA),
-                                  reinterpret_cast<volatile int*>(tmem_slot + 2), threadIdx.x, threadIdx.x, o);
+    if (e.mt || e.gk) {
+      // grouped mode: the tile's row bound, its group's bias or gradient output
+      TcEpi eg = e;
+      eg.M = mend;
+      eg.rlim = mend;
+      if (e.mt && e.bias) eg.bias = e.bias + (long long)grp * e.gs;
+      if (e.gk) eg.C = e.C + (long long)grp * e.gs;
+      tc_epilogue<BN, MODE, KB, F8>(eg, tmem + ((uint32_t)(warp * 32) << 16), m0, n0, 0, 1, 0,
+                                    reinterpret_cast<__nv_bfloat16*>(sA),
+                                    reinterpret_cast<volatile int*>(tmem_slot + 2), threadIdx.x, threadIdx.x, o);
+    } else {
+      tc_epilogue<BN, MODE, KB, F8>(e, tmem + ((uint32_t)(warp * 32) << 16), m0, n0, blockIdx.z, gridDim.z,
+                                    blockIdx.y * gridDim.x + blockIdx.x, reinterpret_cast<__nv_bfloat16*>(sA),
+                                    reinterpret_cast<volatile int*>(tmem_slot + 2), threadIdx.x, threadIdx.x, o);
+    }
     tma_st_drain(lane);
   }
   if (!ok && threadIdx.x == 0 && e.err) atomicOr(e.err, kErrTcTimeout);
@@ -196,10 +229,11 @@ cudaError_t launch_bn_mode(const TcGemm& g, cudaStream_t st) {
   });
   if (attr_err != cudaSuccess) return attr_err;
   TcEpi e{g.M, g.N, g.K, g.H, g.k, g.C, g.ldc, g.Cb, g.ldcb, g.CbT, g.ldct, g.bias, g.R, g.ldr, g.Aux, g.ldaux, g.err,
-          g.inv_a, g.inv_b, g.b_early ? 1 : 0, g.ws, g.cnt, 0, 0, g.has_tmc ? 1 : 0, g.has_tmcb ? 1 : 0};
+          g.inv_a, g.inv_b, g.b_early ? 1 : 0, g.ws, g.cnt, 0, 0, g.has_tmc ? 1 : 0, g.has_tmcb ? 1 : 0,
+          g.mt, g.gk, (long long)g.gs, INT_MAX};
   constexpr int SW = (MODE == TC_BRANCH) ? BN / KB : BN;
   const int ntile = (MODE == TC_BRANCH) ? (g.H + SW - 1) / SW : (g.N + BN - 1) / BN;
-  dim3 grid(ntile, (g.M + BM - 1) / BM, g.splitk > 1 ? g.splitk : 1);
+  dim3 grid(ntile, g.mt ? g.nmt : (g.M + BM - 1) / BM, g.gk ? g.ngk : (g.splitk > 1 ? g.splitk : 1));
   return launch_k(k, grid, dim3(128), smem_bytes<BN>(), st, g.ta, g.tb, g.tmc, g.tmcb, e);
 }
 
@@ -232,6 +266,23 @@ int make_tmap_bf16(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t co
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return fail(EDPC_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return EDPC_OK;
+}
+
+int make_tmap_bf16_groups(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
+                          uint64_t groups, uint64_t gstride, uint32_t box_rows) {
+  auto enc = get_encode();
+  if (!enc) return fail(EDPC_ECUDA, "cuTensorMapEncodeTiled is not available");
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((ld * 2) & 15) || ((gstride * 2) & 15) || groups < 1)
+    return fail(EDPC_EINVAL, "grouped tensor map base or strides are not 16-byte aligned");
+  cuuint64_t dims[3] = {cols, rows, groups};
+  cuuint64_t strides[2] = {ld * 2, gstride * 2};
+  cuuint32_t box[3] = {64, box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(EDPC_ECUDA, "cuTensorMapEncodeTiled (3-D) failed: " + std::to_string((int)r));
   return EDPC_OK;
 }
 
@@ -271,7 +322,9 @@ int tc_build_out_maps(TcGemm* g) {
   // A TMA store must start on a 16-byte boundary: the branch modes start
   // branch i's chunks at column i * H, so H must be a multiple of 8 (BF16).
   const bool cols_ok = g->mode == TC_PLAIN || g->H % 8 == 0;
-  if (g->splitk <= 1 && cols_ok) {  // split-K partials and their sums keep direct stores
+  // split-K partials and their sums, and grouped weight gradients (one output
+  // base per group), keep direct stores
+  if (g->splitk <= 1 && cols_ok && !g->gk) {
     g->has_tmc = build(&g->tmc, g->C, wc, g->ldc, 4, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, CU_TENSOR_MAP_SWIZZLE_128B);
     g->has_tmcb = build(&g->tmcb, g->Cb, wcb, g->ldcb, 2, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, CU_TENSOR_MAP_SWIZZLE_64B);
   }
@@ -312,6 +365,12 @@ cudaError_t launch_gemm_tc_t(const TcGemm& g, cudaStream_t st) {
     const int nk = (g.K + bk_elems<F8>() - 1) / bk_elems<F8>();
     if (g.mode != TC_PLAIN || g.bias || g.R || g.Cb || g.CbT || !g.ws || !g.cnt || g.splitk > nk ||
         g.splitk > 65535)
+      return cudaErrorInvalidValue;
+  }
+  if (g.mt || g.gk) {
+    // grouped mode: one-tile kernel, no split-K, a non-empty tile or group list
+    if (g.persistent || g.splitk > 1 || (g.mt && g.gk) || (g.mt && (g.nmt < 1 || g.nmt > 65535)) ||
+        (g.gk && (g.ngk < 1 || g.ngk > 65535)) || (g.gk && (g.has_tmc || g.has_tmcb)))
       return cudaErrorInvalidValue;
   }
   if (g.persistent) return launch_gemm_tcp(g, st);  // checks the tile against the box itself

@@ -66,6 +66,20 @@ struct TcGemm {
   bool b_early = true; // B was written two or more launches back: prefetch it before the PDL wait
   const float* inv_a = nullptr;
   const float* inv_b = nullptr;
+  // Grouped mode (independent per-file models; BF16, one-tile kernel only):
+  //   mt  forward / dX GEMMs: nmt M tiles {m0, m_end, group, 0}: the tile
+  //       covers rows [m0, m_end) (rows from m_end to m0 + 128 belong to the
+  //       next group and are neither stored nor read back); tb is a 3-D map
+  //       over the groups' B matrices (group coordinate z) and the bias of
+  //       the tile's group starts at bias + group * gs.
+  //   gk  weight-gradient GEMMs (K = streams): ngk groups {k0, nkb, 0, 0}:
+  //       grid.z runs over the groups, group g contracts K elements
+  //       [k0, k0 + 64 nkb) and writes C + g * gs.
+  const int4* mt = nullptr;
+  int nmt = 0;
+  const int4* gk = nullptr;
+  int ngk = 0;
+  size_t gs = 0;
 };
 
 constexpr int kErrTcTimeout = 4;
@@ -77,6 +91,11 @@ int make_tmap_bf16(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t co
 // The same for a byte matrix (FP8 e4m3) with row stride ld bytes and boxes of
 // 128 columns x box_rows rows.
 int make_tmap_u8(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols, uint64_t ld, uint32_t box_rows);
+// A 3-D BF16 map over `groups` row-major matrices [rows][cols] (row stride ld
+// elements), matrix g at base + g * gstride elements, boxes of 64 columns x
+// box_rows rows of one matrix.
+int make_tmap_bf16_groups(CUtensorMap* tm, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
+                          uint64_t groups, uint64_t gstride, uint32_t box_rows);
 
 cudaError_t launch_gemm_tc(const TcGemm& g, cudaStream_t st);
 // The persistent kernel (g.persistent), dispatched by launch_gemm_tc.

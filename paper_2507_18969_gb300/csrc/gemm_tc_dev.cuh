@@ -39,6 +39,10 @@ struct TcEpi {
   unsigned* cnt;       // split-K arrival counter per output tile
   int ntn, ntm;        // persistent kernel: N tiles and M tiles of the problem
   int tma_c, tma_cb;   // C / Cb have output tensor maps: whole 32 x 32 chunks go out by TMA store
+  const int4* mt;      // grouped mode (see TcGemm): M tiles of the forward / dX GEMMs
+  const int4* gk;      // grouped mode: K ranges of the weight-gradient GEMMs
+  long long gs;        // grouped mode: parameter stride between groups (floats)
+  int rlim;            // rows at or beyond rlim are not written by the transposed stores
 };
 
 // Per-warp output staging for TMA stores: 4 KB FP32 rows (128-byte swizzle)
@@ -89,6 +93,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// 3-D tiled load (grouped mode: coordinate c2 selects the group's matrix).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -228,14 +241,14 @@ __device__ __forceinline__ bool epi_and(bool p) {
 // runs to CT[(n0 + c) * ldct + m0 + row]. Columns at or beyond N and 8-row runs
 // at or beyond ldct are skipped. Collective over the epilogue threads.
 __device__ __forceinline__ void store_T32(const float (&v)[32], __nv_bfloat16* sT, int m0, int n0, int N,
-                                          __nv_bfloat16* CT, int ldct, int r, int et) {
+                                          __nv_bfloat16* CT, int ldct, int r, int et, int rlim) {
 #pragma unroll
   for (int c = 0; c < 32; ++c) sT[c * 128 + r] = __float2bfloat16_rn(v[c]);
   epi_sync();
   for (int idx = et; idx < 32 * 16; idx += 128) {
     const int c = idx >> 4, seg = idx & 15;
     const int row0 = m0 + seg * 8;
-    if (n0 + c < N && row0 + 8 <= ldct)
+    if (n0 + c < N && row0 + 8 <= ldct && row0 + 8 <= rlim)
       *reinterpret_cast<uint4*>(CT + (size_t)(n0 + c) * ldct + row0) =
           *reinterpret_cast<const uint4*>(sT + c * 128 + seg * 8);
   }
@@ -425,7 +438,7 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t trow, int m
         for (int j = 0; j < 32; ++j) v[j] += rr[j];
       }
       out_chunk(e, o, v, rok, row, 0, nb, e.N, e.C, e.ldc, e.Cb, e.ldcb);
-      if (e.CbT) store_T32(v, sT, m0, nb, e.N, e.CbT, e.ldct, r, et);
+      if (e.CbT) store_T32(v, sT, m0, nb, e.N, e.CbT, e.ldct, r, et, e.rlim);
     }
   } else if (MODE == TC_BRANCH) {
     // X_i for the tile's hidden units h = n0 + c0 + j (32 at a time), then
@@ -453,7 +466,7 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t trow, int m
 #pragma unroll
       for (int j = 0; j < 32; ++j) g[j] = gelu_f(g[j]);
       out_chunk(e, o, g, rok, row, 0, hb, e.H, nullptr, 0, e.Cb, e.ldcb);
-      store_T32(g, sT, m0, hb, e.H, e.CbT, e.ldct, r, et);
+      store_T32(g, sT, m0, hb, e.H, e.CbT, e.ldct, r, et, e.rlim);
     }
   } else {
     // TC_BRANCH_BWD: dG tile of hidden units [n0, n0 + BN).
@@ -496,7 +509,7 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t trow, int m
         }
         const int colb = i * e.H;
         out_chunk(e, o, dd, rok, row, colb, hb, e.H, e.C, e.ldc, e.Cb, e.ldcb);
-        store_T32(dd, sT, m0, colb + hb, colb + e.H, e.CbT, e.ldct, r, et);
+        store_T32(dd, sT, m0, colb + hb, colb + e.H, e.CbT, e.ldct, r, et, e.rlim);
       }
     }
   }

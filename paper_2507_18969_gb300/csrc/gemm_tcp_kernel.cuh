@@ -22,6 +22,7 @@
 
 #include <cudaTypedefs.h>
 
+#include <climits>
 #include <mutex>
 
 #include "gemm_tc.cuh"
@@ -239,7 +240,8 @@ cudaError_t launch_p(const TcGemm& g, cudaStream_t st) {
   const int ntm = (g.M + BM - 1) / BM;
   const int S = g.splitk > 1 ? g.splitk : 1;
   TcEpi e{g.M, g.N, g.K, g.H, g.k, g.C, g.ldc, g.Cb, g.ldcb, g.CbT, g.ldct, g.bias, g.R, g.ldr, g.Aux, g.ldaux, g.err,
-          g.inv_a, g.inv_b, 0, g.ws, g.cnt, ntn, ntm, g.has_tmc ? 1 : 0, g.has_tmcb ? 1 : 0};
+          g.inv_a, g.inv_b, 0, g.ws, g.cnt, ntn, ntm, g.has_tmc ? 1 : 0, g.has_tmcb ? 1 : 0,
+          nullptr, nullptr, 0, INT_MAX};
   const long long units = (long long)ntn * ntm * S;
   if (units <= 0 || units > (1ll << 30)) return cudaErrorInvalidValue;
   const int nct = (int)(units < max_ctas ? units : max_ctas);

@@ -77,10 +77,11 @@ __device__ __forceinline__ int warp_isum(int v) {
 // ============================================================================================
 __global__ void embed_kernel(const uint8_t* __restrict__ data, Split sp, const StepCtl* __restrict__ ctl,
                              const float* __restrict__ E, int K, int D, float* __restrict__ X,
-                             uint8_t* __restrict__ ctx) {
+                             uint8_t* __restrict__ ctx, const int* __restrict__ rg, size_t gs) {
   pdl_wait();
   pdl_launch();
   const int s = blockIdx.x;
+  if (rg) E += (size_t)rg[s] * gs;  // grouped mode: the row's own model
   const int F = K * D;
   // A stream past its end (inactive) keeps its last context: its bytes
   // [i - K, i) would run beyond the stream, and its outputs are masked.
@@ -97,8 +98,8 @@ __global__ void embed_kernel(const uint8_t* __restrict__ data, Split sp, const S
 }
 
 cudaError_t launch_embed(const uint8_t* data, Split sp, const StepCtl* ctl, const float* E, int b, int K,
-                         int D, float* X, uint8_t* ctx, cudaStream_t st) {
-  return launch_k(embed_kernel, dim3(b), dim3(128), 0, st, data, sp, ctl, E, K, D, X, ctx);
+                         int D, float* X, uint8_t* ctx, cudaStream_t st, const int* rg, size_t gs) {
+  return launch_k(embed_kernel, dim3(b), dim3(128), 0, st, data, sp, ctl, E, K, D, X, ctx, rg, gs);
 }
 
 // ============================================================================================
@@ -929,15 +930,23 @@ cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st, bool persist
 __global__ void __launch_bounds__(256) embed_bwd_owner_kernel(const uint8_t* __restrict__ ctx,
                                                               const float* __restrict__ dX, int P, int D,
                                                               float* __restrict__ dE, float* __restrict__ part,
-                                                              unsigned* __restrict__ cnt) {
+                                                              unsigned* __restrict__ cnt,
+                                                              const GroupInfo* __restrict__ gi, int K, size_t gs) {
   pdl_wait();
   pdl_launch();
   __shared__ float wsum[8][64];
   __shared__ int is_last;
   const uint32_t c = blockIdx.x;
-  const int nq = gridDim.y, q = blockIdx.y;
+  // grouped mode: blockIdx.y is the group, one chunk = its rows' positions
+  const int nq = gi ? 1 : gridDim.y, q = gi ? 0 : blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int c_lo = min(P, q * kEmbChunkPos), c_hi = min(P, c_lo + kEmbChunkPos);
+  int c_lo = min(P, q * kEmbChunkPos), c_hi = min(P, c_lo + kEmbChunkPos);
+  if (gi) {
+    const GroupInfo g = gi[blockIdx.y];
+    c_lo = g.r0 * K;
+    c_hi = g.r1 * K;
+    dE += (size_t)blockIdx.y * gs;
+  }
   const int per = ((c_hi - c_lo + 8 * 128 - 1) / (8 * 128)) * 128;  // positions per warp, a multiple of 128
   const int p_lo = min(c_hi, c_lo + w * per), p_hi = min(c_hi, p_lo + per);
   const bool al4 = (reinterpret_cast<uintptr_t>(ctx) & 3) == 0;
@@ -1032,7 +1041,14 @@ cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, 
   const int nq = embed_bwd_chunks(b, K);
   if (nq > 1 && (!part || !cnt)) return cudaErrorInvalidValue;
   return launch_k(embed_bwd_owner_kernel, dim3(256, nq < 1 ? 1 : nq), dim3(256), 0, st, ctx, dX, b * K, D, dE, part,
-                  cnt);
+                  cnt, (const GroupInfo*)nullptr, K, (size_t)0);
+}
+
+cudaError_t launch_embed_bwd_groups(const uint8_t* ctx, const float* dX, int K, int D, float* dE,
+                                    const GroupInfo* gi, int ngroups, size_t gs, cudaStream_t st) {
+  if (D > 64 || ngroups < 1 || ngroups > 65535 || !gi) return cudaErrorInvalidValue;
+  return launch_k(embed_bwd_owner_kernel, dim3(256, ngroups), dim3(256), 0, st, ctx, dX, 0, D, dE, (float*)nullptr,
+                  (unsigned*)nullptr, gi, K, gs);
 }
 
 // ============================================================================================
@@ -1068,11 +1084,9 @@ cudaError_t launch_adam(float* P, const float* G, float* M, float* V, size_t n, 
 // Reads the step control of the current step from `src` and writes the next
 // step's to `dst` (the same record, or the other of the delayed-update
 // schedule's two, whose sticky error bits are kept).
-__global__ void step_advance_kernel(const StepCtl* src, StepCtl* dst, Split sp, int K, int ring_slots, int b) {
-  pdl_wait();
-  pdl_launch();
-  StepCtl c = *src;
-  c.err |= dst->err;
+// The control record of the next step (i + 1) from that of the current one.
+__device__ __forceinline__ StepCtl advance_ctl(StepCtl c, int dst_err, Split sp, int K, int ring_slots, int b) {
+  c.err |= dst_err;
   c.i += 1;
   c.t += 1;
   long long i = c.i;
@@ -1089,9 +1103,15 @@ __global__ void step_advance_kernel(const StepCtl* src, StepCtl* dst, Split sp, 
   c.bc1 = 1.0f - powf(kB1, (float)c.t);
   c.bc2 = 1.0f - powf(kB2, (float)c.t);
   c.slot = (int)((i - K) % ring_slots);
-  *dst = c;
+  c.arrive = 0u;
+  return c;
 }
 
+__global__ void step_advance_kernel(const StepCtl* src, StepCtl* dst, Split sp, int K, int ring_slots, int b) {
+  pdl_wait();
+  pdl_launch();
+  *dst = advance_ctl(*src, dst->err, sp, K, ring_slots, b);
+}
 cudaError_t launch_step_advance(StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st,
                                 StepCtl* dst) {
   return launch_k(step_advance_kernel, dim3(1), dim3(1), 0, st, (const StepCtl*)ctl, dst ? dst : ctl, sp, K,
@@ -1445,10 +1465,15 @@ __global__ void __launch_bounds__(32 * kRowsT) head_kernel(HeadArgs a) {
 
     float* dz = a.dz + (size_t)s * 256 + lane * 8;
     float* po = a.p ? a.p + (size_t)s * 256 + lane * 8 : nullptr;
+    float inv = c.inv_bact;
+    if (a.rg) {  // grouped mode: the mean over the row's own group (as set_ctl / step_advance form it)
+      const int n = group_active(a.gi[a.rg[s]], c.i);
+      inv = n > 0 ? 1.0f / (float)n : 0.f;
+    }
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
       int j = lane * 8 + q;
-      dzv[q] = active ? (p[q] - (j == x ? 1.0f : 0.0f)) * c.inv_bact : 0.f;
+      dzv[q] = active ? (p[q] - (j == x ? 1.0f : 0.0f)) * inv : 0.f;
       dz[q] = dzv[q];
       if (po) po[q] = p[q];
     }
@@ -1508,7 +1533,8 @@ template <int NPL>
 __global__ void __launch_bounds__(32 * kRowsLN)
     ln_fwd_bf16_kernel(const float* __restrict__ X, const float* __restrict__ g, const float* __restrict__ be,
                        float* __restrict__ xhat, float* __restrict__ rstd, __nv_bfloat16* __restrict__ X0b,
-                       __nv_bfloat16* __restrict__ X0bT, int b, int F, int ldT) {
+                       __nv_bfloat16* __restrict__ X0bT, int b, int F, int ldT, const int* __restrict__ rg,
+                       size_t gs) {
   pdl_wait();
   pdl_launch();
   extern __shared__ __nv_bfloat16 tile_dyn[];
@@ -1516,6 +1542,10 @@ __global__ void __launch_bounds__(32 * kRowsLN)
   const int row = blockIdx.x * kRowsLN + warp;
   __nv_bfloat16* trow = tile_dyn + (size_t)warp * F;
   if (row < b) {
+    if (rg) {  // grouped mode: the row's own gamma and beta
+      g += (size_t)rg[row] * gs;
+      be += (size_t)rg[row] * gs;
+    }
     const float* x = X + (size_t)row * F;
     if (NPL > 0) {
       float v[NPL > 0 ? NPL : 1];
@@ -1569,23 +1599,119 @@ __global__ void __launch_bounds__(32 * kRowsLN)
 }
 
 cudaError_t launch_ln_fwd_bf16(const float* X, const float* g, const float* be, float* xhat, float* rstd,
-                               __nv_bfloat16* X0b, __nv_bfloat16* X0bT, int b, int F, int ldT, cudaStream_t st) {
+                               __nv_bfloat16* X0b, __nv_bfloat16* X0bT, int b, int F, int ldT, cudaStream_t st,
+                               const int* rg, size_t gs) {
   const size_t smem = (size_t)kRowsLN * F * sizeof(__nv_bfloat16);
   const dim3 grid(div_up(b, kRowsLN)), block(32 * kRowsLN);
   switch (F) {
-    case 128: return launch_k(ln_fwd_bf16_kernel<4>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT);
-    case 256: return launch_k(ln_fwd_bf16_kernel<8>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT);
-    case 512: return launch_k(ln_fwd_bf16_kernel<16>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT);
-    case 1024: return launch_k(ln_fwd_bf16_kernel<32>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT);
-    default: return launch_k(ln_fwd_bf16_kernel<0>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT);
+    case 128:
+      return launch_k(ln_fwd_bf16_kernel<4>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT, rg, gs);
+    case 256:
+      return launch_k(ln_fwd_bf16_kernel<8>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT, rg, gs);
+    case 512:
+      return launch_k(ln_fwd_bf16_kernel<16>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT, rg,
+                      gs);
+    case 1024:
+      return launch_k(ln_fwd_bf16_kernel<32>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT, rg,
+                      gs);
+    default:
+      return launch_k(ln_fwd_bf16_kernel<0>, grid, block, smem, st, X, g, be, xhat, rstd, X0b, X0bT, b, F, ldT, rg, gs);
   }
+}
+
+// Embedding (the model input) and the first block's LayerNorm in one launch:
+// warp w of the CTA gathers row s's context (as embed_kernel does), holds
+// X[s][c] for c = lane + 32 q in registers, writes X (FP32) and then runs
+// exactly the arithmetic of ln_fwd_bf16_kernel<NPL> on those values.
+template <int NPL>
+__global__ void __launch_bounds__(32 * kRowsLN)
+    embed_ln_bf16_kernel(const uint8_t* __restrict__ data, Split sp, const StepCtl* __restrict__ ctl,
+                         const float* __restrict__ E, int K, int D, float* __restrict__ X, uint8_t* __restrict__ ctx,
+                         const float* __restrict__ g, const float* __restrict__ be, float* __restrict__ xhat,
+                         float* __restrict__ rstd, __nv_bfloat16* __restrict__ X0b, __nv_bfloat16* __restrict__ X0bT,
+                         int b, int ldT, const int* __restrict__ rg, size_t gs) {
+  pdl_wait();
+  pdl_launch();
+  constexpr int F = 32 * NPL;
+  extern __shared__ __nv_bfloat16 tile_dyn[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * kRowsLN + warp;
+  __nv_bfloat16* trow = tile_dyn + (size_t)warp * F;
+  if (s < b) {
+    if (rg) {  // grouped mode: the row's own model
+      const size_t o = (size_t)rg[s] * gs;
+      E += o;
+      g += o;
+      be += o;
+    }
+    const int i = ctl->i;
+    // A stream past its end (inactive) keeps its last context, as in embed_kernel.
+    if (data && i <= sp.len(s)) {
+      const long long base = sp.off(s) + i - K;
+      for (int k = lane; k < K; k += 32) ctx[(size_t)s * K + k] = data[base + k];
+    }
+    __syncwarp();
+    float v[NPL];
+#pragma unroll
+    for (int q = 0; q < NPL; ++q) {
+      const int c = lane + 32 * q, k = c / D, dd = c - k * D;
+      v[q] = E[(int)ctx[(size_t)s * K + k] * D + dd];
+      X[(size_t)s * F + c] = v[q];
+    }
+    float sm = 0.f;
+#pragma unroll
+    for (int q = 0; q < NPL; ++q) sm += v[q];
+    const float mean = warp_sum(sm) / (float)F;
+    float qv = 0.f;
+#pragma unroll
+    for (int q = 0; q < NPL; ++q) {
+      const float d = v[q] - mean;
+      qv += d * d;
+    }
+    const float r = 1.0f / sqrtf(warp_sum(qv) / (float)F + kLnEps);
+#pragma unroll
+    for (int q = 0; q < NPL; ++q) {
+      const int c = lane + 32 * q;
+      const float h = (v[q] - mean) * r;
+      xhat[(size_t)s * F + c] = h;
+      const __nv_bfloat16 o = __float2bfloat16_rn(h * g[c] + be[c]);
+      X0b[(size_t)s * F + c] = o;
+      trow[c] = o;
+    }
+    if (lane == 0) rstd[s] = r;
+  } else {
+    for (int c = lane; c < F; c += 32) trow[c] = __float2bfloat16_rn(0.f);
+  }
+  __syncthreads();
+  store_tile_T<kRowsLN>(tile_dyn, F, F, blockIdx.x * kRowsLN, X0bT, ldT);
+}
+
+cudaError_t launch_embed_ln_bf16(const uint8_t* data, Split sp, const StepCtl* ctl, const float* E, int b, int K,
+                                 int D, float* X, uint8_t* ctx, const float* g, const float* be, float* xhat,
+                                 float* rstd, __nv_bfloat16* X0b, __nv_bfloat16* X0bT, int ldT, cudaStream_t st,
+                                 const int* rg, size_t gs) {
+  const int F = K * D;
+  const size_t smem = (size_t)kRowsLN * F * sizeof(__nv_bfloat16);
+  const dim3 grid(div_up(b, kRowsLN)), block(32 * kRowsLN);
+#define EDPC_ELN(NPL) \
+  launch_k(embed_ln_bf16_kernel<NPL>, grid, block, smem, st, data, sp, ctl, E, K, D, X, ctx, g, be, xhat, rstd, X0b, \
+           X0bT, b, ldT, rg, gs)
+  switch (F) {
+    case 128: return EDPC_ELN(4);
+    case 256: return EDPC_ELN(8);
+    case 512: return EDPC_ELN(16);
+    case 1024: return EDPC_ELN(32);
+    default: return cudaErrorInvalidValue;
+  }
+#undef EDPC_ELN
 }
 
 template <int NPL>
 __global__ void __launch_bounds__(32 * kRowsLN)
     ln_bwd_bf16_kernel(const float* __restrict__ dX0, const float* __restrict__ xhat, const float* __restrict__ rstd,
                        const float* __restrict__ g, const float* __restrict__ dRes, float* __restrict__ dX,
-                       __nv_bfloat16* __restrict__ dXb, __nv_bfloat16* __restrict__ dXbT, int b, int F, int ldT) {
+                       __nv_bfloat16* __restrict__ dXb, __nv_bfloat16* __restrict__ dXbT, int b, int F, int ldT,
+                       const int* __restrict__ rg, size_t gs) {
   pdl_wait();
   pdl_launch();
   extern __shared__ __nv_bfloat16 tile_dyn[];
@@ -1593,6 +1719,7 @@ __global__ void __launch_bounds__(32 * kRowsLN)
   const int row = blockIdx.x * kRowsLN + warp;
   __nv_bfloat16* trow = tile_dyn + (size_t)warp * F;
   if (row < b) {
+    if (rg) g += (size_t)rg[row] * gs;  // grouped mode: the row's own gamma
     const size_t o = (size_t)row * F;
     const float r = rstd[row];
     if (NPL > 0) {
@@ -1654,21 +1781,20 @@ __global__ void __launch_bounds__(32 * kRowsLN)
 
 cudaError_t launch_ln_bwd_bf16(const float* dX0, const float* xhat, const float* rstd, const float* g,
                                const float* dRes, float* dX, __nv_bfloat16* dXb, __nv_bfloat16* dXbT, int b, int F,
-                               int ldT, cudaStream_t st) {
+                               int ldT, cudaStream_t st, const int* rg, size_t gs) {
   const size_t smem = dXbT ? (size_t)kRowsLN * F * sizeof(__nv_bfloat16) : 0;
   const dim3 grid(div_up(b, kRowsLN)), block(32 * kRowsLN);
+#define EDPC_LNB(NPL)                                                                                      \
+  launch_k(ln_bwd_bf16_kernel<NPL>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT, rg, \
+           gs)
   switch (F) {
-    case 128:
-      return launch_k(ln_bwd_bf16_kernel<4>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT);
-    case 256:
-      return launch_k(ln_bwd_bf16_kernel<8>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT);
-    case 512:
-      return launch_k(ln_bwd_bf16_kernel<16>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT);
-    case 1024:
-      return launch_k(ln_bwd_bf16_kernel<32>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT);
-    default:
-      return launch_k(ln_bwd_bf16_kernel<0>, grid, block, smem, st, dX0, xhat, rstd, g, dRes, dX, dXb, dXbT, b, F, ldT);
+    case 128: return EDPC_LNB(4);
+    case 256: return EDPC_LNB(8);
+    case 512: return EDPC_LNB(16);
+    case 1024: return EDPC_LNB(32);
+    default: return EDPC_LNB(0);
   }
+#undef EDPC_LNB
 }
 
 // ============================================================================================
@@ -1852,12 +1978,53 @@ cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st) {
 }
 
 // ============================================================================================
+// Grouped column sums (bias and LN-affine gradients of independent per-file
+// models): CTA = 128 columns of one job and one group; thread t sums column
+// c0 + t over the group's rows in increasing order.
+// ============================================================================================
+__global__ void __launch_bounds__(128) colsum_groups_kernel(ColsumJobs jobs, const GroupInfo* __restrict__ gi,
+                                                            size_t gs) {
+  pdl_wait();
+  pdl_launch();
+  const ColsumJob j = jobs.job[blockIdx.z];
+  const GroupInfo g = gi[blockIdx.y];
+  const int c = blockIdx.x * 128 + threadIdx.x;
+  if (c >= j.cols) return;
+  float acc = 0.f;
+  const float* x = j.X + (size_t)g.r0 * j.ld + c;
+  if (j.Y) {
+    const float* y = j.Y + (size_t)g.r0 * j.ld + c;
+    for (int r = 0; r < g.r1 - g.r0; ++r) acc += x[(size_t)r * j.ld] * y[(size_t)r * j.ld];
+  } else {
+    for (int r = 0; r < g.r1 - g.r0; ++r) acc += x[(size_t)r * j.ld];
+  }
+  j.out[(size_t)blockIdx.y * gs + c] = acc;
+}
+
+cudaError_t launch_colsum_groups(const ColsumJobs& jobs, const GroupInfo* gi, int ngroups, size_t gs,
+                                 cudaStream_t st) {
+  if (jobs.n < 1 || jobs.n > kMaxColsumJobs || ngroups < 1 || ngroups > 65535 || !gi) return cudaErrorInvalidValue;
+  int maxc = 0;
+  for (int k = 0; k < jobs.n; ++k) maxc = max(maxc, jobs.job[k].cols);
+  return launch_k(colsum_groups_kernel, dim3(div_up(maxc, 128), ngroups, jobs.n), dim3(128), 0, st, jobs, gi, gs);
+}
+
+// ============================================================================================
 // Adam with the BF16 weight copy refreshed in the same pass; transposed copies
 // of every weight matrix in one launch (32 x 32 tiles through shared memory).
 // ============================================================================================
+// With adv set, the last CTA to finish (counted on ctl->arrive after a fence,
+// so every CTA has read the step's scalars and written its parameters) also
+// writes the next step's control record, as step_advance_kernel does.
+struct AdvanceArgs {
+  int on;
+  Split sp;
+  int K, ring_slots, b;
+};
+
 __global__ void adam_bf16_kernel(float* P, const float* Pin, const float* __restrict__ G, float* __restrict__ M,
-                                 float* __restrict__ V, __nv_bfloat16* __restrict__ Pb, size_t n,
-                                 const StepCtl* __restrict__ ctl) {
+                                 float* __restrict__ V, __nv_bfloat16* __restrict__ Pb, size_t n, StepCtl* ctl,
+                                 AdvanceArgs adv) {
   pdl_wait();
   pdl_launch();
   const StepCtl c = *ctl;
@@ -1870,13 +2037,34 @@ __global__ void adam_bf16_kernel(float* P, const float* Pin, const float* __rest
     V[e] = v;
     Pb[e] = __float2bfloat16_rn(p);
   }
+  if (!adv.on) return;
+  __shared__ int last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    const int err = *reinterpret_cast<volatile int*>(&ctl->err);
+    *ctl = advance_ctl(c, err, adv.sp, adv.K, adv.ring_slots, adv.b);
+  }
 }
-
 cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
                              const StepCtl* ctl, cudaStream_t st, const float* Pin) {
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
-  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, Pin ? Pin : P, G, M, V, Pb, n, ctl);
+  AdvanceArgs adv{};
+  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, Pin ? Pin : P, G, M, V, Pb, n,
+                  const_cast<StepCtl*>(ctl), adv);
+}
+cudaError_t launch_adam_bf16_advance(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
+                                     StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st) {
+  int grid = (int)((n + 255) / 256);
+  if (grid > 152 * 8) grid = 152 * 8;
+  AdvanceArgs adv{1, sp, K, ring_slots, b};
+  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, (const float*)P, G, M, V, Pb, n, ctl, adv);
 }
 
 __global__ void transpose_tiles_kernel(const __nv_bfloat16* __restrict__ Pb, __nv_bfloat16* __restrict__ PbT,

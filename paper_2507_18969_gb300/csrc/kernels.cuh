@@ -16,8 +16,10 @@ cudaError_t launch_init_values(float* dst, size_t n, uint64_t seed, int tid, flo
 // X[s][k*D + d] = E[ctx(s,k)][d]. With data != nullptr the context is gathered
 // from the stream bytes at the step's position and also written to ctx;
 // otherwise ctx (b x K) is read.
+// Grouped mode (rg != nullptr): row s reads the table of its group, E + rg[s] * gs.
 cudaError_t launch_embed(const uint8_t* data, Split sp, const StepCtl* ctl, const float* E, int b,
-                         int K, int D, float* X, uint8_t* ctx, cudaStream_t st);
+                         int K, int D, float* X, uint8_t* ctx, cudaStream_t st, const int* rg = nullptr,
+                         size_t gs = 0);
 // Row-wise LayerNorm: xhat, rstd, X0 = g * xhat + beta.
 cudaError_t launch_ln_fwd(const float* X, const float* g, const float* be, float* xhat, float* rstd,
                           float* X0, int b, int F, cudaStream_t st);
@@ -60,6 +62,10 @@ struct HeadArgs {
   __nv_bfloat16* dzbT;       // optional 256 x ldT transposed BF16 copy of dz
   int ldT;
   int* err;
+  // grouped mode: row s belongs to group rg[s]; its CE gradient is divided by
+  // the count of that group's active streams (group_active(gi[rg[s]], i))
+  const int* rg = nullptr;
+  const GroupInfo* gi = nullptr;
 };
 cudaError_t launch_head(const HeadArgs& a, cudaStream_t st);
 
@@ -141,6 +147,12 @@ constexpr int kEmbChunkPos = 16384;
 int embed_bwd_chunks(int b, int K);
 cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, float* part,
                              unsigned* cnt, cudaStream_t st);
+// Grouped mode: dE of group g (at dE + g * gs) sums the positions of its rows
+// [gi[g].r0, gi[g].r1) only; one CTA per byte value and group, each group's
+// positions in one chunk (at most kEmbChunkPos of them).
+cudaError_t launch_embed_bwd_groups(const uint8_t* ctx, const float* dX, int K, int D, float* dE,
+                                    const GroupInfo* gi, int ngroups, size_t gs, cudaStream_t st);
+
 // Adam over the flat shared parameters; bf16 != nullptr also refreshes the BF16 copy.
 // Pin: the parameters read (nullptr: P itself, an in-place update).
 cudaError_t launch_adam(float* P, const float* G, float* M, float* V, size_t n, const StepCtl* ctl,
@@ -188,12 +200,21 @@ cudaError_t launch_gemm_f32(const GemmF32& g, cudaStream_t st);
 // multiple of 16; padding rows are written as zero) goes out in 32-byte runs.
 constexpr int kRowsT = 16;
 // LayerNorm forward writing xhat, rstd and the BF16 copies of X0 (row-major and transposed).
+// Grouped mode (rg != nullptr): row r uses g + rg[r] * gs and be + rg[r] * gs.
 cudaError_t launch_ln_fwd_bf16(const float* X, const float* g, const float* be, float* xhat, float* rstd,
-                               __nv_bfloat16* X0b, __nv_bfloat16* X0bT, int b, int F, int ldT, cudaStream_t st);
+                               __nv_bfloat16* X0b, __nv_bfloat16* X0bT, int b, int F, int ldT, cudaStream_t st,
+                               const int* rg = nullptr, size_t gs = 0);
+// Embedding and the first block's LayerNorm forward in one launch (F = K * D
+// in {128, 256, 512, 1024}; otherwise cudaErrorInvalidValue): X and ctx as
+// launch_embed, xhat, rstd, X0b, X0bT as launch_ln_fwd_bf16, same arithmetic.
+cudaError_t launch_embed_ln_bf16(const uint8_t* data, Split sp, const StepCtl* ctl, const float* E, int b, int K,
+                                 int D, float* X, uint8_t* ctx, const float* g, const float* be, float* xhat,
+                                 float* rstd, __nv_bfloat16* X0b, __nv_bfloat16* X0bT, int ldT, cudaStream_t st,
+                                 const int* rg = nullptr, size_t gs = 0);
 // LayerNorm backward: dX = dRes + LN adjoint; also the BF16 copies of dX when non-null.
 cudaError_t launch_ln_bwd_bf16(const float* dX0, const float* xhat, const float* rstd, const float* g,
                                const float* dRes, float* dX, __nv_bfloat16* dXb, __nv_bfloat16* dXbT, int b, int F,
-                               int ldT, cudaStream_t st);
+                               int ldT, cudaStream_t st, const int* rg = nullptr, size_t gs = 0);
 // Batched deterministic column sums: one launch for up to kMaxColsumJobs tensors.
 constexpr int kMaxColsumJobs = 8;
 struct ColsumJob {
@@ -225,9 +246,18 @@ int colsum_tiles(const ColsumJobs& jobs);
 int colsum_chunk_rows(int rows, int tiles);
 constexpr int kColsumMaxChunks = 64;
 cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st);
+// Grouped column sums: for each job and group g, out[g * gs + c] = sum over
+// the group's rows r in [gi[g].r0, gi[g].r1) of X[r][c] (* Y[r][c]), rows in
+// increasing order (chunk fields of jobs unused).
+cudaError_t launch_colsum_groups(const ColsumJobs& jobs, const GroupInfo* gi, int ngroups, size_t gs,
+                                 cudaStream_t st);
 // Adam that also writes the BF16 copy Pb of every updated parameter (same flat layout).
 cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
                              const StepCtl* ctl, cudaStream_t st, const float* Pin = nullptr);
+// The same (in place) and then, in the launch's last CTA, the next step's
+// control record (what launch_step_advance writes), one launch fewer per step.
+cudaError_t launch_adam_bf16_advance(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
+                                     StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st);
 // Transposed BF16 copies of several matrices in one launch: PbT[off + c*rows + r] = Pb[off + r*cols + c].
 struct TransposeTile {
   unsigned long long off;
