@@ -418,7 +418,16 @@ int Model::init(const edpc_cfg& cfg, int streams, const std::vector<GroupInfo>* 
     EDPC_CUDA(cudaMemcpyAsync(gkr, gk_h.data(), sizeof(int4) * ngroups, cudaMemcpyHostToDevice, st));
     EDPC_CUDA(cudaStreamSynchronize(st));  // the host tables above are locals
   }
-  EDPC_CUDA(launch_init_values(U, fdm, seed, kFdmTid, (float)std::sqrt(3.0 / Fp), 0, 0.f, st));
+  if (ngroups) {
+    // each group's FDMs start as its file's would alone: row j of the group
+    // takes the values of stream j (the counter restarts at the group's first row)
+    const size_t per = (size_t)d.Fp * d.Fp;
+    for (const GroupInfo& g : groups_h)
+      EDPC_CUDA(launch_init_values(U + (size_t)g.r0 * per, (size_t)(g.r1 - g.r0) * per, seed, kFdmTid,
+                                   (float)std::sqrt(3.0 / Fp), 0, 0.f, st));
+  } else {
+    EDPC_CUDA(launch_init_values(U, fdm, seed, kFdmTid, (float)std::sqrt(3.0 / Fp), 0, 0.f, st));
+  }
   // Stream priorities (the default is the least): with the delayed update the
   // adjoint's streams go first and the FDM update last.
   int prio_least = 0, prio_greatest = 0;
