@@ -13,6 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libedpc.so")
 
 EDPC_ABI_VERSION = 1
+EDPC_FORMAT_VERSION = 1  # container format (include/edpc.h)
 EDPC_FP32 = 0
 EDPC_BF16 = 1
 EDPC_FP8E4M3 = 2

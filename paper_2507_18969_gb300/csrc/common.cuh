@@ -59,8 +59,7 @@ struct StepCtl {
   float lr;
   int err;        // sticky error bits
   int cpi;        // next entry of the active-count table (uneven splits)
-  unsigned arrive;  // CTAs of the Adam launch that also advances the step, done so far (0 between steps)
-  int pad[5];
+  int pad[6];
 };
 
 // Change point of the active-stream count: from time index i on, bact

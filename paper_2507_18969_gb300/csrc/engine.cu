@@ -1484,12 +1484,6 @@ int Model::step(const StepIO& io, cudaStream_t st) {
   EDPC_TRY(forward(io, st));
   EDPC_TRY(head(io, st));
   EDPC_TRY(backward(io, st));
-  if (io.update && io.advance && precision != EDPC_FP32) {
-    // Adam with the step advance in its last CTA
-    NoPdl scope;  // follows the join of the side stream
-    EDPC_CUDA(launch_adam_bf16_advance(P, G, M, V, Pb, np_all, ctl, io.sp, d.K, io.ring_slots, d.b, st));
-    return EDPC_OK;
-  }
   if (io.update) EDPC_TRY(adam(st));
   if (io.advance) EDPC_CUDA(launch_step_advance(ctl, io.sp, d.K, io.ring_slots, d.b, st));
   return EDPC_OK;
@@ -1538,7 +1532,7 @@ int Model::launches_per_step() const {
     int n = 1 + 3 * d.n - (d.nloc > 0 ? 1 : 0) + 3 + 1 + 1;
     // backward: head dW/colsum/dX, per block 3 main + 3 side, LTE 3 + 2 side ... + embed
     n += 3 + 6 * d.n + 3 + 4 + 1;
-    return n + 2;  // adam (with the step advance), transpose
+    return n + 3;  // adam, transpose, advance
   }
   int n = 1 + 4 * d.n + 3 + 1 + 1;
   n += 3 + 10 * d.n + 3 + 1 + 3 + 1;

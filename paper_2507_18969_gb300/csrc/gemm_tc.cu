@@ -47,7 +47,9 @@ constexpr size_t smem_bytes() {
 
 // KB: branch count k (TC_BRANCH, TC_BRANCH_BWD; 1 otherwise). In TC_BRANCH mode
 // the N tile holds k sections of SW = BN / k hidden units each.
-template <int BN, int MODE, int KB, bool F8>
+// GR: grouped mode (the tile list, or each group's K range; see TcGemm). The
+// other instantiations carry none of its code.
+template <int BN, int MODE, int KB, bool F8, bool GR>
 __global__ void __launch_bounds__(128, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
                    const __grid_constant__ CUtensorMap tmc, const __grid_constant__ CUtensorMap tmcb, const TcEpi e) {
@@ -71,7 +73,7 @@ __global__ void __launch_bounds__(128, 1)
   // Rows [m0, mend) of the tile are stored; grouped mode reads the tile (and
   // its group) from the tile list, or the group's K range (weight gradients).
   int m0 = blockIdx.y * BM, mend = e.M, grp = 0;
-  if (e.mt) {
+  if (GR && e.mt) {
     const int4 t = e.mt[blockIdx.y];
     m0 = t.x;
     mend = t.y;
@@ -83,7 +85,7 @@ __global__ void __launch_bounds__(128, 1)
   // K blocks of this CTA: all of them, split z of gridDim.z (split-K), or the
   // group's own range (grouped weight gradients; k0 is a multiple of 64)
   int kel0 = 0, kb_lo = 0, nk = 0;
-  if (e.gk) {
+  if (GR && e.gk) {
     grp = blockIdx.z;
     const int4 t = e.gk[grp];
     kel0 = t.x;
@@ -123,7 +125,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
     for (int i = 0; i < SECTIONS; ++i) {
       const int brow = (MODE == TC_BRANCH ? i * e.H : 0) + n0;
-      if (e.mt)
+      if (GR && e.mt)
         tma_load_3d(sB + s * B_BYTES + i * (SW * BKB), &tb, kc, brow, grp, &full[s]);
       else
         tma_load_2d(sB + s * B_BYTES + i * (SW * BKB), &tb, kc, brow, &full[s]);
@@ -179,28 +181,11 @@ __global__ void __launch_bounds__(128, 1)
   const bool ok = __syncthreads_and(mbar_wait(done, 0, abort_flag) ? 1 : 0) != 0;
   tc_fence_after();
   // The pipeline's A stages are idle now: reuse them to stage the transposed
-  // stores (8 KB) and the TMA stores (6 KB per warp), and (LayerNorm-fused
-  // modes) the row sums the cluster's CTAs read (1 KB).
-  static_assert(STAGES * A_BYTES >= 8192 + kStageOut + ((MODE == TC_LN_FWD || MODE == TC_LN_BWD) ? 1024 : 0),
-                "A stages hold the epilogue staging");
-  if (MODE == TC_LN_FWD || MODE == TC_LN_BWD) {
-    // every CTA of the cluster runs the epilogue's cluster barriers, ok or not
+  // stores (8 KB) and the TMA stores (6 KB per warp).
+  static_assert(STAGES * A_BYTES >= 8192 + kStageOut, "A stages hold the epilogue staging");
+  if (ok) {
     const EpiOut o{&tmc, &tmcb, sA + 8192 + warp * kStageOutWarp, m0 + warp * 32, lane};
-    float* red = reinterpret_cast<float*>(sA + 8192 + kStageOut);
-    TcEpi eg = e;
-    if (e.mt) {
-      eg.M = mend;
-      eg.rlim = mend;
-      if (e.bias) eg.bias = e.bias + (long long)grp * e.gs;
-      eg.ln.g = e.ln.g + (long long)grp * e.gs;
-      if (e.ln.b) eg.ln.b = e.ln.b + (long long)grp * e.gs;
-    }
-    tc_epilogue_ln<BN, MODE, F8>(eg, tmem + ((uint32_t)(warp * 32) << 16), m0, n0,
-                                 reinterpret_cast<__nv_bfloat16*>(sA), red, threadIdx.x, threadIdx.x, o, ok);
-    tma_st_drain(lane);
-  } else if (ok) {
-    const EpiOut o{&tmc, &tmcb, sA + 8192 + warp * kStageOutWarp, m0 + warp * 32, lane};
-    if (e.mt || e.gk) {
+    if constexpr (GR) {
       // grouped mode: the tile's row bound, its group's bias or gradient output
       TcEpi eg = e;
       eg.M = mend;
@@ -234,9 +219,9 @@ __global__ void __launch_bounds__(128, 1)
   }
 }
 
-template <int BN, int MODE, int KB = 1, bool F8 = false>
-cudaError_t launch_bn_mode(const TcGemm& g, cudaStream_t st) {
-  auto k = gemm_tc_kernel<BN, MODE, KB, F8>;
+template <int BN, int MODE, int KB, bool F8, bool GR>
+cudaError_t launch_bn_mode_g(const TcGemm& g, cudaStream_t st) {
+  auto k = gemm_tc_kernel<BN, MODE, KB, F8, GR>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [&] {
@@ -247,18 +232,18 @@ cudaError_t launch_bn_mode(const TcGemm& g, cudaStream_t st) {
   if (attr_err != cudaSuccess) return attr_err;
   TcEpi e{g.M, g.N, g.K, g.H, g.k, g.C, g.ldc, g.Cb, g.ldcb, g.CbT, g.ldct, g.bias, g.R, g.ldr, g.Aux, g.ldaux, g.err,
           g.inv_a, g.inv_b, g.b_early ? 1 : 0, g.ws, g.cnt, 0, 0, g.has_tmc ? 1 : 0, g.has_tmcb ? 1 : 0,
-          g.mt, g.gk, (long long)g.gs, INT_MAX, g.ln};
+          g.mt, g.gk, (long long)g.gs, INT_MAX};
   constexpr int SW = (MODE == TC_BRANCH) ? BN / KB : BN;
   const int ntile = (MODE == TC_BRANCH) ? (g.H + SW - 1) / SW : (g.N + BN - 1) / BN;
   dim3 grid(ntile, g.mt ? g.nmt : (g.M + BM - 1) / BM, g.gk ? g.ngk : (g.splitk > 1 ? g.splitk : 1));
-  if (MODE == TC_LN_FWD || MODE == TC_LN_BWD) {
-    // one cluster per row tile: the N tiles of a row (at most 8, the portable cluster size)
-    if (g.N % BN || ntile > 8 || g.splitk > 1 || g.gk || !g.ln.g || !g.ln.xhat || !g.ln.rstd ||
-        (MODE == TC_LN_FWD && (!g.ln.b || !g.ln.yb || !g.ln.ybT)) || (MODE == TC_LN_BWD && (!g.ln.res || !g.ln.y)))
-      return cudaErrorInvalidValue;
-    return launch_kc(k, grid, dim3(128), smem_bytes<BN>(), (unsigned)ntile, st, g.ta, g.tb, g.tmc, g.tmcb, e);
-  }
   return launch_k(k, grid, dim3(128), smem_bytes<BN>(), st, g.ta, g.tb, g.tmc, g.tmcb, e);
+}
+
+// Grouped launches (BF16 only) use the GR instantiation.
+template <int BN, int MODE, int KB = 1, bool F8 = false>
+cudaError_t launch_bn_mode(const TcGemm& g, cudaStream_t st) {
+  if (g.mt || g.gk) return F8 ? cudaErrorInvalidValue : launch_bn_mode_g<BN, MODE, KB, false, true>(g, st);
+  return launch_bn_mode_g<BN, MODE, KB, F8, false>(g, st);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
@@ -397,7 +382,6 @@ cudaError_t launch_gemm_tc_t(const TcGemm& g, cudaStream_t st) {
         (g.gk && (g.ngk < 1 || g.ngk > 65535)) || (g.gk && (g.has_tmc || g.has_tmcb)))
       return cudaErrorInvalidValue;
   }
-  if (g.persistent && (g.mode == TC_LN_FWD || g.mode == TC_LN_BWD)) return cudaErrorInvalidValue;
   if (g.persistent) return launch_gemm_tcp(g, st);  // checks the tile against the box itself
   if (g.mode == TC_BRANCH) {
     // box_b = section width; bn = k sections
@@ -426,17 +410,6 @@ cudaError_t launch_gemm_tc_t(const TcGemm& g, cudaStream_t st) {
       case 1128: return launch_bn_mode<128, TC_BRANCH_BWD, 1, F8>(g, st);
       case 2128: return launch_bn_mode<128, TC_BRANCH_BWD, 2, F8>(g, st);
       case 3128: return launch_bn_mode<128, TC_BRANCH_BWD, 3, F8>(g, st);
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  if (g.mode == TC_LN_FWD || g.mode == TC_LN_BWD) {
-    if (g.persistent) return cudaErrorInvalidValue;
-    const bool fw = g.mode == TC_LN_FWD;
-    switch (g.bn) {
-      case 32: return fw ? launch_bn_mode<32, TC_LN_FWD, 1, F8>(g, st) : launch_bn_mode<32, TC_LN_BWD, 1, F8>(g, st);
-      case 64: return fw ? launch_bn_mode<64, TC_LN_FWD, 1, F8>(g, st) : launch_bn_mode<64, TC_LN_BWD, 1, F8>(g, st);
-      case 128:
-        return fw ? launch_bn_mode<128, TC_LN_FWD, 1, F8>(g, st) : launch_bn_mode<128, TC_LN_BWD, 1, F8>(g, st);
       default: return cudaErrorInvalidValue;
     }
   }

@@ -18,32 +18,7 @@ namespace edpc {
 //   TC_BRANCH_BWD adjoint of Eqs. 11-12 on dG = acc: with X_i read from Aux
 //                ([m][i*H+h]), dX_i = dG * GELU'(prod X) * prod_{l!=i} X_l is
 //                stored to C (FP32), Cb (BF16) and CbT (BF16, [i*H+h][m]).
-//   TC_LN_FWD    v = acc + bias + R to C as TC_PLAIN, then the LayerNorm of
-//                Eq. 9 of every row v (all N columns): the CTAs of one row
-//                tile form a thread-block cluster along N and add their row
-//                sums (mean, then centred squares) through distributed shared
-//                memory in rank order; writes ln.xhat, ln.rstd and the BF16
-//                copies of ln.g * xhat + ln.b (ln.yb, ln.ybT).
-//   TC_LN_BWD    C = acc (the LN output's gradient dX0) as TC_PLAIN, then the
-//                LayerNorm adjoint with d = acc * ln.g: ln.y = ln.res +
-//                rstd (d - mean(d) - xhat mean(d xhat)) (FP32) and its BF16
-//                copies ln.yb / ln.ybT when set; the two means are cluster
-//                sums as in TC_LN_FWD.
-enum TcMode { TC_PLAIN = 0, TC_BRANCH = 1, TC_BRANCH_BWD = 2, TC_LN_FWD = 3, TC_LN_BWD = 4 };
-
-// LayerNorm fused into a GEMM epilogue (TC_LN_FWD / TC_LN_BWD); row vectors
-// are [M][N] with row stride N, ybT is [N][ldT].
-struct LnFuse {
-  const float* g = nullptr;   // gamma (N); grouped mode: + group * gs
-  const float* b = nullptr;   // beta (N; forward); grouped mode: + group * gs
-  float* xhat = nullptr;      // forward: written; backward: read
-  float* rstd = nullptr;      // forward: written; backward: read
-  const float* res = nullptr; // backward: the residual path's gradient (added)
-  float* y = nullptr;         // backward: the input gradient (FP32)
-  __nv_bfloat16* yb = nullptr;
-  __nv_bfloat16* ybT = nullptr;
-  int ldT = 0;
-};
+enum TcMode { TC_PLAIN = 0, TC_BRANCH = 1, TC_BRANCH_BWD = 2 };
 
 // C[m][n] = sum_k A[m][k] B[n][k] (+ epilogue); A is M x K and B is N x K,
 // both BF16 (or both FP8 e4m3 with power-of-two per-tensor scales) and
@@ -105,7 +80,6 @@ struct TcGemm {
   const int4* gk = nullptr;
   int ngk = 0;
   size_t gs = 0;
-  LnFuse ln;  // TC_LN_FWD / TC_LN_BWD
 };
 
 constexpr int kErrTcTimeout = 4;

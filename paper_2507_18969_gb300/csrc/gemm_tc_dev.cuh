@@ -43,7 +43,6 @@ struct TcEpi {
   const int4* gk;      // grouped mode: K ranges of the weight-gradient GEMMs
   long long gs;        // grouped mode: parameter stride between groups (floats)
   int rlim;            // rows at or beyond rlim are not written by the transposed stores
-  LnFuse ln;           // TC_LN_FWD / TC_LN_BWD
 };
 
 // Per-warp output staging for TMA stores: 4 KB FP32 rows (128-byte swizzle)
@@ -104,30 +103,6 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, in
           smem_u32(dst)),
       "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
-}
-
-// Thread-block cluster barrier (all threads of every CTA of the cluster);
-// release / acquire order the shared-memory writes before it.
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_size() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-  return r;
-}
-// The float at the same shared-memory offset as `local` in cluster CTA `rank`.
-__device__ __forceinline__ float ld_dsmem(const float* local, uint32_t rank) {
-  uint32_t ra;
-  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(local)), "r"(rank));
-  float v;
-  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
-  return v;
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -536,137 +511,6 @@ __device__ __forceinline__ void tc_epilogue(const TcEpi& e, uint32_t trow, int m
         out_chunk(e, o, dd, rok, row, colb, hb, e.H, e.C, e.ldc, e.Cb, e.ldcb);
         store_T32(dd, sT, m0, colb + hb, colb + e.H, e.CbT, e.ldct, r, et, e.rlim);
       }
-    }
-  }
-}
-
-// The LayerNorm-fused epilogues (TC_LN_FWD, TC_LN_BWD) of one 128 x BN tile,
-// run by the 128 epilogue threads of every CTA in the row tile's cluster
-// (gridDim.x CTAs along N, N = gridDim.x * BN). Every CTA executes the same
-// three cluster barriers whether or not its main loop completed (ok), so a
-// CTA that gave up on a wait never leaves its peers waiting; its values are
-// then meaningless and the launch has already recorded the error. red: 256
-// floats of shared memory for the row sums the peers read.
-template <int BN, int MODE, bool F8>
-__device__ __forceinline__ void tc_epilogue_ln(const TcEpi& e, uint32_t trow, int m0, int n0, __nv_bfloat16* sT,
-                                               float* red, int r, int et, const EpiOut& o, bool ok) {
-  const int row = m0 + r;
-  const bool rok = ok && row < e.M;
-  const float sc = F8 ? e.inv_a[0] * e.inv_b[0] : 1.f;
-  const uint32_t nr = cluster_size();
-  const float fN = (float)e.N;
-  auto load_v = [&](int c0, float (&v)[32]) {  // the GEMM's output chunk (TC_PLAIN arithmetic)
-    tmem_ld32(trow + (uint32_t)c0, v);
-    if (F8) {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] *= sc;
-    }
-    if (MODE == TC_LN_FWD) {
-      const int nb = n0 + c0;
-      if (e.bias) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] += e.bias[nb + j];
-      }
-      if (e.R && rok) {
-        float rr[32];
-        load_row32(e.R + (size_t)row * e.ldr, nb, e.N, rr);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) v[j] += rr[j];
-      }
-    }
-  };
-  auto row_sum = [&](const float* slot) {  // the cluster's CTAs in rank order
-    float t = 0.f;
-    for (uint32_t k = 0; k < nr; ++k) t += ld_dsmem(slot, k);
-    return t;
-  };
-  if (MODE == TC_LN_FWD) {
-    float s1 = 0.f;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      float v[32];
-      load_v(c0, v);
-      out_chunk(e, o, v, rok, row, 0, n0 + c0, e.N, e.C, e.ldc, nullptr, 0);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) s1 += v[j];
-    }
-    red[r] = s1;
-    cluster_sync();
-    const float mean = row_sum(&red[r]) / fN;
-    float s2 = 0.f;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      float v[32];
-      load_v(c0, v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float d = v[j] - mean;
-        s2 += d * d;
-      }
-    }
-    red[128 + r] = s2;
-    cluster_sync();
-    const float rs = 1.0f / sqrtf(row_sum(&red[128 + r]) / fN + kLnEps);
-    cluster_sync();  // every peer has read this CTA's sums
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      const int nb = n0 + c0;
-      float v[32], h[32];
-      load_v(c0, v);
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        h[j] = (v[j] - mean) * rs;
-        v[j] = h[j] * e.ln.g[nb + j] + e.ln.b[nb + j];
-      }
-      store_row32(h, rok, nb, e.N, e.ln.xhat + (size_t)row * e.N, nullptr);
-      store_row32(v, rok, nb, e.N, nullptr, e.ln.yb + (size_t)row * e.N);
-      store_T32(v, sT, m0, nb, e.N, e.ln.ybT, e.ln.ldT, r, et, e.rlim);
-    }
-    if (rok && cluster_rank() == 0) e.ln.rstd[row] = rs;
-  } else {
-    const float rs = rok ? e.ln.rstd[row] : 0.f;
-    float s1 = 0.f, s2 = 0.f;
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      const int nb = n0 + c0;
-      float v[32], xh[32];
-      load_v(c0, v);
-      out_chunk(e, o, v, rok, row, 0, nb, e.N, e.C, e.ldc, nullptr, 0);
-      if (rok) {
-        load_row32(e.ln.xhat + (size_t)row * e.N, nb, e.N, xh);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) xh[j] = 0.f;
-      }
-#pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const float d = v[j] * e.ln.g[nb + j];
-        s1 += d;
-        s2 += d * xh[j];
-      }
-    }
-    red[r] = s1;
-    red[128 + r] = s2;
-    cluster_sync();
-    const float m1 = row_sum(&red[r]) / fN;
-    const float m2 = row_sum(&red[128 + r]) / fN;
-    cluster_sync();  // every peer has read this CTA's sums
-#pragma unroll 1
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      const int nb = n0 + c0;
-      float v[32], xh[32], rr[32];
-      load_v(c0, v);
-      if (rok) {
-        load_row32(e.ln.xhat + (size_t)row * e.N, nb, e.N, xh);
-        load_row32(e.ln.res + (size_t)row * e.N, nb, e.N, rr);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) xh[j] = rr[j] = 0.f;
-      }
-#pragma unroll
-      for (int j = 0; j < 32; ++j) v[j] = rr[j] + rs * (v[j] * e.ln.g[nb + j] - m1 - xh[j] * m2);
-      store_row32(v, rok, nb, e.N, e.ln.y + (size_t)row * e.N, e.ln.yb ? e.ln.yb + (size_t)row * e.N : nullptr);
-      if (e.ln.ybT) store_T32(v, sT, m0, nb, e.N, e.ln.ybT, e.ln.ldT, r, et, e.rlim);
     }
   }
 }

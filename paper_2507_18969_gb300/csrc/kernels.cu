@@ -1103,7 +1103,6 @@ __device__ __forceinline__ StepCtl advance_ctl(StepCtl c, int dst_err, Split sp,
   c.bc1 = 1.0f - powf(kB1, (float)c.t);
   c.bc2 = 1.0f - powf(kB2, (float)c.t);
   c.slot = (int)((i - K) % ring_slots);
-  c.arrive = 0u;
   return c;
 }
 
@@ -2013,18 +2012,9 @@ cudaError_t launch_colsum_groups(const ColsumJobs& jobs, const GroupInfo* gi, in
 // Adam with the BF16 weight copy refreshed in the same pass; transposed copies
 // of every weight matrix in one launch (32 x 32 tiles through shared memory).
 // ============================================================================================
-// With adv set, the last CTA to finish (counted on ctl->arrive after a fence,
-// so every CTA has read the step's scalars and written its parameters) also
-// writes the next step's control record, as step_advance_kernel does.
-struct AdvanceArgs {
-  int on;
-  Split sp;
-  int K, ring_slots, b;
-};
-
 __global__ void adam_bf16_kernel(float* P, const float* Pin, const float* __restrict__ G, float* __restrict__ M,
-                                 float* __restrict__ V, __nv_bfloat16* __restrict__ Pb, size_t n, StepCtl* ctl,
-                                 AdvanceArgs adv) {
+                                 float* __restrict__ V, __nv_bfloat16* __restrict__ Pb, size_t n,
+                                 const StepCtl* __restrict__ ctl) {
   pdl_wait();
   pdl_launch();
   const StepCtl c = *ctl;
@@ -2037,34 +2027,12 @@ __global__ void adam_bf16_kernel(float* P, const float* Pin, const float* __rest
     V[e] = v;
     Pb[e] = __float2bfloat16_rn(p);
   }
-  if (!adv.on) return;
-  __shared__ int last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    last = atomicAdd(&ctl->arrive, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (last && threadIdx.x == 0) {
-    __threadfence();
-    const int err = *reinterpret_cast<volatile int*>(&ctl->err);
-    *ctl = advance_ctl(c, err, adv.sp, adv.K, adv.ring_slots, adv.b);
-  }
 }
 cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
                              const StepCtl* ctl, cudaStream_t st, const float* Pin) {
   int grid = (int)((n + 255) / 256);
   if (grid > 152 * 8) grid = 152 * 8;
-  AdvanceArgs adv{};
-  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, Pin ? Pin : P, G, M, V, Pb, n,
-                  const_cast<StepCtl*>(ctl), adv);
-}
-cudaError_t launch_adam_bf16_advance(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
-                                     StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st) {
-  int grid = (int)((n + 255) / 256);
-  if (grid > 152 * 8) grid = 152 * 8;
-  AdvanceArgs adv{1, sp, K, ring_slots, b};
-  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, (const float*)P, G, M, V, Pb, n, ctl, adv);
+  return launch_k(adam_bf16_kernel, dim3(grid), dim3(256), 0, st, P, Pin ? Pin : P, G, M, V, Pb, n, ctl);
 }
 
 __global__ void transpose_tiles_kernel(const __nv_bfloat16* __restrict__ Pb, __nv_bfloat16* __restrict__ PbT,

@@ -254,10 +254,6 @@ cudaError_t launch_colsum_groups(const ColsumJobs& jobs, const GroupInfo* gi, in
 // Adam that also writes the BF16 copy Pb of every updated parameter (same flat layout).
 cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
                              const StepCtl* ctl, cudaStream_t st, const float* Pin = nullptr);
-// The same (in place) and then, in the launch's last CTA, the next step's
-// control record (what launch_step_advance writes), one launch fewer per step.
-cudaError_t launch_adam_bf16_advance(float* P, const float* G, float* M, float* V, __nv_bfloat16* Pb, size_t n,
-                                     StepCtl* ctl, Split sp, int K, int ring_slots, int b, cudaStream_t st);
 // Transposed BF16 copies of several matrices in one launch: PbT[off + c*rows + r] = Pb[off + r*cols + c].
 struct TransposeTile {
   unsigned long long off;

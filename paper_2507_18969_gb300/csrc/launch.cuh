@@ -44,28 +44,4 @@ inline cudaError_t launch_k(void (*k)(KArgs...), dim3 grid, dim3 block, size_t s
   return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
 }
 
-// The same with thread-block clusters of `cluster` CTAs along x (gridDim.x a
-// multiple of it). No kernel of this library loads across a cluster (no TMA
-// multicast); clusters only exchange row sums through distributed shared
-// memory.
-template <typename... KArgs, typename... Args>
-inline cudaError_t launch_kc(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, unsigned cluster,
-                             cudaStream_t st, Args&&... args) {
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = grid;
-  cfg.blockDim = block;
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = st;
-  cudaLaunchAttribute at[2];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = cluster;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at[1].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = g_pdl_enabled ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
-}
-
 }  // namespace edpc

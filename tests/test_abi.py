@@ -107,12 +107,18 @@ def test_file_set_plan_rejects_too_many_streams(lib):
         pkg.archive_plan([10, 20], pkg.make_cfg(streams=70000))
 
 
-def _indep(nfiles, members, L=65536, crc_ok=True, magic=0x49504445):
+def _fmt():
+    from paper_2507_18969_gb300 import _lib
+    return _lib.EDPC_FORMAT_VERSION
+
+
+def _indep(nfiles, members, L=65536, crc_ok=True, magic=0x49504445, version=None):
     """An archive of independent models built by hand (table + members)."""
     import struct
     import zlib
+    version = _fmt() if version is None else version
     hl = 24 + 24 * nfiles + 4
-    head = struct.pack("<IIQQ", magic, 1, nfiles, L)
+    head = struct.pack("<IIQQ", magic, version, nfiles, L)
     o = hl
     for m, size in members:
         head += struct.pack("<QQQ", o, len(m), size)
@@ -127,6 +133,9 @@ def test_independent_archive_table_is_checked(lib):
     bad magic, a bad CRC, a truncated table and members out of range."""
     import paper_2507_18969_gb300 as edpc
     assert edpc.independent_info(_indep(0, [])) == []
+    with pytest.raises(edpc.EdpcError) as ev:  # a container of a format version this library lacks
+        edpc.independent_info(_indep(0, [], version=_fmt() + 1))
+    assert ev.value.code == 4  # EDPC_EVERSION
     assert edpc.independent_info(_indep(2, [(b"ab", 7), (b"", 0)])) == [7, 0]
     for bad in (_indep(0, [], magic=0x12345678), _indep(1, [(b"xy", 3)], crc_ok=False),
                 _indep(2, [(b"ab", 7), (b"", 0)])[:40]):
@@ -136,7 +145,7 @@ def test_independent_archive_table_is_checked(lib):
     # a member that runs past the end of the archive
     import struct
     import zlib
-    head = struct.pack("<IIQQ", 0x49504445, 1, 1, 4096) + struct.pack("<QQQ", 52, 1000, 5)
+    head = struct.pack("<IIQQ", 0x49504445, _fmt(), 1, 4096) + struct.pack("<QQQ", 52, 1000, 5)
     head += struct.pack("<I", zlib.crc32(head) & 0xFFFFFFFF)
     with pytest.raises(edpc.EdpcError):
         edpc.independent_info(head + b"short")
@@ -149,7 +158,7 @@ def _header(sched, precision=1, n=100):
     # variant-0 container of one empty stream: fixed header, one length word, CRC
     b = 1
     hl = 88 + 4 * b + 4
-    h = struct.pack("<IIIIIIIIIIf", 0x43504445, 1, hl, precision, 16, 16, 128, 128, 2, 2, 1e-3)
+    h = struct.pack("<IIIIIIIIIIf", 0x43504445, _fmt(), hl, precision, 16, 16, 128, 128, 2, 2, 1e-3)
     h += struct.pack("<IQQIIQII", sched, 1, n, 1, b, 0, 0, 0)
     h += struct.pack("<I", 0)
     assert len(h) == hl - 4
