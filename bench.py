@@ -44,6 +44,10 @@ under profiles/ are taken with these):
       Every tcgen05 GEMM site of CASE's model with every tile code set to CODE
       (0: the size heuristic), each launched alone (Model.time_gemms): ms,
       GFLOP and TFLOP/s per site.
+  python bench.py case indep [NFILES [MB]]
+      NFILES files of MB megabytes of the multimedia mix as an archive of
+      independent per-file models (one batch: the grouped GEMMs), 64 KiB
+      streams, the 64 MiB workload's model; prints seconds and MB/s.
   python bench.py case ifr [STEPS]
       Sec. 3.1.1's Information Flow Refinement on the 64 MiB mix: models with
       1, 2 and 3 MBRB branches (c1's dims) each take STEPS online steps on the
@@ -180,7 +184,27 @@ def case_ifr(steps: int = 256) -> dict:
     return res
 
 
+def case_indep(nfiles: int = 8, mb: float = 1.0) -> dict:
+    """Independent per-file models of nfiles files of `mb` MB (the multimedia
+    mix, 64 KiB streams, the 64 MiB workload's model) compressed as one batch."""
+    import paper_2507_18969_gb300 as edpc
+    import synth
+    n = int(mb * 1e6)
+    x = synth.multimedia_mix(nfiles * n, 20250719)
+    files = [x[i * n:(i + 1) * n] for i in range(nfiles)]
+    c = CASES["c1"]
+    t0 = time.perf_counter()
+    bits = edpc.compress_independent(files, case_cfg(c, edpc), stream_len=65536)
+    t = time.perf_counter() - t0
+    return dict(case="indep", files=nfiles, bytes=nfiles * n, seconds=t, mbs=nfiles * n / t / 1e6,
+                bits_per_byte=8 * len(bits) / (nfiles * n))
+
+
 def run_case(argv) -> int:
+    if argv and argv[0] == "indep":
+        print(json.dumps(case_indep(int(argv[1]) if len(argv) > 1 else 8, float(argv[2]) if len(argv) > 2 else 1.0)),
+              flush=True)
+        return 0
     if argv and argv[0] == "ifr":
         print(json.dumps(case_ifr(int(argv[1]) if len(argv) > 1 else 256)), flush=True)
         return 0
@@ -369,6 +393,34 @@ def traffic_from_profile(name: str):
         return float(re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt).group(1))
     except Exception:
         return None
+
+
+def sgemm_peak_tflops() -> float:
+    """Measured FP32 (SIMT, no TF32) GEMM throughput of this GPU: cuBLAS SGEMM
+    8192^3 through torch with TF32 off, best of 5 after 2 warm-ups (CUDA events).
+    The roofline denominator of the plain FP32 path's GEMMs."""
+    import torch
+    keep = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        n = 8192
+        a = torch.randn(n, n, device="cuda")
+        b = torch.randn(n, n, device="cuda")
+        for _ in range(2):
+            torch.matmul(a, b)
+        best = 1e30
+        for _ in range(5):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        del a, b
+        return 2.0 * n ** 3 / (best / 1e3) / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = keep
 
 
 def timed_session(sess, warmup_chunks, steps_chunks, stream, d: Dist, clocks=None, profile=False):
@@ -683,6 +735,19 @@ def run_ours(args, d: Dist):
                 "bound": "hbm (FDM forward, adjoint and Adam: 28 B x b x F'^2 per model step)",
                 "peaks": f"HBM {peak:.0f} GB/s, BF16 {tsus:.0f} TFLOP/s sustained (measured)"}
 
+    # ---- the plain FP32 path against its own bounds --------------------------------------------
+    fp32_roof = None
+    if fp32_value:
+        ms32 = t32 / done32 * 1e3
+        p32 = sgemm_peak_tflops()
+        gf = float(g_fl[used].sum())
+        fp32_roof = {"model_step_ms": ms32, "gemm_gflop_per_model_step": gf / 1e9,
+                     "sgemm_peak_tflops": p32, "gemm_floor_ms": gf / (p32 * 1e9),
+                     "frac_gemm": gf / (p32 * 1e9) / ms32,
+                     "hbm_floor_ms": 28.0 * fdm_elems / (peak * 1e6),
+                     "frac_serial": (gf / (p32 * 1e9) + 28.0 * fdm_elems / (peak * 1e6)) / ms32,
+                     "peak_source": "measured here: cuBLAS SGEMM 8192^3, TF32 off (the FP32 path's GEMMs are SIMT)"}
+
     # ---- CPU oracle baseline ------------------------------------------------------------------
     cpu = None
     if d.rank == 0 and d.world == 1 and not args.quick and not args.no_cpu_baseline:
@@ -730,7 +795,8 @@ def run_ours(args, d: Dist):
             "delayed_update": delayed,
             "bits_per_byte": bpb, "bits_per_byte_prefix": bpb_prefix, "lossless": lossless,
             "e2e": e2e, "gpu_launches": out["launches"],
-            "roofline": roof, "step_roofline": step, "gemm_roofline": gemm, "cpu_baseline": cpu,
+            "roofline": roof, "step_roofline": step, "gemm_roofline": gemm, "fp32_roofline": fp32_roof,
+            "cpu_baseline": cpu,
             "clocks": out["clocks"],
         }
         if sweep:

@@ -849,10 +849,17 @@ int Model::build_tc_sites() {
   // bitstream); else 32 while 64-wide tiles would leave the GPU mostly idle
   // (small b), else 64; the GEMMs over the streams (M = b) take 128-wide
   // tiles from 2048 streams on, where they were measured fastest.
-  const bool big = d.b >= 2048;
-  auto bn_heur = [&](int N) { return ((d.b + 127) / 128) * ((N + 63) / 64) < 2 * 152 ? 32 : 64; };
+  // Grouped mode: tile shapes that do not depend on the batch (a member's
+  // arithmetic must be the same alone and in any batch).
+  const bool big = !ngroups && d.b >= 2048;
+  auto bn_heur = [&](int N) { return ngroups ? 64 : (((d.b + 127) / 128) * ((N + 63) / 64) < 2 * 152 ? 32 : 64); };
   auto bn_site = [&](int id, int N) { return (tile_code[id] & 15) ? 32 * (tile_code[id] & 15) : bn_heur(N); };
   auto bn_rows = [&](int id, int N) { return (tile_code[id] & 15) || !big ? bn_site(id, N) : 128; };
+  // Weight gradients: in grouped mode every group contracts only its own rows
+  // (a few K blocks), so wide N tiles keep the CTA count (groups x tiles) and
+  // the per-CTA fixed cost down.
+  auto bn_dw = [&](int id, int N) { return ngroups ? (N >= 256 ? 256 : (N >= 128 ? 128 : (N >= 64 ? 64 : 32)))
+                                                   : bn_site(id, N); };
   // dW GEMMs (K = streams): split K when the output has too few tiles for the GPU
   auto split_site = [&](int id) -> int {
     TcGemm& g = tcp.site[id];
@@ -982,7 +989,7 @@ int Model::build_tc_sites() {
     }
     {  // dWo = dOut^T G
       int id = blk_site(OUT_DW, j);
-      int bn = bn_site(id, H);
+      int bn = bn_dw(id, H);
       EDPC_TRY(site(id, F, H, b, q.dOutbT, F, b, T, q.GbT, H, b, T, bn, bn));
       TcGemm& g = tcp.site[id];
       g.C = G + o.Wo;
@@ -999,7 +1006,7 @@ int Model::build_tc_sites() {
     }
     {  // dW = dA^T X0
       int id = blk_site(BR_DW, j);
-      int bn = bn_site(id, F);
+      int bn = bn_dw(id, F);
       EDPC_TRY(site(id, kH, F, b, q.dAbT, kH, b, T, q.X0bT, F, b, T, bn, bn));
       TcGemm& g = tcp.site[id];
       g.C = G + o.W;
@@ -1044,7 +1051,7 @@ int Model::build_tc_sites() {
     g.ldct = T;
   }
   {  // dWh = dz^T X
-    int bn = bn_site(kSiteHeadDw, F);
+    int bn = bn_dw(kSiteHeadDw, F);
     EDPC_TRY(site(kSiteHeadDw, 256, F, b, dzbT, 256, b, T, Shead_bT, F, b, T, bn, bn));
     TcGemm& g = tcp.site[kSiteHeadDw];
     g.C = G + po.Wh;
@@ -1059,7 +1066,7 @@ int Model::build_tc_sites() {
     g.ldc = Fp;
   }
   if (d.lte) {  // dW2 = dX^T Y
-    int bn = bn_site(kSiteLteUpDw, Fp);
+    int bn = bn_dw(kSiteLteUpDw, Fp);
     EDPC_TRY(site(kSiteLteUpDw, F, Fp, b, dLtebT, F, b, T, YbT, Fp, b, T, bn, bn));
     TcGemm& g = tcp.site[kSiteLteUpDw];
     g.C = G + po.W2;
@@ -1083,7 +1090,7 @@ int Model::build_tc_sites() {
     }
   }
   if (d.lte) {  // dW1 = dX'^T X
-    int bn = bn_site(kSiteLteDownDw, F);
+    int bn = bn_dw(kSiteLteDownDw, F);
     EDPC_TRY(site(kSiteLteDownDw, Fp, F, b, dXpbT, Fp, b, T, Slte_bT, F, b, T, bn, bn));
     TcGemm& g = tcp.site[kSiteLteDownDw];
     g.C = G + po.W1;
