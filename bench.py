@@ -44,10 +44,11 @@ under profiles/ are taken with these):
       Every tcgen05 GEMM site of CASE's model with every tile code set to CODE
       (0: the size heuristic), each launched alone (Model.time_gemms): ms,
       GFLOP and TFLOP/s per site.
-  python bench.py case indep [NFILES [MB]]
+  python bench.py case indep [NFILES [MB [STREAM_LEN]]]
       NFILES files of MB megabytes of the multimedia mix as an archive of
-      independent per-file models (one batch: the grouped GEMMs), 64 KiB
-      streams, the 64 MiB workload's model; prints seconds and MB/s.
+      independent per-file models (one batch: the grouped GEMMs), streams of
+      at most STREAM_LEN bytes (64 KiB), the 64 MiB workload's model; prints
+      compress and decompress MB/s (round trip checked).
   python bench.py case ifr [STEPS]
       Sec. 3.1.1's Information Flow Refinement on the 64 MiB mix: models with
       1, 2 and 3 MBRB branches (c1's dims) each take STEPS online steps on the
@@ -184,9 +185,9 @@ def case_ifr(steps: int = 256) -> dict:
     return res
 
 
-def case_indep(nfiles: int = 8, mb: float = 1.0) -> dict:
+def case_indep(nfiles: int = 8, mb: float = 1.0, stream_len: int = 65536) -> dict:
     """Independent per-file models of nfiles files of `mb` MB (the multimedia
-    mix, 64 KiB streams, the 64 MiB workload's model) compressed as one batch."""
+    mix, the 64 MiB workload's model) compressed as one batch, then decoded."""
     import paper_2507_18969_gb300 as edpc
     import synth
     n = int(mb * 1e6)
@@ -194,16 +195,21 @@ def case_indep(nfiles: int = 8, mb: float = 1.0) -> dict:
     files = [x[i * n:(i + 1) * n] for i in range(nfiles)]
     c = CASES["c1"]
     t0 = time.perf_counter()
-    bits = edpc.compress_independent(files, case_cfg(c, edpc), stream_len=65536)
+    bits = edpc.compress_independent(files, case_cfg(c, edpc), stream_len=stream_len)
     t = time.perf_counter() - t0
-    return dict(case="indep", files=nfiles, bytes=nfiles * n, seconds=t, mbs=nfiles * n / t / 1e6,
+    t0 = time.perf_counter()
+    back = edpc.decompress_independent(bits)
+    td = time.perf_counter() - t0
+    assert all(np.array_equal(a, b) for a, b in zip(files, back))
+    return dict(case="indep", files=nfiles, bytes=nfiles * n, stream_len=stream_len, seconds=t,
+                mbs=nfiles * n / t / 1e6, decompress_mbs=nfiles * n / td / 1e6,
                 bits_per_byte=8 * len(bits) / (nfiles * n))
 
 
 def run_case(argv) -> int:
     if argv and argv[0] == "indep":
-        print(json.dumps(case_indep(int(argv[1]) if len(argv) > 1 else 8, float(argv[2]) if len(argv) > 2 else 1.0)),
-              flush=True)
+        print(json.dumps(case_indep(int(argv[1]) if len(argv) > 1 else 8, float(argv[2]) if len(argv) > 2 else 1.0,
+                                    int(argv[3]) if len(argv) > 3 else 65536)), flush=True)
         return 0
     if argv and argv[0] == "ifr":
         print(json.dumps(case_ifr(int(argv[1]) if len(argv) > 1 else 256)), flush=True)
@@ -238,6 +244,8 @@ def parse():
                     help="e2e leg on the whole input (the default for mix64m; about 25 min per direction for mix1g; "
                          "files1000: all 1000 files instead of a sample)")
     ap.add_argument("--prefix-e2e", action="store_true", help="e2e leg on a prefix of each stream only")
+    ap.add_argument("--indep-stream-len", type=int, default=0,
+                    help="files1000 --independent: stream length of the independent archive (0: the autotuned one)")
     ap.add_argument("--ablation", action="store_true",
                     help="also compress and decode the whole workload with 3 MBRB branches and without the LTE")
     return ap.parse_args()
@@ -895,7 +903,8 @@ def run_files(args, d: Dist):
         icfg = cfg(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ibits = edpc.compress_independent(sample, icfg, stream_len=int(plan.stream_len), concurrency=16)
+        iL = args.indep_stream_len or int(plan.stream_len)
+        ibits = edpc.compress_independent(sample, icfg, stream_len=iL, concurrency=16)
         t_ic = time.perf_counter() - t0
         t0 = time.perf_counter()
         iback = edpc.decompress_independent(ibits, concurrency=16)
@@ -907,7 +916,7 @@ def run_files(args, d: Dist):
         t_one = time.perf_counter() - t0
         assert np.array_equal(one, sample[big])
         indep = {"compress_mbs": sb / t_ic / 1e6, "decompress_mbs": sb / t_id / 1e6, "bits_per_byte": 8 * len(ibits) / sb,
-                 "concurrency": 16, "stream_len": int(plan.stream_len),
+                 "concurrency": 16, "stream_len": iL,
                  "largest_member_alone": {"bytes": int(sample[big].size), "seconds": t_one},
                  "input": f"edpc_compress_independent of the same {len(sample)} files from host memory"}
 

@@ -930,23 +930,15 @@ cudaError_t launch_fdm_adam(const FdmSplitArgs& a, cudaStream_t st, bool persist
 __global__ void __launch_bounds__(256) embed_bwd_owner_kernel(const uint8_t* __restrict__ ctx,
                                                               const float* __restrict__ dX, int P, int D,
                                                               float* __restrict__ dE, float* __restrict__ part,
-                                                              unsigned* __restrict__ cnt,
-                                                              const GroupInfo* __restrict__ gi, int K, size_t gs) {
+                                                              unsigned* __restrict__ cnt) {
   pdl_wait();
   pdl_launch();
   __shared__ float wsum[8][64];
   __shared__ int is_last;
   const uint32_t c = blockIdx.x;
-  // grouped mode: blockIdx.y is the group, one chunk = its rows' positions
-  const int nq = gi ? 1 : gridDim.y, q = gi ? 0 : blockIdx.y;
+  const int nq = gridDim.y, q = blockIdx.y;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int c_lo = min(P, q * kEmbChunkPos), c_hi = min(P, c_lo + kEmbChunkPos);
-  if (gi) {
-    const GroupInfo g = gi[blockIdx.y];
-    c_lo = g.r0 * K;
-    c_hi = g.r1 * K;
-    dE += (size_t)blockIdx.y * gs;
-  }
+  const int c_lo = min(P, q * kEmbChunkPos), c_hi = min(P, c_lo + kEmbChunkPos);
   const int per = ((c_hi - c_lo + 8 * 128 - 1) / (8 * 128)) * 128;  // positions per warp, a multiple of 128
   const int p_lo = min(c_hi, c_lo + w * per), p_hi = min(c_hi, p_lo + per);
   const bool al4 = (reinterpret_cast<uintptr_t>(ctx) & 3) == 0;
@@ -1041,14 +1033,91 @@ cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, 
   const int nq = embed_bwd_chunks(b, K);
   if (nq > 1 && (!part || !cnt)) return cudaErrorInvalidValue;
   return launch_k(embed_bwd_owner_kernel, dim3(256, nq < 1 ? 1 : nq), dim3(256), 0, st, ctx, dX, b * K, D, dE, part,
-                  cnt, (const GroupInfo*)nullptr, K, (size_t)0);
+                  cnt);
+}
+
+// Grouped embedding adjoint: CTA (group g, block of 8 byte values); warp w
+// owns byte value 8 cb + w and walks the group's context positions in
+// increasing order, 512 at a time (four 32-bit words of 4 positions per
+// lane, loaded together), finds the value's positions by ballot and adds
+// their gradient rows (lane d: dimensions d and d + 32) in position order,
+// eight rows' loads in flight at a time. So each dE[g][c] is a sum in
+// increasing position order that depends on the group alone.
+__global__ void __launch_bounds__(256) embed_bwd_groups_kernel(const uint8_t* __restrict__ ctx,
+                                                               const float* __restrict__ dX, int K, int D,
+                                                               float* __restrict__ dE,
+                                                               const GroupInfo* __restrict__ gi, size_t gs) {
+  pdl_wait();
+  pdl_launch();
+  const GroupInfo g = gi[blockIdx.x];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t c = blockIdx.y * 8 + w;
+  // the group's streams only: its padding rows never hold a byte (their
+  // gradient is zero) and their all-zero contexts would all match byte 0
+  const int p_lo = g.r0 * K, p_hi = (g.r0 + g.s) * K;
+  float a0 = 0.f, a1 = 0.f;
+  int pend[8];
+  int np = 0;
+  auto flush = [&]() {
+    float v0[8], v1[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      v0[k] = (k < np && lane < D) ? dX[(size_t)pend[k] * D + lane] : 0.f;
+      v1[k] = (k < np && lane + 32 < D) ? dX[(size_t)pend[k] * D + lane + 32] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      if (k < np) {
+        a0 += v0[k];
+        a1 += v1[k];
+      }
+    }
+    np = 0;
+  };
+  for (int pb = p_lo; pb < p_hi; pb += 4 * 128) {
+    uint32_t xs[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      // positions pw..pw+3 (p_lo is a multiple of 4; bytes at or past p_hi never match)
+      const int pw = pb + k * 128 + 4 * lane;
+      uint32_t x = pw < p_hi ? *reinterpret_cast<const uint32_t*>(ctx + pw) : (c ^ 1u) * 0x01010101u;
+      for (int u = 0; u < 4; ++u)
+        if (pw + u >= p_hi) x = (x & ~(0xFFu << (8 * u))) | ((c ^ 1u) & 0xFFu) << (8 * u);
+      xs[k] = x;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int p0 = pb + k * 128;
+      uint32_t m[4], any = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        m[u] = __ballot_sync(0xffffffffu, ((xs[k] >> (8 * u)) & 0xffu) == c);
+        any |= m[u];
+      }
+      while (any) {  // warp-uniform: lanes in increasing order, then their bytes
+        const int l = __ffs(any) - 1;
+        any &= any - 1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if ((m[u] >> l) & 1u) {
+            pend[np++] = p0 + 4 * l + u;
+            if (np == 8) flush();
+          }
+        }
+      }
+    }
+  }
+  flush();
+  float* out = dE + (size_t)blockIdx.x * gs + (size_t)c * D;
+  if (lane < D) out[lane] = a0;
+  if (lane + 32 < D) out[lane + 32] = a1;
 }
 
 cudaError_t launch_embed_bwd_groups(const uint8_t* ctx, const float* dX, int K, int D, float* dE,
                                     const GroupInfo* gi, int ngroups, size_t gs, cudaStream_t st) {
-  if (D > 64 || ngroups < 1 || ngroups > 65535 || !gi) return cudaErrorInvalidValue;
-  return launch_k(embed_bwd_owner_kernel, dim3(256, ngroups), dim3(256), 0, st, ctx, dX, 0, D, dE, (float*)nullptr,
-                  (unsigned*)nullptr, gi, K, gs);
+  if (D > 64 || ngroups < 1 || ngroups > 65535 || !gi || (reinterpret_cast<uintptr_t>(ctx) & 3))
+    return cudaErrorInvalidValue;
+  return launch_k(embed_bwd_groups_kernel, dim3(ngroups, 32), dim3(256), 0, st, ctx, dX, K, D, dE, gi, gs);
 }
 
 // ============================================================================================
@@ -1979,7 +2048,7 @@ cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st) {
 // ============================================================================================
 // Grouped column sums (bias and LN-affine gradients of independent per-file
 // models): CTA = 128 columns of one job and one group; thread t sums column
-// c0 + t over the group's rows in increasing order.
+// c0 + t over the group's streams with four interleaved accumulators.
 // ============================================================================================
 __global__ void __launch_bounds__(128) colsum_groups_kernel(ColsumJobs jobs, const GroupInfo* __restrict__ gi,
                                                             size_t gs) {
@@ -1989,15 +2058,24 @@ __global__ void __launch_bounds__(128) colsum_groups_kernel(ColsumJobs jobs, con
   const GroupInfo g = gi[blockIdx.y];
   const int c = blockIdx.x * 128 + threadIdx.x;
   if (c >= j.cols) return;
-  float acc = 0.f;
-  const float* x = j.X + (size_t)g.r0 * j.ld + c;
-  if (j.Y) {
-    const float* y = j.Y + (size_t)g.r0 * j.ld + c;
-    for (int r = 0; r < g.r1 - g.r0; ++r) acc += x[(size_t)r * j.ld] * y[(size_t)r * j.ld];
-  } else {
-    for (int r = 0; r < g.r1 - g.r0; ++r) acc += x[(size_t)r * j.ld];
+  // the group's streams only (its padding rows hold zero gradients): four
+  // interleaved accumulators over rows r, r + 1, r + 2, r + 3, the last
+  // rows into the first, added as (a0 + a1) + (a2 + a3)
+  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+  const size_t ld = (size_t)j.ld;
+  const float* x = j.X + (size_t)g.r0 * ld + c;
+  const float* y = j.Y ? j.Y + (size_t)g.r0 * ld + c : nullptr;
+  const int nr = g.s, n4 = nr & ~3;
+  auto val = [&](int r) { return y ? x[r * ld] * y[r * ld] : x[r * ld]; };
+#pragma unroll 2
+  for (int r = 0; r < n4; r += 4) {
+    a0 += val(r);
+    a1 += val(r + 1);
+    a2 += val(r + 2);
+    a3 += val(r + 3);
   }
-  j.out[(size_t)blockIdx.y * gs + c] = acc;
+  for (int r = n4; r < nr; ++r) a0 += val(r);
+  j.out[(size_t)blockIdx.y * gs + c] = (a0 + a1) + (a2 + a3);
 }
 
 cudaError_t launch_colsum_groups(const ColsumJobs& jobs, const GroupInfo* gi, int ngroups, size_t gs,
@@ -2036,27 +2114,30 @@ cudaError_t launch_adam_bf16(float* P, const float* G, float* M, float* V, __nv_
 }
 
 __global__ void transpose_tiles_kernel(const __nv_bfloat16* __restrict__ Pb, __nv_bfloat16* __restrict__ PbT,
-                                       const TransposeTile* __restrict__ tiles) {
+                                       const TransposeTile* __restrict__ tiles, int ntiles) {
   pdl_wait();
   pdl_launch();
   __shared__ __nv_bfloat16 t[32][34];
-  const TransposeTile tl = tiles[blockIdx.x];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  for (int k = ty; k < 32; k += 8) {
-    int r = tl.r0 + k, cc = tl.c0 + tx;
-    t[k][tx] = (r < tl.rows && cc < tl.cols) ? Pb[tl.off + (size_t)r * tl.cols + cc] : __float2bfloat16_rn(0.f);
-  }
-  __syncthreads();
-  for (int k = ty; k < 32; k += 8) {
-    int cc = tl.c0 + k, r = tl.r0 + tx;
-    if (cc < tl.cols && r < tl.rows) PbT[tl.off + (size_t)cc * tl.rows + r] = t[tx][k];
+  for (int i = blockIdx.x; i < ntiles; i += gridDim.x) {  // several tiles per CTA when there are many
+    const TransposeTile tl = tiles[i];
+    if (i != (int)blockIdx.x) __syncthreads();  // the previous tile's reads of t are done
+    for (int k = ty; k < 32; k += 8) {
+      int r = tl.r0 + k, cc = tl.c0 + tx;
+      t[k][tx] = (r < tl.rows && cc < tl.cols) ? Pb[tl.off + (size_t)r * tl.cols + cc] : __float2bfloat16_rn(0.f);
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+      int cc = tl.c0 + k, r = tl.r0 + tx;
+      if (cc < tl.cols && r < tl.rows) PbT[tl.off + (size_t)cc * tl.rows + r] = t[tx][k];
+    }
   }
 }
-
 cudaError_t launch_transpose_tiles(const __nv_bfloat16* Pb, __nv_bfloat16* PbT, const TransposeTile* tiles,
                                    int ntiles, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-  return launch_k(transpose_tiles_kernel, dim3(ntiles), dim3(256), 0, st, Pb, PbT, tiles);
+  const int grid = ntiles < 152 * 16 ? ntiles : 152 * 16;
+  return launch_k(transpose_tiles_kernel, dim3(grid), dim3(256), 0, st, Pb, PbT, tiles, ntiles);
 }
 
 // ============================================================================================

@@ -147,9 +147,9 @@ constexpr int kEmbChunkPos = 16384;
 int embed_bwd_chunks(int b, int K);
 cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, float* part,
                              unsigned* cnt, cudaStream_t st);
-// Grouped mode: dE of group g (at dE + g * gs) sums the positions of its rows
-// [gi[g].r0, gi[g].r1) only; one CTA per byte value and group, each group's
-// positions in one chunk (at most kEmbChunkPos of them).
+// Grouped mode: dE of group g (at dE + g * gs) sums the positions of its
+// stream rows [gi[g].r0, gi[g].r0 + gi[g].s) only, in increasing position
+// order; CTAs per group and block of 8 byte values (ctx 4-byte aligned).
 cudaError_t launch_embed_bwd_groups(const uint8_t* ctx, const float* dX, int K, int D, float* dE,
                                     const GroupInfo* gi, int ngroups, size_t gs, cudaStream_t st);
 
@@ -247,8 +247,9 @@ int colsum_chunk_rows(int rows, int tiles);
 constexpr int kColsumMaxChunks = 64;
 cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st);
 // Grouped column sums: for each job and group g, out[g * gs + c] = sum over
-// the group's rows r in [gi[g].r0, gi[g].r1) of X[r][c] (* Y[r][c]), rows in
-// increasing order (chunk fields of jobs unused).
+// the group's stream rows r in [gi[g].r0, gi[g].r0 + gi[g].s) of X[r][c]
+// (* Y[r][c]) in a fixed order that depends on the group alone (its padding
+// rows hold zero gradients; chunk fields of jobs unused).
 cudaError_t launch_colsum_groups(const ColsumJobs& jobs, const GroupInfo* gi, int ngroups, size_t gs,
                                  cudaStream_t st);
 // Adam that also writes the BF16 copy Pb of every updated parameter (same flat layout).
