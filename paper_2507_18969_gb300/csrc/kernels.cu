@@ -388,8 +388,6 @@ __global__ void __launch_bounds__(FdmRing<FP>::NT)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  pdl_wait();
-  pdl_launch();
   // producer cursor (thread 0): next stream and stage to copy, copies issued
   int ps = blockIdx.x, pst = 0;
   uint32_t issued = 0;
@@ -408,10 +406,16 @@ __global__ void __launch_bounds__(FdmRing<FP>::NT)
       ps = next_active(ps + gridDim.x);
     }
   };
+  // The first copies go out before the dependent-launch wait: U and the step
+  // control were written by launches that completed before the preceding
+  // launch (whose own wait this one follows) could start; only x' comes from
+  // the preceding launch, and every thread reads it after the wait below.
   if (t == 0) {
     ps = next_active(ps);
     for (int q = 0; q < RING; ++q) issue_one();
   }
+  pdl_wait();
+  pdl_launch();
   uint32_t used = 0;  // copies consumed (same sequence as issued)
   bool ok = true;
   for (int s = blockIdx.x; s < b; s += gridDim.x) {
