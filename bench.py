@@ -34,12 +34,13 @@ seed); the value is the total bytes of all ranks over the slowest rank's time.
 Timing cases (named models on device-resident random bytes; the ncu profiles
 under profiles/ are taken with these):
 
-  python bench.py case steps CASE [CHUNKS [delayed]]
+  python bench.py case steps CASE [CHUNKS [delayed] [fp32]]
       An encoder session on CASE's model and stream count over random bytes
       already on the device (the kernels' work does not depend on the byte
       values): one warm-up chunk of 64 model steps, then CHUNKS timed chunks;
       prints milliseconds per model step (CUDA events). "delayed" selects the
-      delayed-update schedule (EDPC_FLAG_DELAYED_UPDATE).
+      delayed-update schedule (EDPC_FLAG_DELAYED_UPDATE), "fp32" the plain
+      FP32 (SIMT) path instead of BF16.
   python bench.py case gemm CASE CODE
       Every tcgen05 GEMM site of CASE's model with every tile code set to CODE
       (0: the size heuristic), each launched alone (Model.time_gemms): ms,
@@ -114,12 +115,13 @@ CASES = {
 }
 
 
-def case_cfg(c, edpc, **kw):
+def case_cfg(c, edpc, precision=None, **kw):
     return edpc.make_cfg(streams=c["b"], context=c["K"], embed_dim=16, latent=c["Fp"], hidden=c["H"], blocks=c["n"],
-                         branches=2, lr=1e-3, seed=1, precision=edpc.EDPC_BF16, **kw)
+                         branches=2, lr=1e-3, seed=1,
+                         precision=edpc.EDPC_BF16 if precision is None else precision, **kw)
 
 
-def case_steps(name: str, chunks: int = 2, delayed: bool = False) -> dict:
+def case_steps(name: str, chunks: int = 2, delayed: bool = False, fp32: bool = False) -> dict:
     import torch
     import paper_2507_18969_gb300 as edpc
     c = CASES[name]
@@ -127,7 +129,9 @@ def case_steps(name: str, chunks: int = 2, delayed: bool = False) -> dict:
     x = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda")
     st = torch.cuda.current_stream()
     flags = edpc.EDPC_FLAG_DELAYED_UPDATE if delayed else 0
-    enc = edpc.Encoder(case_cfg(c, edpc, flags=flags), device_ptr=x.data_ptr(), length=n, stream=st.cuda_stream)
+    prec = edpc.EDPC_FP32 if fp32 else edpc.EDPC_BF16
+    enc = edpc.Encoder(case_cfg(c, edpc, precision=prec, flags=flags), device_ptr=x.data_ptr(), length=n,
+                       stream=st.cuda_stream)
     enc.run(64)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -138,7 +142,8 @@ def case_steps(name: str, chunks: int = 2, delayed: bool = False) -> dict:
     torch.cuda.synchronize()
     enc.close()
     ms = e0.elapsed_time(e1) / done
-    return dict(case=name, streams=c["b"], delayed=delayed, ms_per_model_step=ms, mbs=c["b"] / ms / 1e3)
+    return dict(case=name, streams=c["b"], delayed=delayed, precision="fp32" if fp32 else "bf16",
+                ms_per_model_step=ms, mbs=c["b"] / ms / 1e3)
 
 
 def case_gemm(name: str, code: int) -> list[dict]:
@@ -218,8 +223,8 @@ def run_case(argv) -> int:
         print(__doc__)
         return 2
     if argv[0] == "steps":
-        print(json.dumps(case_steps(argv[1], int(argv[2]) if len(argv) > 2 else 2,
-                                    len(argv) > 3 and argv[3] == "delayed")), flush=True)
+        print(json.dumps(case_steps(argv[1], int(argv[2]) if len(argv) > 2 else 2, "delayed" in argv[3:],
+                                    "fp32" in argv[3:])), flush=True)
     else:
         for r in case_gemm(argv[1], int(argv[2]) if len(argv) > 2 else 0):
             print(json.dumps(r), flush=True)
