@@ -1040,25 +1040,29 @@ cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, 
                   cnt);
 }
 
-// Grouped embedding adjoint: CTA (group g, block of 8 byte values); warp w
-// owns byte value 8 cb + w and walks the group's context positions in
-// increasing order, 512 at a time (four 32-bit words of 4 positions per
-// lane, loaded together), finds the value's positions by ballot and adds
-// their gradient rows (lane d: dimensions d and d + 32) in position order,
-// eight rows' loads in flight at a time. So each dE[g][c] is a sum in
-// increasing position order that depends on the group alone.
+// Grouped embedding adjoint: CTA (group g, pair of byte values); warps 4v to
+// 4v + 3 own byte value 2 cb + v, each one quarter of the group's context
+// positions (in blocks of 512). A warp walks its quarter in increasing order,
+// 512 positions at a time (four 32-bit words of 4 positions per lane, loaded
+// together), finds the value's positions by ballot and adds their gradient
+// rows (lane d: dimensions d and d + 32) in position order, eight rows'
+// loads in flight at a time; the four quarter sums are then added in order.
+// So each dE[g][c] is a fixed-order sum that depends on the group alone.
 __global__ void __launch_bounds__(256) embed_bwd_groups_kernel(const uint8_t* __restrict__ ctx,
                                                                const float* __restrict__ dX, int K, int D,
                                                                float* __restrict__ dE,
                                                                const GroupInfo* __restrict__ gi, size_t gs) {
   pdl_wait();
   pdl_launch();
+  __shared__ float part[8][64];
   const GroupInfo g = gi[blockIdx.x];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t c = blockIdx.y * 8 + w;
+  const uint32_t c = blockIdx.y * 2 + (w >> 2);
   // the group's streams only: its padding rows never hold a byte (their
   // gradient is zero) and their all-zero contexts would all match byte 0
-  const int p_lo = g.r0 * K, p_hi = (g.r0 + g.s) * K;
+  const int g_lo = g.r0 * K, g_hi = (g.r0 + g.s) * K;
+  const int per = ((g_hi - g_lo + 4 * 512 - 1) / (4 * 512)) * 512;  // a quarter, whole 512-position blocks
+  const int p_lo = min(g_hi, g_lo + (w & 3) * per), p_hi = min(g_hi, p_lo + per);
   float a0 = 0.f, a1 = 0.f;
   int pend[8];
   int np = 0;
@@ -1112,16 +1116,22 @@ __global__ void __launch_bounds__(256) embed_bwd_groups_kernel(const uint8_t* __
     }
   }
   flush();
-  float* out = dE + (size_t)blockIdx.x * gs + (size_t)c * D;
-  if (lane < D) out[lane] = a0;
-  if (lane + 32 < D) out[lane + 32] = a1;
+  part[w][lane] = a0;
+  part[w][lane + 32] = a1;
+  __syncthreads();
+  if ((w & 3) == 0) {
+    float* out = dE + (size_t)blockIdx.x * gs + (size_t)c * D;
+    if (lane < D) out[lane] = ((part[w][lane] + part[w + 1][lane]) + part[w + 2][lane]) + part[w + 3][lane];
+    if (lane + 32 < D)
+      out[lane + 32] = ((part[w][lane + 32] + part[w + 1][lane + 32]) + part[w + 2][lane + 32]) + part[w + 3][lane + 32];
+  }
 }
 
 cudaError_t launch_embed_bwd_groups(const uint8_t* ctx, const float* dX, int K, int D, float* dE,
                                     const GroupInfo* gi, int ngroups, size_t gs, cudaStream_t st) {
   if (D > 64 || ngroups < 1 || ngroups > 65535 || !gi || (reinterpret_cast<uintptr_t>(ctx) & 3))
     return cudaErrorInvalidValue;
-  return launch_k(embed_bwd_groups_kernel, dim3(ngroups, 32), dim3(256), 0, st, ctx, dX, K, D, dE, gi, gs);
+  return launch_k(embed_bwd_groups_kernel, dim3(ngroups, 128), dim3(256), 0, st, ctx, dX, K, D, dE, gi, gs);
 }
 
 // ============================================================================================
@@ -2051,35 +2061,33 @@ cudaError_t launch_colsum_multi(const ColsumJobs& jobs, cudaStream_t st) {
 
 // ============================================================================================
 // Grouped column sums (bias and LN-affine gradients of independent per-file
-// models): CTA = 128 columns of one job and one group; thread t sums column
-// c0 + t over the group's streams with four interleaved accumulators.
+// models): CTA = 32 columns of one job and one group, 16 warps; warp w sums
+// the group's stream rows w, w + 16, ... for its lane's column, and the 16
+// warp sums are added in warp order.
 // ============================================================================================
-__global__ void __launch_bounds__(128) colsum_groups_kernel(ColsumJobs jobs, const GroupInfo* __restrict__ gi,
+__global__ void __launch_bounds__(512) colsum_groups_kernel(ColsumJobs jobs, const GroupInfo* __restrict__ gi,
                                                             size_t gs) {
   pdl_wait();
   pdl_launch();
+  __shared__ float part[16][33];
   const ColsumJob j = jobs.job[blockIdx.z];
   const GroupInfo g = gi[blockIdx.y];
-  const int c = blockIdx.x * 128 + threadIdx.x;
-  if (c >= j.cols) return;
-  // the group's streams only (its padding rows hold zero gradients): four
-  // interleaved accumulators over rows r, r + 1, r + 2, r + 3, the last
-  // rows into the first, added as (a0 + a1) + (a2 + a3)
-  float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-  const size_t ld = (size_t)j.ld;
-  const float* x = j.X + (size_t)g.r0 * ld + c;
-  const float* y = j.Y ? j.Y + (size_t)g.r0 * ld + c : nullptr;
-  const int nr = g.s, n4 = nr & ~3;
-  auto val = [&](int r) { return y ? x[r * ld] * y[r * ld] : x[r * ld]; };
-#pragma unroll 2
-  for (int r = 0; r < n4; r += 4) {
-    a0 += val(r);
-    a1 += val(r + 1);
-    a2 += val(r + 2);
-    a3 += val(r + 3);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int c = blockIdx.x * 32 + lane;
+  float a = 0.f;
+  if (c < j.cols) {
+    const size_t ld = (size_t)j.ld;
+    for (int r = g.r0 + w; r < g.r0 + g.s; r += 16)
+      a += j.Y ? j.X[r * ld + c] * j.Y[r * ld + c] : j.X[r * ld + c];
   }
-  for (int r = n4; r < nr; ++r) a0 += val(r);
-  j.out[(size_t)blockIdx.y * gs + c] = (a0 + a1) + (a2 + a3);
+  part[w][lane] = a;
+  __syncthreads();
+  if (w == 0 && c < j.cols) {
+    float t = part[0][lane];
+#pragma unroll
+    for (int q = 1; q < 16; ++q) t += part[q][lane];
+    j.out[(size_t)blockIdx.y * gs + c] = t;
+  }
 }
 
 cudaError_t launch_colsum_groups(const ColsumJobs& jobs, const GroupInfo* gi, int ngroups, size_t gs,
@@ -2087,7 +2095,7 @@ cudaError_t launch_colsum_groups(const ColsumJobs& jobs, const GroupInfo* gi, in
   if (jobs.n < 1 || jobs.n > kMaxColsumJobs || ngroups < 1 || ngroups > 65535 || !gi) return cudaErrorInvalidValue;
   int maxc = 0;
   for (int k = 0; k < jobs.n; ++k) maxc = max(maxc, jobs.job[k].cols);
-  return launch_k(colsum_groups_kernel, dim3(div_up(maxc, 128), ngroups, jobs.n), dim3(128), 0, st, jobs, gi, gs);
+  return launch_k(colsum_groups_kernel, dim3(div_up(maxc, 32), ngroups, jobs.n), dim3(512), 0, st, jobs, gi, gs);
 }
 
 // ============================================================================================

@@ -149,7 +149,7 @@ cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, 
                              unsigned* cnt, cudaStream_t st);
 // Grouped mode: dE of group g (at dE + g * gs) sums the positions of its
 // stream rows [gi[g].r0, gi[g].r0 + gi[g].s) only, in increasing position
-// order; CTAs per group and block of 8 byte values (ctx 4-byte aligned).
+// order; CTAs per group and pair of byte values (ctx 4-byte aligned).
 cudaError_t launch_embed_bwd_groups(const uint8_t* ctx, const float* dX, int K, int D, float* dE,
                                     const GroupInfo* gi, int ngroups, size_t gs, cudaStream_t st);
 
