@@ -34,13 +34,14 @@ seed); the value is the total bytes of all ranks over the slowest rank's time.
 Timing cases (named models on device-resident random bytes; the ncu profiles
 under profiles/ are taken with these):
 
-  python bench.py case steps CASE [CHUNKS [delayed] [fp32]]
+  python bench.py case steps CASE [CHUNKS [delayed] [fp32] [mix]]
       An encoder session on CASE's model and stream count over random bytes
-      already on the device (the kernels' work does not depend on the byte
+      already on the device (the kernels' launches do not depend on the byte
       values): one warm-up chunk of 64 model steps, then CHUNKS timed chunks;
       prints milliseconds per model step (CUDA events). "delayed" selects the
       delayed-update schedule (EDPC_FLAG_DELAYED_UPDATE), "fp32" the plain
-      FP32 (SIMT) path instead of BF16.
+      FP32 (SIMT) path instead of BF16, "mix" the multimedia mix (the
+      workloads' data) instead of uniform random bytes.
   python bench.py case gemm CASE CODE
       Every tcgen05 GEMM site of CASE's model with every tile code set to CODE
       (0: the size heuristic), each launched alone (Model.time_gemms): ms,
@@ -121,12 +122,16 @@ def case_cfg(c, edpc, precision=None, **kw):
                          precision=edpc.EDPC_BF16 if precision is None else precision, **kw)
 
 
-def case_steps(name: str, chunks: int = 2, delayed: bool = False, fp32: bool = False) -> dict:
+def case_steps(name: str, chunks: int = 2, delayed: bool = False, fp32: bool = False, mix: bool = False) -> dict:
     import torch
     import paper_2507_18969_gb300 as edpc
     c = CASES[name]
     n = c["b"] * (c["K"] + (chunks + 2) * 64 + 8)
-    x = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda")
+    if mix:
+        import synth
+        x = torch.from_numpy(synth.multimedia_mix(n, 20250719)).cuda()
+    else:
+        x = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda")
     st = torch.cuda.current_stream()
     flags = edpc.EDPC_FLAG_DELAYED_UPDATE if delayed else 0
     prec = edpc.EDPC_FP32 if fp32 else edpc.EDPC_BF16
@@ -143,7 +148,7 @@ def case_steps(name: str, chunks: int = 2, delayed: bool = False, fp32: bool = F
     enc.close()
     ms = e0.elapsed_time(e1) / done
     return dict(case=name, streams=c["b"], delayed=delayed, precision="fp32" if fp32 else "bf16",
-                ms_per_model_step=ms, mbs=c["b"] / ms / 1e3)
+                data="multimedia mix" if mix else "uniform random", ms_per_model_step=ms, mbs=c["b"] / ms / 1e3)
 
 
 def case_gemm(name: str, code: int) -> list[dict]:
@@ -224,7 +229,7 @@ def run_case(argv) -> int:
         return 2
     if argv[0] == "steps":
         print(json.dumps(case_steps(argv[1], int(argv[2]) if len(argv) > 2 else 2, "delayed" in argv[3:],
-                                    "fp32" in argv[3:])), flush=True)
+                                    "fp32" in argv[3:], "mix" in argv[3:])), flush=True)
     else:
         for r in case_gemm(argv[1], int(argv[2]) if len(argv) > 2 else 0):
             print(json.dumps(r), flush=True)
