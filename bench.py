@@ -132,7 +132,8 @@ def case_steps(name: str, chunks: int = 2, delayed: bool = False, fp32: bool = F
         x = torch.from_numpy(synth.multimedia_mix(n, 20250719)).cuda()
     else:
         x = torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda")
-    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    st = work_stream()
     flags = edpc.EDPC_FLAG_DELAYED_UPDATE if delayed else 0
     prec = edpc.EDPC_FP32 if fp32 else edpc.EDPC_BF16
     enc = edpc.Encoder(case_cfg(c, edpc, precision=prec, flags=flags), device_ptr=x.data_ptr(), length=n,
@@ -441,8 +442,22 @@ def sgemm_peak_tflops() -> float:
         torch.backends.cuda.matmul.allow_tf32 = keep
 
 
+def work_stream():
+    """A stream of this process's own, made current. A session given the NULL
+    stream runs on a private stream of the library's (the C ABI's rule), which
+    events on torch's default stream would not bracket; so every timed session
+    runs on this one, and the CUDA events of its timed region are recorded on
+    the stream its kernels are launched on."""
+    import torch
+    st = torch.cuda.Stream()
+    torch.cuda.set_stream(st)
+    return st
+
+
 def timed_session(sess, warmup_chunks, steps_chunks, stream, d: Dist, clocks=None, profile=False):
     import torch
+    if not stream.cuda_stream:
+        raise RuntimeError("timed sessions need a non-NULL stream (the library runs NULL-stream sessions on its own)")
     sess.run(warmup_chunks * CHUNK, sync=True)
     if profile:
         sess.profile(True)
@@ -535,7 +550,7 @@ def run_ours(args, d: Dist):
     torch.cuda.set_device(d.local)
     edpc.load()
     x = workload_input(d.rank)
-    stream = torch.cuda.current_stream()
+    stream = work_stream()
     W, K = args.warmup, args.steps
     out = {}
 
@@ -864,12 +879,12 @@ def run_files(args, d: Dist):
     torch.cuda.set_device(d.local)
     edpc.load()
     w = FILES
+    stream = work_stream()
     files = synth.uneven_files(w["files"], w["data_seed"] + d.rank, lo=w["lo"], hi=w["hi"])
     sizes = [f.size for f in files]
     cat = np.concatenate(files)
     xd = torch.from_numpy(cat).cuda()
     offs = np.concatenate([[0], np.cumsum(sizes)[:-1]])
-    stream = torch.cuda.current_stream()
     W, K = args.warmup, args.steps
 
     def cfg(streams, prec=edpc.EDPC_BF16):
