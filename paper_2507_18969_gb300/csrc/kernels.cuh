@@ -148,8 +148,10 @@ int embed_bwd_chunks(int b, int K);
 cudaError_t launch_embed_bwd(const uint8_t* ctx, const float* dX, int b, int K, int D, float* dE, float* part,
                              unsigned* cnt, cudaStream_t st);
 // Grouped mode: dE of group g (at dE + g * gs) sums the positions of its
-// stream rows [gi[g].r0, gi[g].r0 + gi[g].s) only, in increasing position
-// order; CTAs per group and pair of byte values (ctx 4-byte aligned).
+// stream rows [gi[g].r0, gi[g].r0 + gi[g].s) only, in a fixed order that
+// depends on the group alone (four quarters of the positions, each summed in
+// increasing order, then added in order); CTAs per group and pair of byte
+// values (ctx 4-byte aligned).
 cudaError_t launch_embed_bwd_groups(const uint8_t* ctx, const float* dX, int K, int D, float* dE,
                                     const GroupInfo* gi, int ngroups, size_t gs, cudaStream_t st);
 
